@@ -1,0 +1,416 @@
+/*
+ * ks_oracle.c -- plain, slow, single-threaded CPU oracle of persistent
+ * call-auction clearing over an ensemble of independent markets.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load or call this file.  It shares no code,
+ * header, table or helper with the CUDA library: every constant below is
+ * restated here from its published source.
+ *
+ * What it computes, and where each piece comes from:
+ *  - Clearing (Sec. II-A, Eq. 1-2): D_cum[p] = sum_{q>=p} BUY[q],
+ *    S_cum[p] = sum_{q<=p} SELL[q], V(p) = min(D_cum, S_cum),
+ *    p* = argmax V with ties to the lowest tick (Sec. III-D, Phase 4).
+ *    With max V = 0 there is no trade (a reading: the paper is silent).
+ *  - Allocation (Sec. IV-C worked example): all trades at p*; buys fill in
+ *    price priority from the top tick down, sells from the bottom tick up,
+ *    until V* is used up on each side.  Inside one tick the orders fill in
+ *    ascending agent index (a reading: the paper's book has no order identity).
+ *  - Agents, RNG and book dynamics are the build's stated readings of the
+ *    benchmark configurations (one working order per agent, Philox4x32-10
+ *    draws keyed by (seed, market, agent, step)); see the function comments.
+ *  - Philox4x32-10 is written from Salmon, Moraes, Dror and Shaw, "Parallel
+ *    random numbers: as easy as 1, 2, 3", SC'11.
+ *  - The trace hash uses the SplitMix64 finaliser printed in Sec. III-F.
+ *  - The MLP policy forward/backward are plain fp64 loops (behaviour-cloning
+ *    loss: cross-entropy on side and offset, squared error on log-quantity).
+ *
+ * The clearing loops are the definitions evaluated directly; the allocation is
+ * a greedy walk over price levels.  No blocking, fusion or reordering.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (SC'11): round function on a 4x32 counter with a 2x32 key.  */
+/* Multipliers and Weyl key increments as published with the generator.     */
+/* ------------------------------------------------------------------------ */
+static const uint32_t KO_PHILOX_MUL_A = 0xD2511F53u;
+static const uint32_t KO_PHILOX_MUL_B = 0xCD9E8D57u;
+static const uint32_t KO_PHILOX_WEYL_A = 0x9E3779B9u;
+static const uint32_t KO_PHILOX_WEYL_B = 0xBB67AE85u;
+
+void ko_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { /* key schedule: bump before every round but the first */
+      k0 += KO_PHILOX_WEYL_A;
+      k1 += KO_PHILOX_WEYL_B;
+    }
+    uint64_t prodA = (uint64_t)KO_PHILOX_MUL_A * (uint64_t)x0;
+    uint64_t prodB = (uint64_t)KO_PHILOX_MUL_B * (uint64_t)x2;
+    uint32_t hiA = (uint32_t)(prodA >> 32), loA = (uint32_t)prodA;
+    uint32_t hiB = (uint32_t)(prodB >> 32), loB = (uint32_t)prodB;
+    uint32_t y0 = hiB ^ x1 ^ k0;
+    uint32_t y1 = loB;
+    uint32_t y2 = hiA ^ x3 ^ k1;
+    uint32_t y3 = loA;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One Philox block for counter (step, agent, market, stream) under the key   */
+/* (seed low word, seed high word).                                           */
+static void ko_draw(uint64_t seed, uint32_t step, uint32_t agent, uint32_t market,
+                    uint32_t stream, uint32_t w[4]) {
+  uint32_t ctr[4] = {step, agent, market, stream};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  ko_philox4x32_10(ctr, key, w);
+}
+
+/* floor(u * n) for u = w / 2^32: the integer range draw of Sec. III-C's      */
+/* q = 1 + floor(u q_max), taken on the 32-bit word directly.                 */
+static int64_t ko_range(uint32_t w, int64_t n) { return (int64_t)(((uint64_t)w * (uint64_t)n) >> 32); }
+
+static int32_t ko_clamp(int64_t x, int32_t lo, int32_t hi) {
+  if (x < lo) return lo;
+  if (x > hi) return hi;
+  return (int32_t)x;
+}
+
+/* SplitMix64 finaliser (Sec. III-F) used to fold the clearing trace. */
+static uint64_t ko_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+uint64_t ko_trace_hash_update(uint64_t h, uint32_t step, int32_t pstar, int32_t vol) {
+  uint64_t word = ((uint64_t)(uint32_t)pstar << 32) | (uint64_t)(uint32_t)vol;
+  return ko_mix64(h ^ word ^ ((uint64_t)step * 0x9E3779B97F4A7C15ull));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Clearing of one aggregated book (Sec. II-A, Eq. 1-2; Sec. III-D).          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t vstar;   /* executed volume V* = max_p V(p); 0 means no trade     */
+  int32_t pstar;   /* clearing tick, -1 when V* = 0                         */
+  int32_t p_buy;   /* marginal buy tick  max{p : D_cum[p] >= V*}, -1 if none */
+  int32_t p_sell;  /* marginal sell tick min{p : S_cum[p] >= V*}, -1 if none */
+  int32_t argmax;  /* argmax of V under the tie rule, defined also at V* = 0 */
+} ko_clear_result;
+
+/* tie_rule 0: lowest tick among maximisers (Sec. III-D).
+ * tie_rule 1: smallest |D_cum - S_cum| among maximisers, then lowest tick.   */
+int ko_clear_book(int32_t L, const int64_t* buy, const int64_t* sell, int32_t tie_rule,
+                  int64_t* dcum, int64_t* scum, int64_t* vol, ko_clear_result* res) {
+  if (L <= 0) return -1;
+  /* D_cum[p] = sum over q >= p of BUY[q] */
+  int64_t run = 0;
+  for (int32_t p = L - 1; p >= 0; --p) {
+    run += buy[p];
+    dcum[p] = run;
+  }
+  /* S_cum[p] = sum over q <= p of SELL[q] */
+  run = 0;
+  for (int32_t p = 0; p < L; ++p) {
+    run += sell[p];
+    scum[p] = run;
+  }
+  /* V(p) = min(D_cum[p], S_cum[p]) */
+  for (int32_t p = 0; p < L; ++p) vol[p] = dcum[p] < scum[p] ? dcum[p] : scum[p];
+  /* maximum executable volume */
+  int64_t vmax = vol[0];
+  for (int32_t p = 1; p < L; ++p)
+    if (vol[p] > vmax) vmax = vol[p];
+  /* clearing tick under the tie rule */
+  int32_t best = -1;
+  for (int32_t p = 0; p < L; ++p) {
+    if (vol[p] != vmax) continue;
+    if (best < 0) { best = p; continue; }
+    if (tie_rule == 1) {
+      int64_t ib = dcum[best] - scum[best]; if (ib < 0) ib = -ib;
+      int64_t ip = dcum[p] - scum[p];       if (ip < 0) ip = -ip;
+      if (ip < ib) best = p;               /* equal imbalance keeps the lower tick */
+    }
+  }
+  res->argmax = best;
+  res->vstar = vmax;
+  if (vmax <= 0) {
+    res->vstar = 0;
+    res->pstar = -1;
+    res->p_buy = -1;
+    res->p_sell = -1;
+    return 0;
+  }
+  res->pstar = best;
+  res->p_buy = -1;
+  for (int32_t p = 0; p < L; ++p)
+    if (dcum[p] >= vmax) res->p_buy = p;      /* keeps the largest such p */
+  res->p_sell = -1;
+  for (int32_t p = L - 1; p >= 0; --p)
+    if (scum[p] >= vmax) res->p_sell = p;     /* keeps the smallest such p */
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Greedy allocation (Sec. IV-C): fill buys from the highest tick down and    */
+/* sells from the lowest tick up, each tick in ascending agent index, until   */
+/* V* is used up on each side.  side: 0 = buy, 1 = sell; qty 0 = no order.   */
+/* fill[a] receives the executed quantity of agent a's order.                 */
+/* ------------------------------------------------------------------------ */
+int ko_allocate(int32_t L, int32_t A, const int32_t* side, const int32_t* tick,
+                const int32_t* qty, int64_t vstar, int32_t* fill) {
+  for (int32_t a = 0; a < A; ++a) fill[a] = 0;
+  if (vstar <= 0) return 0;
+  /* per-tick order lists in ascending agent index: count, then place */
+  int32_t* start = (int32_t*)calloc((size_t)2 * (L + 1), sizeof(int32_t));
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(A > 0 ? A : 1));
+  int32_t* cursor = (int32_t*)malloc(sizeof(int32_t) * (size_t)2 * L);
+  if (!start || !order || !cursor) { free(start); free(order); free(cursor); return -2; }
+  for (int32_t a = 0; a < A; ++a) {
+    if (qty[a] <= 0) continue;
+    if (tick[a] < 0 || tick[a] >= L) { free(start); free(order); free(cursor); return -3; }
+    start[side[a] * (L + 1) + tick[a] + 1] += 1;
+  }
+  int32_t base = 0;
+  for (int32_t s = 0; s < 2; ++s) {
+    start[s * (L + 1)] = base;
+    for (int32_t p = 0; p < L; ++p) {
+      int32_t c = start[s * (L + 1) + p + 1];
+      start[s * (L + 1) + p + 1] = start[s * (L + 1) + p] + c;
+    }
+    base = start[s * (L + 1) + L];
+  }
+  for (int32_t s = 0; s < 2; ++s)
+    for (int32_t p = 0; p < L; ++p) cursor[s * L + p] = start[s * (L + 1) + p];
+  for (int32_t a = 0; a < A; ++a) {
+    if (qty[a] <= 0) continue;
+    order[cursor[side[a] * L + tick[a]]++] = a;
+  }
+  /* buys: highest tick first */
+  int64_t left = vstar;
+  for (int32_t p = L - 1; p >= 0 && left > 0; --p) {
+    for (int32_t i = start[p]; i < start[p + 1] && left > 0; ++i) {
+      int32_t a = order[i];
+      int64_t f = qty[a] < left ? qty[a] : left;
+      fill[a] = (int32_t)f;
+      left -= f;
+    }
+  }
+  int64_t buy_left = left;
+  /* sells: lowest tick first */
+  left = vstar;
+  for (int32_t p = 0; p < L && left > 0; ++p) {
+    for (int32_t i = start[(L + 1) + p]; i < start[(L + 1) + p + 1] && left > 0; ++i) {
+      int32_t a = order[i];
+      int64_t f = qty[a] < left ? qty[a] : left;
+      fill[a] = (int32_t)f;
+      left -= f;
+    }
+  }
+  free(start); free(order); free(cursor);
+  /* V* never exceeds either side's total, so both walks must finish */
+  return (buy_left == 0 && left == 0) ? 0 : -4;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Market simulation.                                                         */
+/* ------------------------------------------------------------------------ */
+enum { KO_ZI = 0, KO_MOM = 1, KO_MR = 2 };
+#define KO_HIST 9
+
+typedef struct {
+  uint64_t seed;
+  int32_t carry_book;        /* 0: unfilled orders discarded each step; 1: carried */
+  uint32_t cancel_thresh;    /* a live order is cancelled iff draw word 0 < this    */
+  int32_t mix_pct[3];        /* percent ZI / momentum / mean-reversion              */
+  int32_t zi_offset;         /* ZI tick offset uniform in [-zi_offset, zi_offset]   */
+  int32_t zi_qmax;           /* ZI quantity uniform in [1, zi_qmax]                 */
+  int32_t mom_lookback;      /* momentum return horizon in steps (1..8)             */
+  int32_t mom_offset_max;    /* momentum offset uniform in [0, mom_offset_max]      */
+  int32_t mr_offset_max;     /* mean-reversion offset uniform in [0, mr_offset_max] */
+  int32_t rb_qmax;           /* momentum / mean-reversion quantity in [1, rb_qmax]  */
+  int32_t mlp_pct;           /* percent of agents driven by the MLP policy          */
+  int32_t tie_rule;          /* 0 lowest tick, 1 min imbalance then lowest          */
+} ko_params;
+
+typedef struct {
+  int32_t last;              /* last clearing tick (initially L/2)                  */
+  int32_t hist[KO_HIST];     /* hist[j] = last clearing tick j steps ago            */
+  int32_t fund;              /* per-market fundamental tick                         */
+  int32_t trades;            /* steps with V* > 0                                   */
+  int32_t last_v;            /* V* of the most recent step                          */
+  int32_t pad_;
+  int64_t sum_p;             /* sum of p* over trading steps                        */
+  int64_t sum_v;             /* sum of V* over all steps                            */
+  uint64_t hash;             /* running trace hash                                  */
+} ko_market_scalars;
+
+/* Per-agent arrays of one market (length A each). */
+typedef struct {
+  int32_t* qty;    /* working-order quantity, 0 = no working order */
+  int32_t* side;   /* 0 buy, 1 sell */
+  int32_t* tick;
+  int32_t* atype;  /* KO_ZI / KO_MOM / KO_MR */
+  int32_t* mlp;    /* 1 = decisions come from the MLP policy */
+  int32_t* inv;
+  int64_t* cash;
+} ko_agents;
+
+/* Initial state of market m: price L/2 everywhere in the history, no orders,
+ * zero inventory and cash.  Agent class from stream 1 word 0 as a percentile;
+ * MLP membership from stream 1 word 1; fundamental uniform on [L/4, 3L/4]
+ * from stream 2 word 0. */
+int ko_init_market(const ko_params* P, uint32_t m, int32_t L, int32_t A,
+                   ko_agents* ag, ko_market_scalars* ms) {
+  if (L < 2 || A < 0) return -1;
+  memset(ms, 0, sizeof(*ms));
+  ms->last = L / 2;
+  for (int j = 0; j < KO_HIST; ++j) ms->hist[j] = L / 2;
+  uint32_t w[4];
+  ko_draw(P->seed, 0u, 0u, m, 2u, w);
+  ms->fund = L / 4 + (int32_t)ko_range(w[0], L / 2 + 1);
+  for (int32_t a = 0; a < A; ++a) {
+    ko_draw(P->seed, 0u, (uint32_t)a, m, 1u, w);
+    int64_t pct = ko_range(w[0], 100);
+    if (pct < P->mix_pct[0]) ag->atype[a] = KO_ZI;
+    else if (pct < P->mix_pct[0] + P->mix_pct[1]) ag->atype[a] = KO_MOM;
+    else ag->atype[a] = KO_MR;
+    ag->mlp[a] = ko_range(w[1], 100) < P->mlp_pct ? 1 : 0;
+    ag->qty[a] = 0;
+    ag->side[a] = 0;
+    ag->tick[a] = 0;
+    ag->inv[a] = 0;
+    ag->cash[a] = 0;
+  }
+  return 0;
+}
+
+/* Rule-based decision of one agent with an empty working order, from the
+ * per-step draw words w[1] (side), w[2] (offset), w[3] (quantity). */
+static void ko_decide_rule(const ko_params* P, int32_t L, int32_t atype,
+                           const ko_market_scalars* ms, const uint32_t w[4],
+                           int32_t* side, int32_t* tick, int32_t* qty) {
+  int32_t coin = (w[1] >> 31) ? 1 : 0; /* buy iff w1 < 2^31 */
+  int32_t last = ms->last;
+  if (atype == KO_ZI) {
+    int64_t off = ko_range(w[2], 2 * (int64_t)P->zi_offset + 1) - P->zi_offset;
+    *side = coin;
+    *tick = ko_clamp((int64_t)last + off, 0, L - 1);
+    *qty = 1 + (int32_t)ko_range(w[3], P->zi_qmax);
+    return;
+  }
+  int32_t s;
+  int64_t off;
+  if (atype == KO_MOM) {
+    int32_t ret = ms->hist[0] - ms->hist[P->mom_lookback];
+    s = ret > 0 ? 0 : (ret < 0 ? 1 : coin);
+    off = ko_range(w[2], (int64_t)P->mom_offset_max + 1);
+  } else {
+    s = last < ms->fund ? 0 : (last > ms->fund ? 1 : coin);
+    off = ko_range(w[2], (int64_t)P->mr_offset_max + 1);
+  }
+  *side = s;
+  *tick = ko_clamp((int64_t)last + (s == 0 ? off : -off), 0, L - 1);
+  *qty = 1 + (int32_t)ko_range(w[3], P->rb_qmax);
+}
+
+/* Optional replay of externally supplied decisions for MLP agents (used to
+ * re-run the clearing on orders emitted by another engine).  For step j of
+ * the call and agent a, entry j*A + a holds side (0 buy, 1 sell, 2 pass),
+ * tick and qty; only entries of MLP agents with an empty order are read. */
+typedef struct {
+  const int32_t* side;
+  const int32_t* tick;
+  const int32_t* qty;
+} ko_replay;
+
+/* Run steps [s0, s0 + n) of market m.  trace_p / trace_v (nullable, length n)
+ * receive p* (-1 for no trade) and V* per step.  Returns 0 on success. */
+int ko_run_market(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agents* ag,
+                  ko_market_scalars* ms, uint32_t s0, uint32_t n, const ko_replay* replay,
+                  int32_t* trace_p, int32_t* trace_v) {
+  if (L < 2 || A < 0) return -1;
+  int64_t* buy = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int64_t* sell = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int64_t* dcum = (int64_t*)malloc(sizeof(int64_t) * (size_t)L);
+  int64_t* scum = (int64_t*)malloc(sizeof(int64_t) * (size_t)L);
+  int64_t* vol = (int64_t*)malloc(sizeof(int64_t) * (size_t)L);
+  int32_t* fill = (int32_t*)malloc(sizeof(int32_t) * (size_t)(A > 0 ? A : 1));
+  int rc = 0;
+  if (!buy || !sell || !dcum || !scum || !vol || !fill) { rc = -2; goto done; }
+  for (uint32_t j = 0; j < n; ++j) {
+    uint32_t s = s0 + j;
+    /* 1-2. cancellation of working orders, then decisions of empty agents */
+    for (int32_t a = 0; a < A; ++a) {
+      uint32_t w[4];
+      ko_draw(P->seed, s, (uint32_t)a, m, 0u, w);
+      if (P->carry_book && ag->qty[a] > 0 && w[0] < P->cancel_thresh) ag->qty[a] = 0;
+      if (ag->qty[a] > 0) continue;
+      if (ag->mlp[a]) {
+        if (!replay) { rc = -5; goto done; }
+        size_t e = (size_t)j * (size_t)A + (size_t)a;
+        int32_t sd = replay->side[e];
+        if (sd == 2) continue; /* pass: no order this step */
+        if (sd < 0 || sd > 1 || replay->tick[e] < 0 || replay->tick[e] >= L ||
+            replay->qty[e] <= 0) { rc = -6; goto done; }
+        ag->side[a] = sd;
+        ag->tick[a] = replay->tick[e];
+        ag->qty[a] = replay->qty[e];
+        continue;
+      }
+      ko_decide_rule(P, L, ag->atype[a], ms, w, &ag->side[a], &ag->tick[a], &ag->qty[a]);
+    }
+    /* 3. aggregated book of all working orders */
+    for (int32_t p = 0; p < L; ++p) { buy[p] = 0; sell[p] = 0; }
+    for (int32_t a = 0; a < A; ++a) {
+      if (ag->qty[a] <= 0) continue;
+      if (ag->side[a] == 0) buy[ag->tick[a]] += ag->qty[a];
+      else sell[ag->tick[a]] += ag->qty[a];
+    }
+    /* 4. clearing */
+    ko_clear_result cr;
+    if (ko_clear_book(L, buy, sell, P->tie_rule, dcum, scum, vol, &cr) != 0) { rc = -3; goto done; }
+    if (dcum[0] > INT32_MAX || scum[L - 1] > INT32_MAX) { rc = -7; goto done; }
+    /* 5. allocation and accounts at the single price p* */
+    if (cr.vstar > 0) {
+      int r = ko_allocate(L, A, ag->side, ag->tick, ag->qty, cr.vstar, fill);
+      if (r != 0) { rc = -4; goto done; }
+      for (int32_t a = 0; a < A; ++a) {
+        int32_t f = fill[a];
+        if (f == 0) continue;
+        if (ag->side[a] == 0) {
+          ag->inv[a] += f;
+          ag->cash[a] -= (int64_t)cr.pstar * f;
+        } else {
+          ag->inv[a] -= f;
+          ag->cash[a] += (int64_t)cr.pstar * f;
+        }
+        ag->qty[a] -= f;
+      }
+      ms->last = cr.pstar;
+      ms->sum_p += cr.pstar;
+      ms->sum_v += cr.vstar;
+      ms->trades += 1;
+    }
+    /* 6. discard mode: no order survives the step */
+    if (!P->carry_book)
+      for (int32_t a = 0; a < A; ++a) ag->qty[a] = 0;
+    /* 7. price history, statistics and trace hash */
+    for (int k = KO_HIST - 1; k > 0; --k) ms->hist[k] = ms->hist[k - 1];
+    ms->hist[0] = ms->last;
+    ms->last_v = (int32_t)cr.vstar;
+    ms->hash = ko_trace_hash_update(ms->hash, s, cr.pstar, (int32_t)cr.vstar);
+    if (trace_p) trace_p[j] = cr.pstar;
+    if (trace_v) trace_v[j] = (int32_t)cr.vstar;
+  }
+done:
+  free(buy); free(sell); free(dcum); free(scum); free(vol); free(fill);
+  return rc;
+}

@@ -1,0 +1,282 @@
+"""ctypes front-end of the C oracle in ``ks_oracle.c`` (test infrastructure).
+
+The oracle is a plain single-threaded CPU simulator written from the paper
+(Sec. II-A Eq. 1-2 clearing, Sec. III-D tie rule, Sec. IV-C allocation) and
+from the stated readings of the benchmark configurations.  It shares no code
+with the CUDA library; the only thing both sides receive in common is the
+seeded workload description (ensemble sizes and agent parameters).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` leg of
+``bench.py`` may use it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ks_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libks_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+HIST = 9
+ZI, MOM, MR = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile ks_oracle.c into a shared library with gcc (no GPU code)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+    if fresh and not force:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("carry_book", ctypes.c_int32),
+        ("cancel_thresh", ctypes.c_uint32),
+        ("mix_pct", ctypes.c_int32 * 3),
+        ("zi_offset", ctypes.c_int32),
+        ("zi_qmax", ctypes.c_int32),
+        ("mom_lookback", ctypes.c_int32),
+        ("mom_offset_max", ctypes.c_int32),
+        ("mr_offset_max", ctypes.c_int32),
+        ("rb_qmax", ctypes.c_int32),
+        ("mlp_pct", ctypes.c_int32),
+        ("tie_rule", ctypes.c_int32),
+    ]
+
+
+class MarketScalars(ctypes.Structure):
+    _fields_ = [
+        ("last", ctypes.c_int32),
+        ("hist", ctypes.c_int32 * HIST),
+        ("fund", ctypes.c_int32),
+        ("trades", ctypes.c_int32),
+        ("last_v", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
+        ("sum_p", ctypes.c_int64),
+        ("sum_v", ctypes.c_int64),
+        ("hash", ctypes.c_uint64),
+    ]
+
+
+class _Agents(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("qty", "side", "tick", "atype", "mlp", "inv", "cash")]
+
+
+class _Replay(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("side", "tick", "qty")]
+
+
+class _ClearResult(ctypes.Structure):
+    _fields_ = [
+        ("vstar", ctypes.c_int64),
+        ("pstar", ctypes.c_int32),
+        ("p_buy", ctypes.c_int32),
+        ("p_sell", ctypes.c_int32),
+        ("argmax", ctypes.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # KS_ORACLE_LIB lets the mutation tests load a deliberately broken copy
+            lib = ctypes.CDLL(os.environ.get("KS_ORACLE_LIB") or build())
+            P = ctypes.POINTER
+            lib.ko_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+            lib.ko_philox4x32_10.restype = None
+            lib.ko_trace_hash_update.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32]
+            lib.ko_trace_hash_update.restype = ctypes.c_uint64
+            lib.ko_clear_book.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(_ClearResult)]
+            lib.ko_clear_book.restype = ctypes.c_int
+            lib.ko_allocate.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+            lib.ko_allocate.restype = ctypes.c_int
+            lib.ko_init_market.argtypes = [P(Params), ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                           P(_Agents), P(MarketScalars)]
+            lib.ko_init_market.restype = ctypes.c_int
+            lib.ko_run_market.argtypes = [P(Params), ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                          P(_Agents), P(MarketScalars), ctypes.c_uint32, ctypes.c_uint32,
+                                          P(_Replay), ctypes.c_void_p, ctypes.c_void_p]
+            lib.ko_run_market.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------------------
+# RNG and hash
+# ---------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block (Salmon et al., SC'11) for a 4-word counter and 2-word key."""
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.ko_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def trace_hash_update(h: int, step: int, pstar: int, vol: int) -> int:
+    return int(_load().ko_trace_hash_update(h, step, pstar, vol))
+
+
+# ---------------------------------------------------------------------------
+# Clearing of one book and greedy allocation
+# ---------------------------------------------------------------------------
+@dataclass
+class Clearing:
+    dcum: np.ndarray
+    scum: np.ndarray
+    vol: np.ndarray
+    vstar: int
+    pstar: int
+    p_buy: int
+    p_sell: int
+    argmax: int
+
+
+def clear_book(buy, sell, tie_rule: int = 0) -> Clearing:
+    """Uniform-price call-auction clearing of one aggregated book (Sec. II-A, Eq. 1-2)."""
+    buy = np.ascontiguousarray(buy, dtype=np.int64)
+    sell = np.ascontiguousarray(sell, dtype=np.int64)
+    L = buy.shape[0]
+    assert sell.shape[0] == L
+    d = np.zeros(L, np.int64)
+    s = np.zeros(L, np.int64)
+    v = np.zeros(L, np.int64)
+    r = _ClearResult()
+    rc = _load().ko_clear_book(L, _ptr(buy), _ptr(sell), tie_rule, _ptr(d), _ptr(s), _ptr(v), ctypes.byref(r))
+    if rc != 0:
+        raise ValueError(f"ko_clear_book failed: {rc}")
+    return Clearing(d, s, v, int(r.vstar), int(r.pstar), int(r.p_buy), int(r.p_sell), int(r.argmax))
+
+
+def allocate(L: int, side, tick, qty, vstar: int) -> np.ndarray:
+    """Greedy price-then-agent-index allocation of V* (Sec. IV-C)."""
+    side = np.ascontiguousarray(side, dtype=np.int32)
+    tick = np.ascontiguousarray(tick, dtype=np.int32)
+    qty = np.ascontiguousarray(qty, dtype=np.int32)
+    A = side.shape[0]
+    fill = np.zeros(A, np.int32)
+    rc = _load().ko_allocate(L, A, _ptr(side), _ptr(tick), _ptr(qty), int(vstar), _ptr(fill))
+    if rc != 0:
+        raise ValueError(f"ko_allocate failed: {rc}")
+    return fill
+
+
+# ---------------------------------------------------------------------------
+# Market simulation
+# ---------------------------------------------------------------------------
+@dataclass
+class Market:
+    """Full state of one market as the oracle holds it."""
+    m: int
+    L: int
+    A: int
+    qty: np.ndarray
+    side: np.ndarray
+    tick: np.ndarray
+    atype: np.ndarray
+    mlp: np.ndarray
+    inv: np.ndarray
+    cash: np.ndarray
+    sc: MarketScalars = field(default_factory=MarketScalars)
+
+    def _agents(self) -> _Agents:
+        return _Agents(*[_ptr(getattr(self, n)) for n in ("qty", "side", "tick", "atype", "mlp", "inv", "cash")])
+
+    @property
+    def last(self) -> int:
+        return int(self.sc.last)
+
+    @property
+    def hist(self) -> np.ndarray:
+        return np.array(list(self.sc.hist), dtype=np.int32)
+
+    def scalars(self) -> dict:
+        sc = self.sc
+        return dict(last=int(sc.last), hist=list(sc.hist), fund=int(sc.fund), trades=int(sc.trades),
+                    last_v=int(sc.last_v), sum_p=int(sc.sum_p), sum_v=int(sc.sum_v), hash=int(sc.hash))
+
+
+def make_params(p: dict) -> Params:
+    """Build the oracle's parameter block from a workload description dict."""
+    P = Params()
+    P.seed = int(p["seed"])
+    P.carry_book = int(p["carry_book"])
+    P.cancel_thresh = int(p["cancel_thresh_q32"])
+    for i in range(3):
+        P.mix_pct[i] = int(p["mix_pct"][i])
+    P.zi_offset = int(p["zi_offset"])
+    P.zi_qmax = int(p["zi_qmax"])
+    P.mom_lookback = int(p["mom_lookback"])
+    P.mom_offset_max = int(p["mom_offset_max"])
+    P.mr_offset_max = int(p["mr_offset_max"])
+    P.rb_qmax = int(p["rb_qmax"])
+    P.mlp_pct = int(p.get("mlp_pct", 0))
+    P.tie_rule = int(p.get("tie_rule", 0))
+    return P
+
+
+def init_market(params: dict, m: int, L: int, A: int) -> Market:
+    z = lambda dt: np.zeros(max(A, 1), dt)[:A]  # noqa: E731
+    mk = Market(m, L, A, z(np.int32), z(np.int32), z(np.int32), z(np.int32), z(np.int32), z(np.int32), z(np.int64))
+    P = make_params(params)
+    rc = _load().ko_init_market(ctypes.byref(P), m, L, A, ctypes.byref(mk._agents()), ctypes.byref(mk.sc))
+    if rc != 0:
+        raise ValueError(f"ko_init_market failed: {rc}")
+    return mk
+
+
+def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trace: bool = True):
+    """Advance ``mk`` in place over steps [s0, s0+n).  Returns (trace_p, trace_v) or None.
+
+    ``replay``: optional dict of int32 arrays ``side``, ``tick``, ``qty`` of shape (n, A)
+    holding the decisions of MLP agents (side 2 = pass).
+    """
+    P = make_params(params)
+    tp = np.zeros(max(n, 1), np.int32)
+    tv = np.zeros(max(n, 1), np.int32)
+    rp = None
+    keep = []
+    if replay is not None:
+        arrs = [np.ascontiguousarray(replay[k], dtype=np.int32) for k in ("side", "tick", "qty")]
+        for a in arrs:
+            assert a.size == n * mk.A
+        keep = arrs
+        rp = ctypes.byref(_Replay(*[_ptr(a) for a in arrs]))
+    rc = _load().ko_run_market(ctypes.byref(P), mk.m, mk.L, mk.A, ctypes.byref(mk._agents()), ctypes.byref(mk.sc),
+                               s0, n, rp, _ptr(tp) if want_trace else None, _ptr(tv) if want_trace else None)
+    del keep
+    if rc != 0:
+        raise ValueError(f"ko_run_market failed: {rc}")
+    return (tp[:n], tv[:n]) if want_trace else None
+
+
+def simulate(params: dict, m: int, L: int, A: int, steps: int, replay=None):
+    """Initialise market m and run ``steps`` steps from step 0; returns (market, trace_p, trace_v)."""
+    mk = init_market(params, m, L, A)
+    tp, tv = run_market(params, mk, 0, steps, replay=replay)
+    return mk, tp, tv

@@ -1,0 +1,48 @@
+"""Planted-mistake check of the oracle pins.
+
+Each case copies ks_oracle.c, plants one plausible mistake (a dropped term, a
+wrong sign, a transposed operand, a reversed walk), builds the copy with gcc
+and runs the pin tests against it in a child process.  The pins must fail for
+every mutant, which shows they constrain each part of the oracle.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ks_oracle.c")
+
+MUTANTS = {
+    "exclusive_demand": ("    run += buy[p];\n    dcum[p] = run;", "    dcum[p] = run;\n    run += buy[p];"),
+    "highest_tick_tie": ("if (best < 0) { best = p; continue; }", "best = p; continue;"),
+    "sells_from_top": ("for (int32_t p = 0; p < L && left > 0; ++p) {",
+                       "for (int32_t p = L - 1; p >= 0 && left > 0; --p) {"),
+    "buyer_cash_sign": ("ag->cash[a] -= (int64_t)cr.pstar * f;", "ag->cash[a] += (int64_t)cr.pstar * f;"),
+    "philox_operand": ("KO_PHILOX_MUL_B * (uint64_t)x2", "KO_PHILOX_MUL_B * (uint64_t)x1"),
+    "philox_key_schedule": ("k1 += KO_PHILOX_WEYL_B;", "k1 += KO_PHILOX_WEYL_A;"),
+    "history_not_shifted": ("ms->hist[0] = ms->last;", "ms->hist[0] = ms->hist[1];"),
+    "marginal_buy_strict": ("if (dcum[p] >= vmax) res->p_buy = p;", "if (dcum[p] > vmax) res->p_buy = p;"),
+    "mixer_shift": ("z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;", "z = (z ^ (z >> 28)) * 0x94d049bb133111ebull;"),
+    "agent_priority_reversed": ("for (int32_t a = 0; a < A; ++a) {\n    if (qty[a] <= 0) continue;\n    order[",
+                                "for (int32_t a = A - 1; a >= 0; --a) {\n    if (qty[a] <= 0) continue;\n    order["),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "mut.c")
+        so = os.path.join(d, "libmut.so")
+        open(c, "w").write(src.replace(old, new))
+        subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", so, c, "-lm"], check=True)
+        env = dict(os.environ, KS_ORACLE_LIB=so)
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -1,0 +1,322 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: the expected values are the
+paper's worked example (Sec. IV-C), published generator test vectors, direct
+order-by-order brute force on tiny books, and invariants of a uniform-price
+call auction (conservation, optimality, priority, an uncrossed residual book).
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2606_21784_gb300 import workloads as wl
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_kv(name):
+    out = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(":", 1)
+            out[k.strip()] = [int(x) for x in v.split()]
+    return out
+
+
+# --------------------------------------------------------------------------
+# RNG and hash pins
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    with open(os.path.join(GOLD, "philox4x32_10_kat.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        ctr = [int(x, 16) for x in r[0:4]]
+        key = [int(x, 16) for x in r[4:6]]
+        want = [int(x, 16) for x in r[6:10]]
+        assert [int(x) for x in o.philox4x32_10(ctr, key)] == want
+
+
+def test_trace_hash_mixer_is_splitmix64():
+    # With h = 0 and a zero (p*, V) word the update is the SplitMix64 output
+    # for state k * gamma, so the published sequence pins the mixer constants.
+    with open(os.path.join(GOLD, "splitmix64_sequence.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    for k, out in rows:
+        assert o.trace_hash_update(0, int(k), 0, 0) == int(out, 16)
+
+
+# --------------------------------------------------------------------------
+# Clearing pins
+# --------------------------------------------------------------------------
+def test_worked_example_clearing():
+    g = _read_kv("worked_example_L5.txt")
+    c = o.clear_book(g["BUY"], g["SELL"])
+    assert list(c.dcum) == g["D_cum"]
+    assert list(c.scum) == g["S_cum"]
+    assert list(c.vol) == g["V"]
+    assert c.pstar == g["p_star"][0]
+    assert c.vstar == g["V_star"][0]
+
+
+def test_worked_example_residual_book():
+    # One order per non-empty tick and side, in tick order; the greedy fill
+    # must leave the paper's residual books.
+    g = _read_kv("worked_example_L5.txt")
+    L = g["L"][0]
+    side, tick, qty = [], [], []
+    for s, arr in ((0, g["BUY"]), (1, g["SELL"])):
+        for p, q in enumerate(arr):
+            if q:
+                side.append(s); tick.append(p); qty.append(q)
+    c = o.clear_book(g["BUY"], g["SELL"])
+    fill = o.allocate(L, side, tick, qty, c.vstar)
+    new_bid = np.zeros(L, int)
+    new_ask = np.zeros(L, int)
+    for s, p, q, f in zip(side, tick, qty, fill):
+        (new_bid if s == 0 else new_ask)[p] += q - f
+    assert list(new_bid) == g["new_bid"]
+    assert list(new_ask) == g["new_ask"]
+
+
+def _brute_clear(buy, sell, tie_rule):
+    """Order-by-order evaluation: at each candidate price, every buyer whose
+    limit is at or above it and every seller whose limit is at or below it is
+    willing; the tradable volume is the smaller willing total."""
+    L = len(buy)
+    best_p, best_v, best_imb = None, -1, None
+    for p in range(L):
+        d = 0
+        for q in range(L):
+            if q >= p:
+                d += buy[q]
+        s = 0
+        for q in range(L):
+            if q <= p:
+                s += sell[q]
+        v = min(d, s)
+        imb = abs(d - s)
+        better = v > best_v or (tie_rule == 1 and v == best_v and imb < best_imb)
+        if better:
+            best_p, best_v, best_imb = p, v, imb
+    return best_p, best_v
+
+
+def test_clearing_brute_force_exhaustive_tiny():
+    for L in (1, 2, 3, 4):
+        for vals in itertools.product(range(3), repeat=2 * L):
+            buy, sell = list(vals[:L]), list(vals[L:])
+            for tie in (0, 1):
+                c = o.clear_book(buy, sell, tie)
+                bp, bv = _brute_clear(buy, sell, tie)
+                assert c.vstar == bv
+                if bv > 0:
+                    assert c.pstar == bp, (buy, sell, tie)
+                else:
+                    assert c.pstar == -1
+                    assert c.argmax == bp
+
+
+def test_clearing_brute_force_random():
+    rng = np.random.default_rng(11)
+    for _ in range(3000):
+        L = int(rng.integers(2, 17))
+        dens = rng.random()
+        buy = [int(x) if rng.random() < dens else 0 for x in rng.integers(0, 6, L)]
+        sell = [int(x) if rng.random() < dens else 0 for x in rng.integers(0, 6, L)]
+        for tie in (0, 1):
+            c = o.clear_book(buy, sell, tie)
+            bp, bv = _brute_clear(buy, sell, tie)
+            assert c.vstar == bv
+            assert (c.pstar if bv > 0 else c.argmax) == bp
+            if bv > 0:
+                # marginal ticks by their definitions
+                d = [sum(buy[p:]) for p in range(L)]
+                s = [sum(sell[: p + 1]) for p in range(L)]
+                assert c.p_buy == max(p for p in range(L) if d[p] >= bv)
+                assert c.p_sell == min(p for p in range(L) if s[p] >= bv)
+
+
+# --------------------------------------------------------------------------
+# Allocation pins: priority properties that determine the fill uniquely
+# --------------------------------------------------------------------------
+def _check_allocation(L, side, tick, qty, fill, vstar, pstar):
+    side, tick, qty, fill = map(np.asarray, (side, tick, qty, fill))
+    assert np.all(fill >= 0) and np.all(fill <= qty)
+    for s in (0, 1):
+        sel = side == s
+        assert int(fill[sel].sum()) == vstar
+        # a filled buy is willing at p* (limit >= p*); a filled sell limit <= p*
+        if vstar > 0:
+            if s == 0:
+                assert np.all(tick[sel & (fill > 0)] >= pstar)
+            else:
+                assert np.all(tick[sel & (fill > 0)] <= pstar)
+        idx = np.nonzero(sel & (qty > 0))[0]
+        for a in idx:
+            if fill[a] == 0:
+                continue
+            for b in idx:
+                better_price = tick[b] > tick[a] if s == 0 else tick[b] < tick[a]
+                same_price_earlier = tick[b] == tick[a] and b < a
+                if better_price or same_price_earlier:
+                    assert fill[b] == qty[b], "priority violated"
+    # residual book uncrossed
+    res = qty - fill
+    bids = tick[(side == 0) & (res > 0)]
+    asks = tick[(side == 1) & (res > 0)]
+    if len(bids) and len(asks):
+        assert bids.max() < asks.min()
+
+
+def test_allocation_priority_random():
+    rng = np.random.default_rng(5)
+    for _ in range(1500):
+        L = int(rng.integers(2, 12))
+        A = int(rng.integers(1, 24))
+        side = rng.integers(0, 2, A)
+        tick = rng.integers(0, L, A)
+        qty = rng.integers(0, 5, A)
+        buy = np.zeros(L, int)
+        sell = np.zeros(L, int)
+        for s, p, q in zip(side, tick, qty):
+            (buy if s == 0 else sell)[p] += q
+        c = o.clear_book(buy, sell)
+        fill = o.allocate(L, side, tick, qty, c.vstar)
+        _check_allocation(L, side, tick, qty, fill, c.vstar, c.pstar)
+
+
+# --------------------------------------------------------------------------
+# Simulation invariants
+# --------------------------------------------------------------------------
+def _small(name, **kw):
+    w = wl.workload(name)
+    p = dict(w["params"])
+    p.update(kw)
+    return p
+
+
+def _live_orders(mk):
+    live = mk.qty > 0
+    return live, mk.side, mk.tick
+
+
+@pytest.mark.parametrize("carry", [0, 1])
+def test_step_invariants(carry):
+    """Conservation, volume balance and an uncrossed residual book after every step."""
+    params = _small("plain_mix_8192", carry_book=carry)
+    L, A = 64, 96
+    for m in range(3):
+        mk = o.init_market(params, m, L, A)
+        for s in range(150):
+            inv0 = mk.inv.copy()
+            cash0 = mk.cash.copy()
+            tp, tv = o.run_market(params, mk, s, 1)
+            dinv = mk.inv - inv0
+            dcash = mk.cash - cash0
+            assert int(mk.inv.sum()) == 0
+            assert int(mk.cash.sum()) == 0
+            assert int(np.abs(dinv).sum()) == 2 * int(tv[0])
+            if tv[0] > 0:
+                assert int(tp[0]) == mk.last
+                # every trade at the single price p*
+                assert np.all(dcash == -int(tp[0]) * dinv)
+            else:
+                assert tp[0] == -1 and np.all(dinv == 0)
+            if carry:
+                live = mk.qty > 0
+                bids = mk.tick[live & (mk.side == 0)]
+                asks = mk.tick[live & (mk.side == 1)]
+                if len(bids) and len(asks):
+                    assert bids.max() < asks.min()
+            else:
+                assert np.all(mk.qty == 0)
+            assert list(mk.hist)[0] == mk.last
+
+
+def test_resume_equals_uninterrupted():
+    params = _small("plain_mix_8192")
+    L, A = 128, 64
+    a, tpa, tva = o.simulate(params, 7, L, A, 90)
+    b = o.init_market(params, 7, L, A)
+    tp1, tv1 = o.run_market(params, b, 0, 40)
+    tp2, tv2 = o.run_market(params, b, 40, 50)
+    assert np.array_equal(np.concatenate([tp1, tp2]), tpa)
+    assert np.array_equal(np.concatenate([tv1, tv2]), tva)
+    for f in ("qty", "side", "tick", "inv", "cash"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))
+    assert a.scalars() == b.scalars()
+
+
+def test_trace_hash_and_stats_fold_the_trace():
+    params = _small("plain_zi_64")
+    mk, tp, tv = o.simulate(params, 3, 256, 256, 60)
+    h = 0
+    for s, (p, v) in enumerate(zip(tp, tv)):
+        h = o.trace_hash_update(h, s, int(p), int(v))
+    sc = mk.scalars()
+    assert sc["hash"] == h
+    assert sc["sum_v"] == int(tv.sum())
+    assert sc["trades"] == int((tv > 0).sum())
+    assert sc["sum_p"] == int(tp[tv > 0].sum())
+
+
+def test_zero_intelligence_price_stays_near_centre():
+    # Symmetric ZI order flow around the last price keeps the clearing price
+    # near its start L/2 (the paper's mean clearing price sits at about L/2,
+    # Table I); with L = 256 the mean over 64 markets stays within a few ticks.
+    params = _small("plain_zi_64")
+    means = []
+    for m in range(16):
+        _, tp, tv = o.simulate(params, m, 256, 256, 200)
+        means.append(tp[tv > 0].mean())
+    assert abs(np.mean(means) - 128) < 12
+
+
+def test_agent_rules_follow_stated_readings():
+    """New orders obey the reading of each agent class (ranges and sides)."""
+    params = _small("plain_mix_8192", cancel_thresh_q32=0)
+    L, A = 1024, 400
+    mk = o.init_market(params, 2, L, A)
+    assert 256 <= mk.sc.fund <= 768
+    frac = np.bincount(mk.atype, minlength=3) / A
+    assert abs(frac[0] - 0.6) < 0.1 and abs(frac[1] - 0.2) < 0.08 and abs(frac[2] - 0.2) < 0.08
+    for s in range(60):
+        before_live = mk.qty > 0
+        last, hist = mk.last, mk.hist.copy()
+        o.run_market(params, mk, s, 1)
+        new = (~before_live) & (mk.qty > 0)
+        for a in np.nonzero(new)[0]:
+            t = mk.tick[a]
+            q = mk.qty[a]
+            assert 1 <= q <= 100
+            if mk.atype[a] == o.ZI:
+                assert max(0, last - 32) <= t <= min(L - 1, last + 32)
+            else:
+                if mk.atype[a] == o.MOM:
+                    r = hist[0] - hist[8]
+                    want = 0 if r > 0 else (1 if r < 0 else None)
+                else:
+                    f = mk.sc.fund
+                    want = 0 if last < f else (1 if last > f else None)
+                if want is not None:
+                    assert mk.side[a] == want
+                if mk.side[a] == 0:
+                    assert last <= t <= min(L - 1, last + 8)
+                else:
+                    assert max(0, last - 8) <= t <= last
+
+
+def test_discard_mode_every_agent_orders_each_step():
+    params = _small("plain_zi_64")
+    mk = o.init_market(params, 0, 256, 256)
+    tp, tv = o.run_market(params, mk, 0, 30)
+    # 256 ZI agents with qty in 1..10 on both sides: volume is always positive
+    assert np.all(tv > 0)
+    assert np.all(mk.qty == 0)
