@@ -1,0 +1,219 @@
+/*
+ * kineticsim.h -- C ABI of the GB300 persistent call-auction engine.
+ *
+ * One ensemble = M independent limit-order-book markets, each with L integer
+ * price ticks and A agents, advanced S steps at a time by one persistent
+ * sm_103a kernel that keeps each market's book and agent orders on chip for
+ * all steps of a call (the paper's Algorithm 1: inputs M markets, S steps,
+ * A agents, L price levels; output the final book and clearing statistics in
+ * global memory).
+ *
+ * Every step of every market:
+ *   1. each working order is cancelled with a fixed probability (carried
+ *      books only), then every agent without a working order draws a new
+ *      limit order (side, tick, qty) from one Philox4x32-10 block keyed by
+ *      (seed, market, agent, step);
+ *   2. orders are aggregated into per-tick BUY / SELL quantities;
+ *   3. D_cum[p] = sum_{q>=p} BUY[q], S_cum[p] = sum_{q<=p} SELL[q]
+ *      (Sec. II-A, Eq. 1), the clearing tick p* maximises
+ *      V(p) = min(D_cum[p], S_cum[p]) with ties to the lowest tick
+ *      (Eq. 2, Sec. III-D);
+ *   4. V* = V(p*) units trade at p*: buys fill in price priority from the top
+ *      tick, sells from the bottom tick, ascending agent index within a tick
+ *      (Sec. IV-C); inventory and cash of each agent are updated;
+ *   5. unfilled quantity rests for the next step (carried book) or is
+ *      discarded.
+ * All quantities are integers; results are bit-identical for any launch
+ * shape and any split of the steps over calls.
+ *
+ * Conventions for every function:
+ *  - Returns KS_OK (0) on success.  No function throws or aborts.
+ *  - Argument errors are reported before any GPU work is queued.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Device memory is owned by the caller: the library never allocates
+ *    device memory.  Host memory it needs (the handle) is freed by
+ *    ks_destroy.
+ *  - On KS_ERR_CUDA, ks_last_error() returns the CUDA error text of the
+ *    calling thread's most recent failure.
+ */
+#ifndef KINETICSIM_H
+#define KINETICSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ks_status {
+  KS_OK = 0,
+  KS_ERR_INVALID_ARG = 1,         /* bad pointer, size or parameter value           */
+  KS_ERR_WORKSPACE_TOO_SMALL = 2, /* ws_bytes below ks_workspace_size()             */
+  KS_ERR_CUDA = 3,                /* a CUDA runtime call failed (see ks_last_error) */
+  KS_ERR_UNSUPPORTED = 4,         /* outside the supported envelope (L, A, qty)     */
+  KS_ERR_DEVICE_FAULT = 5,        /* a kernel set the ensemble's device error word  */
+  KS_ERR_TIMEOUT = 6              /* ks_sync deadline passed before the GPU finished */
+} ks_status;
+
+/* Tie rule among ticks of equal maximal executable volume. */
+typedef enum ks_tie_rule {
+  KS_TIE_LOWEST_TICK = 0,   /* the paper's rule (Sec. III-D): lowest price index    */
+  KS_TIE_MIN_IMBALANCE = 1  /* smallest |D_cum - S_cum|, then lowest tick           */
+} ks_tie_rule;
+
+/* Supported envelope. */
+#define KS_MAX_TICKS 4096   /* L in [2, 4096]                                      */
+#define KS_MAX_AGENTS 16384 /* A in [1, 16384]                                     */
+#define KS_MAX_QTY 255      /* zi_qmax, rb_qmax in [1, 255]                        */
+#define KS_HISTORY 9        /* clearing-tick history kept per market               */
+
+/* Agent classes (stored in the order word, see below). */
+#define KS_CLASS_ZI 0   /* zero-intelligence: side 1/2, tick last +/- zi_offset      */
+#define KS_CLASS_MOM 1  /* momentum: side = sign of the mom_lookback-step return    */
+#define KS_CLASS_MR 2   /* mean reversion toward the market's fundamental tick      */
+
+/*
+ * Ensemble description.  Host arrays are copied by ks_create_ensemble.
+ *
+ * Agent rules (every draw is one word of the agent's Philox4x32-10 block for
+ * counter (step, agent, market, 0) under key (seed low 32, seed high 32);
+ * range(w, n) = floor(w * n / 2^32)):
+ *  - cancel: a working order is cancelled iff w0 < cancel_thresh_q32;
+ *  - ZI:  buy iff w1 < 2^31; tick = clamp(last + range(w2, 2*zi_offset+1)
+ *         - zi_offset, 0, L-1); qty = 1 + range(w3, zi_qmax);
+ *  - MOM: r = hist[0] - hist[mom_lookback]; buy if r > 0, sell if r < 0,
+ *         else the ZI side bit; tick = last +/- range(w2, mom_offset_max+1)
+ *         (buy above, sell below), clamped; qty = 1 + range(w3, rb_qmax);
+ *  - MR:  buy if last < fundamental, sell if above, else the side bit;
+ *         tick = last +/- range(w2, mr_offset_max+1); qty as MOM.
+ * Here `market` is the global index market_base + m.
+ * Agent class: percentile range(w0, 100) of block (0, agent, market, 1)
+ * against mix_pct; MLP membership: range(w1, 100) < mlp_pct of that block.
+ * Fundamental: L/4 + range(w0, L/2+1) of block (0, 0, market, 2).
+ */
+typedef struct ks_config {
+  uint32_t n_markets;          /* M >= 1                                          */
+  uint32_t market_base;        /* global index of market 0; market m draws with
+                                  market word market_base + m (shards of one
+                                  larger ensemble use disjoint ranges)            */
+  const int32_t* L;            /* host [M] ticks per market, or NULL -> L_all      */
+  const int32_t* A;            /* host [M] agents per market, or NULL -> A_all     */
+  int32_t L_all;
+  int32_t A_all;
+  uint64_t seed;
+  int32_t carry_book;          /* 0: unfilled orders discarded every step; 1: kept */
+  uint32_t cancel_thresh_q32;  /* per-step cancel probability * 2^32               */
+  uint32_t mix_pct[3];         /* percent ZI / MOM / MR, sum 100                   */
+  int32_t zi_offset;           /* >= 0                                             */
+  int32_t zi_qmax;             /* 1..KS_MAX_QTY                                    */
+  int32_t mom_lookback;        /* 1..8                                             */
+  int32_t mom_offset_max;      /* >= 0                                             */
+  int32_t mr_offset_max;       /* >= 0                                             */
+  int32_t rb_qmax;             /* 1..KS_MAX_QTY                                    */
+  uint32_t mlp_pct;            /* percent of agents driven by the MLP policy       */
+  const void* mlp_params;      /* device pointer to packed policy weights, or NULL */
+  int32_t tie_rule;            /* ks_tie_rule                                      */
+  uint32_t trace_markets;      /* markets 0..trace_markets-1 record a step trace   */
+  uint32_t trace_steps;        /* trace capacity in steps (absolute steps < this)  */
+} ks_config;
+
+typedef struct ks_ensemble ks_ensemble;
+
+/*
+ * Order word (one uint32 per agent):
+ *   bits 0-7   quantity of the working order (0 = no working order)
+ *   bit  8     side (0 buy, 1 sell)
+ *   bits 9-20  limit tick
+ *   bits 21-22 agent class (KS_CLASS_*)
+ *   bit  23    MLP-driven agent
+ */
+#define KS_ORDER_QTY(w) ((int32_t)((w) & 0xFFu))
+#define KS_ORDER_SIDE(w) ((int32_t)(((w) >> 8) & 1u))
+#define KS_ORDER_TICK(w) ((int32_t)(((w) >> 9) & 0xFFFu))
+#define KS_ORDER_CLASS(w) ((int32_t)(((w) >> 21) & 3u))
+#define KS_ORDER_MLP(w) ((int32_t)(((w) >> 23) & 1u))
+
+/*
+ * State view: caller-owned buffers, host or device (any mix; copies use
+ * unified addressing).  A NULL field is skipped.  Agent arrays are indexed by
+ * the global agent id: market m's agents are [off_m, off_m + A_m) with
+ * off_m = A_0 + ... + A_{m-1}; N = off_M.
+ */
+typedef struct ks_state_view {
+  uint32_t* order;       /* [N] order words                                     */
+  int32_t* inventory;    /* [N] shares bought minus sold                         */
+  int64_t* cash;         /* [N] sum of p* x (sold - bought), tick units           */
+  int32_t* last_tick;    /* [M] last clearing tick (initially L/2)               */
+  int32_t* history;      /* [M*KS_HISTORY] history[m*9 + j] = last tick j steps ago */
+  int32_t* fundamental;  /* [M]                                                 */
+  int32_t* trades;       /* [M] steps with V* > 0                                */
+  int32_t* last_volume;  /* [M] V* of the latest step                            */
+  int64_t* sum_price;    /* [M] sum of p* over trading steps                      */
+  int64_t* sum_volume;   /* [M] sum of V* over steps                             */
+  uint64_t* trace_hash;  /* [M] h <- mix64(h ^ (p*<<32 | V*) ^ step*0x9E3779B97F4A7C15),
+                            mix64 = SplitMix64 finaliser (Sec. III-F); p* = -1 when V* = 0 */
+  uint64_t* step;        /* [1] absolute step counter                            */
+  int32_t* trace;        /* [trace_markets*trace_steps*2] (p*, V*) per market and step */
+} ks_state_view;
+
+/* Launch shape of the persistent kernel; results never depend on it. */
+typedef struct ks_launch {
+  int32_t threads;            /* threads per CTA: 64, 128, 256, 512 or 1024      */
+  int32_t agents_per_thread;  /* 1, 2, 4, 8 or 16; threads*agents_per_thread >= A */
+  int32_t ctas_per_sm;        /* 0 = as many as fit                               */
+  int32_t aggregate;          /* 1 = warp-aggregate equal (side,tick) orders with
+                                 __match_any_sync before the shared atomic         */
+} ks_launch;
+
+/* Bytes of device workspace needed for `cfg`. */
+ks_status ks_workspace_size(const ks_config* cfg, size_t* bytes);
+
+/* Validates cfg, lays out the ensemble in `workspace` (device, caller-owned,
+ * 256-byte aligned, at least ks_workspace_size bytes, alive until
+ * ks_destroy) and queues the init kernel on `stream` (step counter 0, every
+ * market at price L/2 with empty books and zero accounts).  Returns a handle
+ * in *out.  Chooses a default launch shape (see ks_set_launch). */
+ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_bytes, void* stream,
+                             ks_ensemble** out);
+
+/* Queues steps [s, s + n_steps) of every market on `stream`, where s is the
+ * ensemble's step counter, then advances the counter on the device.  The
+ * counter lives in device memory, so a CUDA graph captured around this call
+ * continues the simulation on every replay.  Asynchronous; no allocation, no
+ * host synchronisation (capturable). */
+ks_status ks_step_n(ks_ensemble* e, uint32_t n_steps, void* stream);
+
+/* Copies the requested fields into `dst` after the work queued on `stream`,
+ * then synchronises `stream`. */
+ks_status ks_read_state(ks_ensemble* e, const ks_state_view* dst, void* stream);
+
+/* Overwrites the given fields from `src` (resume from a checkpoint made by
+ * ks_read_state).  Queued on `stream`, then synchronised. */
+ks_status ks_write_state(ks_ensemble* e, const ks_state_view* src, void* stream);
+
+/* Waits for `stream` with a host-side deadline (0 = no deadline), then checks
+ * the device error word: KS_ERR_TIMEOUT if the deadline passed (the GPU work
+ * keeps running), KS_ERR_DEVICE_FAULT if a kernel reported an error. */
+ks_status ks_sync(ks_ensemble* e, void* stream, uint32_t timeout_ms);
+
+/* Device error word (0 = none) after synchronising `stream`. */
+ks_status ks_error_word(ks_ensemble* e, void* stream, uint32_t* word);
+
+/* Sets / gets the persistent kernel's launch shape. */
+ks_status ks_set_launch(ks_ensemble* e, const ks_launch* l);
+ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l);
+
+/* Frees the host handle.  The workspace stays the caller's. */
+ks_status ks_destroy(ks_ensemble* e);
+
+const char* ks_status_string(ks_status s);
+const char* ks_last_error(void);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+uint32_t ks_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KINETICSIM_H */

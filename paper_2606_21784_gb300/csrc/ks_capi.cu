@@ -1,0 +1,509 @@
+// ks_capi.cu -- the C ABI of kineticsim.h: validation, workspace layout,
+// ensemble initialisation, persistent-kernel launches and state I/O.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "kineticsim.h"
+#include "ks_device.cuh"
+#include "ks_internal.h"
+#include "ks_plain.cuh"
+
+namespace ks {
+extern const PlainVariant kPlainNT64[5];
+extern const PlainVariant kPlainNT128[5];
+extern const PlainVariant kPlainNT256[5];
+extern const PlainVariant kPlainNT512[5];
+extern const PlainVariant kPlainNT1024[5];
+
+const PlainVariant* find_plain(int threads, int ak) {
+  const PlainVariant* tabs[5] = {kPlainNT64, kPlainNT128, kPlainNT256, kPlainNT512, kPlainNT1024};
+  for (auto* t : tabs)
+    for (int i = 0; i < 5; ++i)
+      if (t[i].threads == threads && t[i].ak == ak) return &t[i];
+  return nullptr;
+}
+
+size_t plain_smem_bytes(int threads, int ak, int Lmax) {
+  size_t o[6];
+  return plain_smem_layout(threads, ak, Lmax, o);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (the paper's Phase 1: empty book, opening price L/2).
+// ---------------------------------------------------------------------------
+__global__ void init_kernel(DevParams P) {
+  for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
+    const int L = P.Ls ? P.Ls[m] : P.L_all;
+    const int A = P.As ? P.As[m] : P.A_all;
+    const int64_t off = P.agent_off ? P.agent_off[m] : (int64_t)m * P.A_all;
+    for (int a = threadIdx.x; a < A; a += blockDim.x) {
+      const uint4 w = philox(0u, (uint32_t)a, P.market_base + m, 1u, P.key0, P.key1);
+      const uint32_t pct = __umulhi(w.x, 100u);
+      const uint32_t cls = pct < P.mix0 ? KS_CLASS_ZI : (pct < P.mix01 ? KS_CLASS_MOM : KS_CLASS_MR);
+      const bool mlp = __umulhi(w.y, 100u) < P.mlp_pct;
+      P.slot[off + a] = (cls << W_CLASS_SHIFT) | (mlp ? W_MLP : 0u);
+      P.inv[off + a] = 0;
+      P.cash[off + a] = 0;
+    }
+    if (threadIdx.x == 0) {
+      int32_t* mi = P.mi32 + (size_t)m * MI32_STRIDE;
+      mi[MI_LAST] = L / 2;
+      for (int j = 0; j < KS_HISTORY; ++j) mi[MI_HIST + j] = L / 2;
+      const uint4 w = philox(0u, 0u, P.market_base + m, 2u, P.key0, P.key1);
+      mi[MI_FUND] = L / 4 + (int)__umulhi(w.x, (uint32_t)(L / 2 + 1));
+      mi[MI_TRADES] = 0;
+      mi[MI_LASTV] = 0;
+      mi[13] = mi[14] = mi[15] = 0;
+      int64_t* m64 = P.mi64 + (size_t)m * MI64_STRIDE;
+      m64[0] = m64[1] = m64[2] = m64[3] = 0;
+    }
+  }
+}
+
+__global__ void step_bump_kernel(uint64_t* step, uint32_t n) { *step += n; }
+
+}  // namespace ks
+
+using namespace ks;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_last_error[512] = "";
+
+static ks_status cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return KS_ERR_CUDA;
+}
+#define KS_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static ks_status arg_fail(ks_status s, const char* msg) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Handle and workspace layout
+// ---------------------------------------------------------------------------
+struct ks_ensemble {
+  ks_config cfg;
+  uint32_t M;
+  int64_t N;
+  int Lmax, Amax;
+  bool uniform;
+  std::vector<int32_t> L, A;
+  std::vector<int64_t> off;
+  unsigned char* ws;
+  size_t ws_bytes;
+  DevParams dp;
+  ks_launch launch;
+  const PlainVariant* var;
+  int grid;
+  size_t smem;
+  int device;
+  int num_sms;
+};
+
+struct Layout {
+  size_t slot, inv, cash, mi32, mi64, aoff, Ls, As, trace, ctrl, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout make_layout(uint32_t M, int64_t N, bool uniform, uint32_t tm, uint32_t ts) {
+  Layout l;
+  size_t o = 0;
+  l.slot = o; o = align256(o + (size_t)N * 4);
+  l.inv = o; o = align256(o + (size_t)N * 4);
+  l.cash = o; o = align256(o + (size_t)N * 8);
+  l.mi32 = o; o = align256(o + (size_t)M * MI32_STRIDE * 4);
+  l.mi64 = o; o = align256(o + (size_t)M * MI64_STRIDE * 8);
+  l.aoff = o; o = align256(o + (uniform ? 0 : (size_t)(M + 1) * 8));
+  l.Ls = o; o = align256(o + (uniform ? 0 : (size_t)M * 4));
+  l.As = o; o = align256(o + (uniform ? 0 : (size_t)M * 4));
+  l.trace = o; o = align256(o + (size_t)tm * ts * 2 * 4);
+  l.ctrl = o; o = align256(o + 64);  // err (u32) at +0, step (u64) at +8, ticket (u32) at +16
+  l.total = o;
+  return l;
+}
+
+struct Sizes {
+  std::vector<int32_t> L, A;
+  std::vector<int64_t> off;
+  int Lmax = 0, Amax = 0;
+  bool uniform = true;
+  int64_t N = 0;
+};
+
+static ks_status validate(const ks_config* c, Sizes* sz) {
+  if (!c) return arg_fail(KS_ERR_INVALID_ARG, "config is NULL");
+  if (c->n_markets == 0) return arg_fail(KS_ERR_INVALID_ARG, "n_markets must be >= 1");
+  if (c->n_markets > (1u << 26)) return arg_fail(KS_ERR_UNSUPPORTED, "n_markets above 2^26");
+  if ((uint64_t)c->market_base + c->n_markets > 0xFFFFFFFFull)
+    return arg_fail(KS_ERR_INVALID_ARG, "market_base + n_markets above 2^32");
+  if (c->mix_pct[0] + c->mix_pct[1] + c->mix_pct[2] != 100u)
+    return arg_fail(KS_ERR_INVALID_ARG, "mix_pct must sum to 100");
+  if (c->zi_offset < 0 || c->zi_offset > KS_MAX_TICKS) return arg_fail(KS_ERR_INVALID_ARG, "zi_offset out of range");
+  if (c->mom_offset_max < 0 || c->mom_offset_max > KS_MAX_TICKS || c->mr_offset_max < 0 ||
+      c->mr_offset_max > KS_MAX_TICKS)
+    return arg_fail(KS_ERR_INVALID_ARG, "offset max out of range");
+  if (c->zi_qmax < 1 || c->rb_qmax < 1) return arg_fail(KS_ERR_INVALID_ARG, "qmax must be >= 1");
+  if (c->zi_qmax > KS_MAX_QTY || c->rb_qmax > KS_MAX_QTY) return arg_fail(KS_ERR_UNSUPPORTED, "qmax above 255");
+  if (c->mom_lookback < 1 || c->mom_lookback > KS_HISTORY - 1)
+    return arg_fail(KS_ERR_INVALID_ARG, "mom_lookback must be in [1, 8]");
+  if (c->tie_rule != KS_TIE_LOWEST_TICK && c->tie_rule != KS_TIE_MIN_IMBALANCE)
+    return arg_fail(KS_ERR_INVALID_ARG, "unknown tie_rule");
+  if (c->mlp_pct > 100u) return arg_fail(KS_ERR_INVALID_ARG, "mlp_pct above 100");
+  if (c->mlp_pct > 0u) return arg_fail(KS_ERR_UNSUPPORTED, "MLP-driven agents need the learned-policy build");
+  if (c->trace_markets > c->n_markets) return arg_fail(KS_ERR_INVALID_ARG, "trace_markets above n_markets");
+  if ((c->trace_markets == 0) != (c->trace_steps == 0) && c->trace_markets != 0)
+    return arg_fail(KS_ERR_INVALID_ARG, "trace_steps must be > 0 when tracing");
+  const uint32_t M = c->n_markets;
+  sz->L.resize(M);
+  sz->A.resize(M);
+  sz->off.resize(M + 1);
+  int64_t n = 0;
+  for (uint32_t m = 0; m < M; ++m) {
+    const int32_t L = c->L ? c->L[m] : c->L_all;
+    const int32_t A = c->A ? c->A[m] : c->A_all;
+    if (L < 2 || A < 0) return arg_fail(KS_ERR_INVALID_ARG, "L must be >= 2 and A >= 0");
+    if (L > KS_MAX_TICKS || A > KS_MAX_AGENTS) return arg_fail(KS_ERR_UNSUPPORTED, "L or A above the envelope");
+    sz->L[m] = L;
+    sz->A[m] = A;
+    sz->off[m] = n;
+    n += A;
+    sz->Lmax = std::max(sz->Lmax, (int)L);
+    sz->Amax = std::max(sz->Amax, (int)A);
+  }
+  sz->off[M] = n;
+  sz->N = n;
+  sz->uniform = true;
+  for (uint32_t m = 1; m < M; ++m)
+    if (sz->L[m] != sz->L[0] || sz->A[m] != sz->A[0]) sz->uniform = false;
+  return KS_OK;
+}
+
+static int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Default launch shape: with few markets, spread each market over many
+// threads; otherwise about 8 agents per thread.
+static ks_launch default_launch(int Amax, uint32_t M, int num_sms) {
+  ks_launch l;
+  memset(&l, 0, sizeof(l));
+  int nt, ak;
+  if ((int)M < 2 * num_sms) {
+    nt = std::min(1024, std::max(64, next_pow2(Amax)));
+  } else {
+    nt = std::min(1024, std::max(64, next_pow2((Amax + 7) / 8)));
+  }
+  ak = next_pow2(std::max(1, (Amax + nt - 1) / nt));
+  while (ak > 16) {
+    nt *= 2;
+    ak = next_pow2(std::max(1, (Amax + nt - 1) / nt));
+  }
+  l.threads = nt;
+  l.agents_per_thread = ak;
+  l.ctas_per_sm = 0;
+  l.aggregate = 0;
+  return l;
+}
+
+static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
+  const PlainVariant* v = find_plain(l->threads, l->agents_per_thread);
+  if (!v) return arg_fail(KS_ERR_INVALID_ARG, "no kernel for this (threads, agents_per_thread)");
+  if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
+    return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
+  if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
+  const size_t smem = plain_smem_bytes(l->threads, l->agents_per_thread, e->Lmax);
+  if (smem > 227 * 1024) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more than 227 KB shared memory");
+  const void* k = l->aggregate ? v->kernel_aggr : v->kernel_plain;
+  KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, l->threads, smem));
+  if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+  const int per_sm = l->ctas_per_sm > 0 ? std::min(occ, l->ctas_per_sm) : occ;
+  e->grid = (int)std::min<int64_t>((int64_t)e->M, (int64_t)per_sm * e->num_sms);
+  e->smem = smem;
+  e->var = v;
+  e->launch = *l;
+  return KS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Public API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+uint32_t ks_version(void) { return 0x000100u; }
+
+const char* ks_last_error(void) { return g_last_error; }
+
+const char* ks_status_string(ks_status s) {
+  switch (s) {
+    case KS_OK: return "ok";
+    case KS_ERR_INVALID_ARG: return "invalid argument";
+    case KS_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case KS_ERR_CUDA: return "CUDA error";
+    case KS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case KS_ERR_DEVICE_FAULT: return "device error word set";
+    case KS_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+ks_status ks_workspace_size(const ks_config* cfg, size_t* bytes) {
+  if (!bytes) return arg_fail(KS_ERR_INVALID_ARG, "bytes is NULL");
+  Sizes sz;
+  ks_status s = validate(cfg, &sz);
+  if (s != KS_OK) return s;
+  *bytes = make_layout(cfg->n_markets, sz.N, sz.uniform, cfg->trace_markets, cfg->trace_steps).total;
+  return KS_OK;
+}
+
+ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_bytes, void* stream,
+                             ks_ensemble** out) {
+  if (!out) return arg_fail(KS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  Sizes sz;
+  ks_status s = validate(cfg, &sz);
+  if (s != KS_OK) return s;
+  if (!workspace) return arg_fail(KS_ERR_INVALID_ARG, "workspace is NULL");
+  if (((uintptr_t)workspace & 255u) != 0) return arg_fail(KS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  const Layout lay = make_layout(cfg->n_markets, sz.N, sz.uniform, cfg->trace_markets, cfg->trace_steps);
+  if (ws_bytes < lay.total) return arg_fail(KS_ERR_WORKSPACE_TOO_SMALL, "workspace smaller than ks_workspace_size");
+  cudaStream_t st = (cudaStream_t)stream;
+
+  ks_ensemble* e = new (std::nothrow) ks_ensemble();
+  if (!e) return arg_fail(KS_ERR_INVALID_ARG, "out of host memory");
+  e->cfg = *cfg;
+  e->cfg.L = nullptr;
+  e->cfg.A = nullptr;
+  e->M = cfg->n_markets;
+  e->N = sz.N;
+  e->Lmax = sz.Lmax;
+  e->Amax = sz.Amax;
+  e->uniform = sz.uniform;
+  e->L = sz.L;
+  e->A = sz.A;
+  e->off = sz.off;
+  e->ws = (unsigned char*)workspace;
+  e->ws_bytes = ws_bytes;
+  cudaError_t ce = cudaGetDevice(&e->device);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+  if (ce != cudaSuccess) {
+    delete e;
+    return cuda_fail(ce, "device query");
+  }
+
+  DevParams& p = e->dp;
+  memset(&p, 0, sizeof(p));
+  p.M = e->M;
+  p.market_base = cfg->market_base;
+  p.L_all = sz.L[0];
+  p.A_all = sz.A[0];
+  p.key0 = (uint32_t)(cfg->seed & 0xffffffffu);
+  p.key1 = (uint32_t)(cfg->seed >> 32);
+  p.carry = cfg->carry_book ? 1 : 0;
+  p.cancel_thr = cfg->cancel_thresh_q32;
+  p.mix0 = cfg->mix_pct[0];
+  p.mix01 = cfg->mix_pct[0] + cfg->mix_pct[1];
+  p.zi_off = cfg->zi_offset;
+  p.zi_qmax = cfg->zi_qmax;
+  p.mom_lb = cfg->mom_lookback;
+  p.mom_omax = cfg->mom_offset_max;
+  p.mr_omax = cfg->mr_offset_max;
+  p.rb_qmax = cfg->rb_qmax;
+  p.mlp_pct = cfg->mlp_pct;
+  p.tie_rule = cfg->tie_rule;
+  p.trace_markets = cfg->trace_markets;
+  p.trace_steps = cfg->trace_steps;
+  p.Lmax = sz.Lmax;
+  unsigned char* w = e->ws;
+  p.slot = (uint32_t*)(w + lay.slot);
+  p.inv = (int32_t*)(w + lay.inv);
+  p.cash = (int64_t*)(w + lay.cash);
+  p.mi32 = (int32_t*)(w + lay.mi32);
+  p.mi64 = (int64_t*)(w + lay.mi64);
+  p.agent_off = sz.uniform ? nullptr : (const int64_t*)(w + lay.aoff);
+  p.Ls = sz.uniform ? nullptr : (const int32_t*)(w + lay.Ls);
+  p.As = sz.uniform ? nullptr : (const int32_t*)(w + lay.As);
+  p.trace = (int32_t*)(w + lay.trace);
+  p.err = (uint32_t*)(w + lay.ctrl);
+  p.step = (const uint64_t*)(w + lay.ctrl + 8);
+
+  ks_launch l = default_launch(e->Amax, e->M, e->num_sms);
+  s = apply_launch(e, &l);
+  if (s != KS_OK) {
+    delete e;
+    return s;
+  }
+
+#define KS_CUDA_E(call)                     \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) {                \
+      delete e;                             \
+      return cuda_fail(e_, #call);          \
+    }                                       \
+  } while (0)
+  if (!sz.uniform) {
+    KS_CUDA_E(cudaMemcpyAsync(w + lay.aoff, sz.off.data(), (size_t)(e->M + 1) * 8, cudaMemcpyHostToDevice, st));
+    KS_CUDA_E(cudaMemcpyAsync(w + lay.Ls, sz.L.data(), (size_t)e->M * 4, cudaMemcpyHostToDevice, st));
+    KS_CUDA_E(cudaMemcpyAsync(w + lay.As, sz.A.data(), (size_t)e->M * 4, cudaMemcpyHostToDevice, st));
+  }
+  KS_CUDA_E(cudaMemsetAsync(w + lay.ctrl, 0, 64, st));
+  if (lay.ctrl > lay.trace) KS_CUDA_E(cudaMemsetAsync(w + lay.trace, 0, lay.ctrl - lay.trace, st));
+  const int grid = (int)std::min<uint32_t>(e->M, 8u * (uint32_t)e->num_sms);
+  init_kernel<<<grid, 256, 0, st>>>(p);
+  KS_CUDA_E(cudaGetLastError());
+  // host copies above read pageable vectors owned by the handle; make sure they are done
+  KS_CUDA_E(cudaStreamSynchronize(st));
+#undef KS_CUDA_E
+  *out = e;
+  return KS_OK;
+}
+
+ks_status ks_step_n(ks_ensemble* e, uint32_t n_steps, void* stream) {
+  if (!e) return arg_fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
+  if (n_steps == 0) return KS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  KS_CUDA(e->var->launch(e->dp, n_steps, e->grid, e->smem, st, e->launch.aggregate));
+  step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, n_steps);
+  KS_CUDA(cudaGetLastError());
+  return KS_OK;
+}
+
+static ks_status copy_market_field(void* dst, const void* src_base, size_t src_pitch, size_t width, uint32_t M,
+                                   cudaStream_t st, bool to_view) {
+  if (to_view) {
+    KS_CUDA(cudaMemcpy2DAsync(dst, width, src_base, src_pitch, width, M, cudaMemcpyDefault, st));
+  } else {
+    KS_CUDA(cudaMemcpy2DAsync((void*)src_base, src_pitch, dst, width, width, M, cudaMemcpyDefault, st));
+  }
+  return KS_OK;
+}
+
+static ks_status state_io(ks_ensemble* e, const ks_state_view* v, cudaStream_t st, bool to_view) {
+  const DevParams& p = e->dp;
+  const size_t N = (size_t)e->N;
+  auto lin = [&](void* view, void* dev, size_t bytes) -> ks_status {
+    if (!view || bytes == 0) return KS_OK;
+    KS_CUDA(cudaMemcpyAsync(to_view ? view : dev, to_view ? dev : view, bytes, cudaMemcpyDefault, st));
+    return KS_OK;
+  };
+  ks_status s;
+  if ((s = lin(v->order, p.slot, N * 4)) != KS_OK) return s;
+  if ((s = lin(v->inventory, p.inv, N * 4)) != KS_OK) return s;
+  if ((s = lin(v->cash, p.cash, N * 8)) != KS_OK) return s;
+  const size_t p32 = MI32_STRIDE * 4, p64 = MI64_STRIDE * 8;
+  struct F {
+    void* view;
+    const void* dev;
+    size_t pitch, width;
+  } fs[] = {
+      {v->last_tick, p.mi32 + MI_LAST, p32, 4},
+      {v->history, p.mi32 + MI_HIST, p32, 4 * KS_HISTORY},
+      {v->fundamental, p.mi32 + MI_FUND, p32, 4},
+      {v->trades, p.mi32 + MI_TRADES, p32, 4},
+      {v->last_volume, p.mi32 + MI_LASTV, p32, 4},
+      {v->sum_price, p.mi64 + MI_SUMP, p64, 8},
+      {v->sum_volume, p.mi64 + MI_SUMV, p64, 8},
+      {v->trace_hash, p.mi64 + MI_HASH, p64, 8},
+  };
+  for (auto& f : fs)
+    if (f.view && (s = copy_market_field(f.view, f.dev, f.pitch, f.width, e->M, st, to_view)) != KS_OK) return s;
+  if ((s = lin(v->step, (void*)p.step, 8)) != KS_OK) return s;
+  if ((s = lin(v->trace, p.trace, (size_t)p.trace_markets * p.trace_steps * 2 * 4)) != KS_OK) return s;
+  KS_CUDA(cudaStreamSynchronize(st));
+  return KS_OK;
+}
+
+ks_status ks_read_state(ks_ensemble* e, const ks_state_view* dst, void* stream) {
+  if (!e || !dst) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  return state_io(e, dst, (cudaStream_t)stream, true);
+}
+
+ks_status ks_write_state(ks_ensemble* e, const ks_state_view* src, void* stream) {
+  if (!e || !src) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  return state_io(e, src, (cudaStream_t)stream, false);
+}
+
+ks_status ks_error_word(ks_ensemble* e, void* stream, uint32_t* word) {
+  if (!e || !word) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  KS_CUDA(cudaMemcpyAsync(word, e->dp.err, 4, cudaMemcpyDeviceToHost, st));
+  KS_CUDA(cudaStreamSynchronize(st));
+  return KS_OK;
+}
+
+ks_status ks_sync(ks_ensemble* e, void* stream, uint32_t timeout_ms) {
+  if (!e) return arg_fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  KS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t ce = cudaEventRecord(ev, st);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(ce, "cudaEventRecord");
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    ce = cudaEventQuery(ev);
+    if (ce == cudaSuccess) break;
+    if (ce != cudaErrorNotReady) {
+      cudaEventDestroy(ev);
+      return cuda_fail(ce, "cudaEventQuery");
+    }
+    if (timeout_ms) {
+      const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+      if (ms.count() >= (long long)timeout_ms) {
+        cudaEventDestroy(ev);
+        return arg_fail(KS_ERR_TIMEOUT, "ks_sync deadline passed before the stream finished");
+      }
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  uint32_t word = 0;
+  ks_status s = ks_error_word(e, stream, &word);
+  if (s != KS_OK) return s;
+  if (word) {
+    snprintf(g_last_error, sizeof(g_last_error), "device error word 0x%x", word);
+    return KS_ERR_DEVICE_FAULT;
+  }
+  return KS_OK;
+}
+
+ks_status ks_set_launch(ks_ensemble* e, const ks_launch* l) {
+  if (!e || !l) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  return apply_launch(e, l);
+}
+
+ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l) {
+  if (!e || !l) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  *l = e->launch;
+  return KS_OK;
+}
+
+ks_status ks_destroy(ks_ensemble* e) {
+  delete e;
+  return KS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// ks_internal.h -- structures shared by the host library and its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kineticsim.h"
+
+namespace ks {
+
+// Per-market scalar block layouts in the workspace.
+constexpr int MI32_STRIDE = 16;  // last, hist[9], fund, trades, last_v, pad x3
+constexpr int MI_LAST = 0;
+constexpr int MI_HIST = 1;
+constexpr int MI_FUND = 10;
+constexpr int MI_TRADES = 11;
+constexpr int MI_LASTV = 12;
+constexpr int MI64_STRIDE = 4;  // sum_p, sum_v, hash, pad
+constexpr int MI_SUMP = 0;
+constexpr int MI_SUMV = 1;
+constexpr int MI_HASH = 2;
+
+// Error word bits.
+constexpr uint32_t ERR_SHAPE = 1u;      // market larger than the launch shape
+constexpr uint32_t ERR_TICK = 2u;       // tick index outside [0, L)
+constexpr uint32_t ERR_RANGE = 4u;      // clearing volume outside the packed range
+constexpr uint32_t ERR_MLP_WAIT = 8u;   // bounded tensor-core wait gave up
+
+// Everything a kernel needs, passed by value.
+struct DevParams {
+  uint32_t M;
+  uint32_t market_base;  // global index of market 0 (Philox counter word)
+  int32_t L_all, A_all;
+  uint32_t key0, key1;
+  int32_t carry;
+  uint32_t cancel_thr;
+  uint32_t mix0, mix01;  // class percentile thresholds: ZI < mix0 <= MOM < mix01 <= MR
+  int32_t zi_off, zi_qmax, mom_lb, mom_omax, mr_omax, rb_qmax;
+  uint32_t mlp_pct;
+  int32_t tie_rule;
+  uint32_t trace_markets, trace_steps;
+  int32_t Lmax;  // largest L in the ensemble (shared-memory sizing)
+
+  uint32_t* slot;
+  int32_t* inv;
+  int64_t* cash;
+  int32_t* mi32;  // [M][MI32_STRIDE]
+  int64_t* mi64;  // [M][MI64_STRIDE]
+  const int64_t* agent_off;  // [M+1] or nullptr (uniform: m*A_all)
+  const int32_t* Ls;         // [M] or nullptr
+  const int32_t* As;         // [M] or nullptr
+  int32_t* trace;            // [trace_markets][trace_steps][2]
+  uint32_t* err;
+  const uint64_t* step;      // absolute step counter (device)
+};
+
+// A persistent launch of the plain kernel template (threads, agents/thread).
+using PlainLaunchFn = cudaError_t (*)(const DevParams& p, uint32_t n_steps, int grid, size_t smem,
+                                      cudaStream_t st, int aggregate);
+struct PlainVariant {
+  int threads;
+  int ak;
+  PlainLaunchFn launch;
+  const void* kernel_plain;  // for occupancy queries
+  const void* kernel_aggr;
+};
+
+// Registry filled by the instantiation translation units.
+const PlainVariant* plain_variants(int* count);
+
+// Shared memory bytes of the plain kernel for a launch shape and max L.
+size_t plain_smem_bytes(int threads, int ak, int Lmax);
+
+}  // namespace ks

@@ -1,0 +1,347 @@
+"""ctypes binding of ``libkineticsim.so`` (the C ABI of ``include/kineticsim.h``).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of the library.  PyTorch provides device memory and streams.  There is
+no fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KS_OK = 0
+KS_ERR_INVALID_ARG = 1
+KS_ERR_WORKSPACE_TOO_SMALL = 2
+KS_ERR_CUDA = 3
+KS_ERR_UNSUPPORTED = 4
+KS_ERR_DEVICE_FAULT = 5
+KS_ERR_TIMEOUT = 6
+KS_HISTORY = 9
+
+_STATUS = {0: "KS_OK", 1: "KS_ERR_INVALID_ARG", 2: "KS_ERR_WORKSPACE_TOO_SMALL", 3: "KS_ERR_CUDA",
+           4: "KS_ERR_UNSUPPORTED", 5: "KS_ERR_DEVICE_FAULT", 6: "KS_ERR_TIMEOUT"}
+
+# every entry point declared in include/kineticsim.h
+EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_state", "ks_write_state",
+           "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
+           "ks_last_error", "ks_version")
+
+
+class KsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)} {detail}".strip())
+
+
+class ks_config(ctypes.Structure):
+    _fields_ = [
+        ("n_markets", ctypes.c_uint32),
+        ("market_base", ctypes.c_uint32),
+        ("L", ctypes.POINTER(ctypes.c_int32)),
+        ("A", ctypes.POINTER(ctypes.c_int32)),
+        ("L_all", ctypes.c_int32),
+        ("A_all", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("carry_book", ctypes.c_int32),
+        ("cancel_thresh_q32", ctypes.c_uint32),
+        ("mix_pct", ctypes.c_uint32 * 3),
+        ("zi_offset", ctypes.c_int32),
+        ("zi_qmax", ctypes.c_int32),
+        ("mom_lookback", ctypes.c_int32),
+        ("mom_offset_max", ctypes.c_int32),
+        ("mr_offset_max", ctypes.c_int32),
+        ("rb_qmax", ctypes.c_int32),
+        ("mlp_pct", ctypes.c_uint32),
+        ("mlp_params", ctypes.c_void_p),
+        ("tie_rule", ctypes.c_int32),
+        ("trace_markets", ctypes.c_uint32),
+        ("trace_steps", ctypes.c_uint32),
+    ]
+
+
+class ks_state_view(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "order", "inventory", "cash", "last_tick", "history", "fundamental", "trades", "last_volume",
+        "sum_price", "sum_volume", "trace_hash", "step", "trace")]
+
+
+class ks_launch(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("agents_per_thread", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("aggregate", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if needed).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    sig = {
+        "ks_workspace_size": ([P(ks_config), P(ctypes.c_size_t)], ctypes.c_int),
+        "ks_create_ensemble": ([P(ks_config), vp, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+        "ks_step_n": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
+        "ks_read_state": ([vp, P(ks_state_view), vp], ctypes.c_int),
+        "ks_write_state": ([vp, P(ks_state_view), vp], ctypes.c_int),
+        "ks_sync": ([vp, vp, ctypes.c_uint32], ctypes.c_int),
+        "ks_error_word": ([vp, vp, P(ctypes.c_uint32)], ctypes.c_int),
+        "ks_set_launch": ([vp, P(ks_launch)], ctypes.c_int),
+        "ks_get_launch": ([vp, P(ks_launch)], ctypes.c_int),
+        "ks_destroy": ([vp], ctypes.c_int),
+        "ks_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "ks_last_error": ([], ctypes.c_char_p),
+        "ks_version": ([], ctypes.c_uint32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != KS_OK:
+        detail = load().ks_last_error()
+        raise KsError(rc, where, detail.decode() if detail else "")
+
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def make_config(w: dict, trace_markets: int = 0, trace_steps: int = 0, L=None, A=None):
+    """ks_config from a workload dict (see ``workloads``).  Returns (config, keepalive)."""
+    from . import workloads
+    p = w["params"]
+    c = ks_config()
+    M = int(w["M"])
+    c.n_markets = M
+    c.market_base = int(w.get("market_base", 0))
+    keep = []
+    if L is None or A is None:
+        L, A = workloads.sizes(w)
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    A = np.ascontiguousarray(A, dtype=np.int32)
+    uniform = bool(np.all(L == L[0]) and np.all(A == A[0]))
+    if uniform:
+        c.L_all, c.A_all = int(L[0]), int(A[0])
+    else:
+        c.L = L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        c.A = A.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        keep += [L, A]
+    c.seed = int(p["seed"])
+    c.carry_book = int(p["carry_book"])
+    c.cancel_thresh_q32 = int(p["cancel_thresh_q32"])
+    for i in range(3):
+        c.mix_pct[i] = int(p["mix_pct"][i])
+    c.zi_offset = int(p["zi_offset"])
+    c.zi_qmax = int(p["zi_qmax"])
+    c.mom_lookback = int(p["mom_lookback"])
+    c.mom_offset_max = int(p["mom_offset_max"])
+    c.mr_offset_max = int(p["mr_offset_max"])
+    c.rb_qmax = int(p["rb_qmax"])
+    c.mlp_pct = int(p.get("mlp_pct", 0))
+    c.mlp_params = None
+    c.tie_rule = int(p.get("tie_rule", 0))
+    c.trace_markets = int(trace_markets)
+    c.trace_steps = int(trace_steps)
+    return c, (keep, L, A)
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers with the C names
+# ---------------------------------------------------------------------------
+def ks_workspace_size(cfg: ks_config) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().ks_workspace_size(ctypes.byref(cfg), ctypes.byref(n)), "ks_workspace_size")
+    return int(n.value)
+
+
+def ks_create_ensemble(cfg: ks_config, workspace_ptr: int, ws_bytes: int, stream=None) -> int:
+    h = ctypes.c_void_p(0)
+    _check(load().ks_create_ensemble(ctypes.byref(cfg), workspace_ptr, ws_bytes, _stream_ptr(stream),
+                                     ctypes.byref(h)), "ks_create_ensemble")
+    return h.value
+
+
+def ks_step_n(h: int, n_steps: int, stream=None):
+    _check(load().ks_step_n(h, int(n_steps), _stream_ptr(stream)), "ks_step_n")
+
+
+def ks_read_state(h: int, view: ks_state_view, stream=None):
+    _check(load().ks_read_state(h, ctypes.byref(view), _stream_ptr(stream)), "ks_read_state")
+
+
+def ks_write_state(h: int, view: ks_state_view, stream=None):
+    _check(load().ks_write_state(h, ctypes.byref(view), _stream_ptr(stream)), "ks_write_state")
+
+
+def ks_sync(h: int, stream=None, timeout_ms: int = 0) -> int:
+    """Returns the status (KS_OK, KS_ERR_TIMEOUT or KS_ERR_DEVICE_FAULT); raises on other errors."""
+    rc = load().ks_sync(h, _stream_ptr(stream), int(timeout_ms))
+    if rc not in (KS_OK, KS_ERR_TIMEOUT, KS_ERR_DEVICE_FAULT):
+        _check(rc, "ks_sync")
+    return rc
+
+
+def ks_error_word(h: int, stream=None) -> int:
+    w = ctypes.c_uint32(0)
+    _check(load().ks_error_word(h, _stream_ptr(stream), ctypes.byref(w)), "ks_error_word")
+    return int(w.value)
+
+
+def ks_set_launch(h: int, threads: int, agents_per_thread: int, ctas_per_sm: int = 0, aggregate: int = 0):
+    l = ks_launch(threads, agents_per_thread, ctas_per_sm, aggregate)
+    _check(load().ks_set_launch(h, ctypes.byref(l)), "ks_set_launch")
+
+
+def ks_get_launch(h: int) -> dict:
+    l = ks_launch()
+    _check(load().ks_get_launch(h, ctypes.byref(l)), "ks_get_launch")
+    return dict(threads=l.threads, agents_per_thread=l.agents_per_thread, ctas_per_sm=l.ctas_per_sm,
+                aggregate=l.aggregate)
+
+
+def ks_destroy(h: int):
+    _check(load().ks_destroy(h), "ks_destroy")
+
+
+# ---------------------------------------------------------------------------
+# Ensemble: workspace owned by a torch tensor
+# ---------------------------------------------------------------------------
+STATE_FIELDS = {
+    # name: (dtype, per) with per in {"agent", "market", "hist", "one", "trace"}
+    "order": (np.uint32, "agent"),
+    "inventory": (np.int32, "agent"),
+    "cash": (np.int64, "agent"),
+    "last_tick": (np.int32, "market"),
+    "history": (np.int32, "hist"),
+    "fundamental": (np.int32, "market"),
+    "trades": (np.int32, "market"),
+    "last_volume": (np.int32, "market"),
+    "sum_price": (np.int64, "market"),
+    "sum_volume": (np.int64, "market"),
+    "trace_hash": (np.uint64, "market"),
+    "step": (np.uint64, "one"),
+    "trace": (np.int32, "trace"),
+}
+
+_TORCH_DT = {np.uint32: "int32", np.int32: "int32", np.int64: "int64", np.uint64: "int64"}
+
+
+class Ensemble:
+    """One ensemble on the current CUDA device.
+
+    ``workload``: a dict from ``workloads.workload`` (M, L, A, params).  The
+    device workspace is a torch uint8 tensor held by this object.
+    """
+
+    def __init__(self, workload: dict, trace_markets: int = 0, trace_steps: int = 0, stream=None, L=None, A=None):
+        import torch
+        self.workload = workload
+        self.cfg, (self._keep, self.L, self.A) = make_config(workload, trace_markets, trace_steps, L, A)
+        self.M = int(workload["M"])
+        self.N = int(self.A.astype(np.int64).sum())
+        self.offsets = np.concatenate([[0], np.cumsum(self.A.astype(np.int64))])
+        self.trace_markets = int(trace_markets)
+        self.trace_steps = int(trace_steps)
+        self.ws_bytes = ks_workspace_size(self.cfg)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.handle = ks_create_ensemble(self.cfg, self.workspace.data_ptr(), self.ws_bytes, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ks_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int, stream=None):
+        ks_step_n(self.handle, n, stream)
+
+    def set_launch(self, threads, agents_per_thread, ctas_per_sm=0, aggregate=0):
+        ks_set_launch(self.handle, threads, agents_per_thread, ctas_per_sm, aggregate)
+
+    def get_launch(self):
+        return ks_get_launch(self.handle)
+
+    def sync(self, timeout_ms: int = 0, stream=None) -> int:
+        return ks_sync(self.handle, stream, timeout_ms)
+
+    def _shape(self, per):
+        return {"agent": (self.N,), "market": (self.M,), "hist": (self.M, KS_HISTORY), "one": (1,),
+                "trace": (self.trace_markets, self.trace_steps, 2)}[per]
+
+    def alloc_view(self, fields=None, device: bool = False, pinned: bool = False):
+        """Allocate torch buffers for ``fields`` and a view pointing at them."""
+        import torch
+        fields = list(STATE_FIELDS) if fields is None else list(fields)
+        bufs = {}
+        v = ks_state_view()
+        for f in fields:
+            dt, per = STATE_FIELDS[f]
+            shape = self._shape(per)
+            t = torch.empty(shape, dtype=getattr(torch, _TORCH_DT[dt]),
+                            device="cuda" if device else "cpu", pin_memory=(pinned and not device))
+            bufs[f] = t
+            setattr(v, f, t.data_ptr() if t.numel() else None)
+        return v, bufs
+
+    def read_state(self, fields=None, stream=None) -> dict:
+        """Copy the state to host numpy arrays."""
+        v, bufs = self.alloc_view(fields)
+        ks_read_state(self.handle, v, stream)
+        out = {}
+        for f, t in bufs.items():
+            dt = STATE_FIELDS[f][0]
+            out[f] = t.numpy().view(dt).copy()
+        return out
+
+    def write_state(self, state: dict, stream=None):
+        import torch
+        v = ks_state_view()
+        keep = []
+        for f, arr in state.items():
+            dt, per = STATE_FIELDS[f]
+            a = np.ascontiguousarray(arr).view(dt).reshape(self._shape(per))
+            t = torch.from_numpy(a.view(np.int64 if a.itemsize == 8 else np.int32).copy())
+            keep.append(t)
+            setattr(v, f, t.data_ptr() if t.numel() else None)
+        ks_write_state(self.handle, v, stream)
+        del keep
+
+    def market_slice(self, m: int) -> slice:
+        return slice(int(self.offsets[m]), int(self.offsets[m + 1]))
+
+
+def unpack_orders(words: np.ndarray) -> dict:
+    """Split order words into fields (layout documented in kineticsim.h)."""
+    w = words.astype(np.uint32)
+    return dict(qty=(w & 0xFF).astype(np.int32), side=((w >> 8) & 1).astype(np.int32),
+                tick=((w >> 9) & 0xFFF).astype(np.int32), atype=((w >> 21) & 3).astype(np.int32),
+                mlp=((w >> 23) & 1).astype(np.int32))

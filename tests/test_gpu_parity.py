@@ -1,0 +1,152 @@
+"""GPU <-> oracle parity of the persistent kernel, bit-exact, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2606_21784_gb300 import kineticsim as ks
+from paper_2606_21784_gb300 import workloads as wl
+
+from helpers import compare_market, oracle_markets
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_gpu(w, steps, trace_markets=0, launch=None, chunks=None, L=None, A=None):
+    import torch
+    ens = ks.Ensemble(w, trace_markets=trace_markets, trace_steps=steps if trace_markets else 0, L=L, A=A)
+    if launch:
+        ens.set_launch(**launch)
+    for c in (chunks or [steps]):
+        ens.step(c)
+    assert ens.sync(timeout_ms=600_000) == ks.KS_OK
+    torch.cuda.synchronize()
+    return ens, ens.read_state()
+
+
+def test_plain_zi_every_market_every_step():
+    """64 markets, L=256, A=256, 1000 steps, discard mode: every market and step."""
+    w = wl.workload("plain_zi_64")
+    ens, gs = _run_gpu(w, w["S"], trace_markets=w["M"])
+    L, A = ens.L, ens.A
+    ref = oracle_markets(w["params"], range(w["M"]), L, A, 0, w["S"])
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
+    assert int(gs["step"][0]) == w["S"]
+
+
+def test_plain_mix_reduced_every_market():
+    """Carried book, 60/20/20 agent mix, L=1024, A=4096, 24 markets x 150 steps."""
+    w = wl.workload("plain_mix_8192", M=24)
+    steps = 150
+    ens, gs = _run_gpu(w, steps, trace_markets=w["M"])
+    ref = oracle_markets(w["params"], range(w["M"]), ens.L, ens.A, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
+
+
+@pytest.mark.parametrize("launch", [
+    dict(threads=256, agents_per_thread=16),
+    dict(threads=512, agents_per_thread=8),
+    dict(threads=1024, agents_per_thread=4),
+    dict(threads=512, agents_per_thread=8, aggregate=1),
+    dict(threads=256, agents_per_thread=16, ctas_per_sm=1, aggregate=1),
+])
+def test_launch_shape_invariance(launch):
+    """Any launch shape gives the same state (races in aggregation or allocation would differ)."""
+    w = wl.workload("plain_mix_8192", M=40)
+    steps = 60
+    ens, gs = _run_gpu(w, steps, trace_markets=4, launch=launch)
+    ref = oracle_markets(w["params"], range(w["M"]), ens.L, ens.A, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp if m < 4 else None, tv if m < 4 else None)
+
+
+def test_split_calls_equal_one_call():
+    w = wl.workload("plain_mix_8192", M=16)
+    _, a = _run_gpu(w, 90, trace_markets=16)
+    _, b = _run_gpu(w, 90, trace_markets=16, chunks=[1, 29, 60])
+    for f in a:
+        assert np.array_equal(a[f], b[f]), f
+
+
+def test_checkpoint_resume():
+    """read_state -> new ensemble -> write_state -> continue equals an uninterrupted run."""
+    import torch
+    w = wl.workload("plain_mix_8192", M=12)
+    _, full = _run_gpu(w, 80)
+    ens1, mid = _run_gpu(w, 35)
+    ens2 = ks.Ensemble(w)
+    ens2.write_state({k: v for k, v in mid.items() if k != "trace"})
+    ens2.step(45)
+    torch.cuda.synchronize()
+    res = ens2.read_state()
+    for f in full:
+        if f != "trace":
+            assert np.array_equal(full[f], res[f]), f
+
+
+def test_edge_shapes_ragged_and_tiny():
+    """Ragged agent counts, non-power-of-two grids, L=2, A=1 and A=0 markets in one ensemble."""
+    Ls = np.array([2, 3, 100, 1000, 130, 64, 2048, 7, 256, 4096], np.int32)
+    As = np.array([1, 5, 77, 999, 0, 3000, 513, 1, 16384, 700], np.int32)
+    w = wl.workload("plain_mix_8192", M=len(Ls))
+    steps = 40
+    ens, gs = _run_gpu(w, steps, trace_markets=len(Ls), L=Ls, A=As)
+    ref = oracle_markets(w["params"], range(len(Ls)), Ls, As, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
+
+
+def test_tie_rule_min_imbalance():
+    w = wl.workload("plain_zi_64", M=16, tie_rule=1)
+    ens, gs = _run_gpu(w, 200, trace_markets=16)
+    ref = oracle_markets(w["params"], range(16), ens.L, ens.A, 0, 200)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
+
+
+def test_graph_capture_replays_continue():
+    """A CUDA graph captured around ks_step_n continues the simulation on each replay."""
+    import torch
+    w = wl.workload("plain_mix_8192", M=8)
+    ens = ks.Ensemble(w)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ens.step(25, stream=torch.cuda.current_stream())
+    # capture does not execute: step counter still 0
+    torch.cuda.synchronize()
+    assert int(ens.read_state(["step"])["step"][0]) == 0
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    got = ens.read_state()
+    _, ref = _run_gpu(w, 75)
+    for f in ref:
+        if f != "trace":
+            assert np.array_equal(got[f], ref[f]), f
+
+
+def test_full_size_plain_mix_sampled_markets():
+    """8192 markets, L=1024, A=4096, 2000 steps in the bench's launch shape; sampled markets vs oracle."""
+    w = wl.workload("plain_mix_8192")
+    ens, gs = _run_gpu(w, w["S"])
+    rng = np.random.default_rng(2)
+    sample = sorted(set([0, w["M"] - 1] + list(rng.integers(0, w["M"], 2))))
+    ref = oracle_markets(w["params"], sample, ens.L, ens.A, 0, w["S"])
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk)
+    # ensemble-wide properties that hold at any size
+    assert int(gs["inventory"].astype(np.int64).sum()) == 0
+    assert int(gs["cash"].sum()) == 0
+    assert np.all(gs["trades"] <= w["S"])
+
+
+def test_error_word_clear_and_sync_deadline():
+    import torch
+    w = wl.workload("plain_mix_8192", M=4)
+    ens = ks.Ensemble(w)
+    ens.step(5)
+    assert ens.sync(timeout_ms=60_000) == ks.KS_OK
+    assert ks.ks_error_word(ens.handle) == 0
+    torch.cuda.synchronize()
