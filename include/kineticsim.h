@@ -164,7 +164,35 @@ typedef struct ks_launch {
   int32_t ctas_per_sm;        /* 0 = as many as fit                               */
   int32_t aggregate;          /* 1 = warp-aggregate equal (side,tick) orders with
                                  __match_any_sync before the shared atomic         */
+  int32_t reg_cap;            /* register cap class: 0 compiler's choice, 1 about 85,
+                                 2 at most 64 registers per thread (aggregate = 0) */
 } ks_launch;
+
+/*
+ * Batched plans for uneven ensembles.  Each market belongs to the first
+ * bucket (in plan order) with L <= L_max and A <= A_max.  A bucket's markets
+ * run on groups of group_threads threads holding agents_per_thread agents
+ * each; several groups share one CTA of cta_threads threads when they fit
+ * (markets per CTA = min(cta_threads / group_threads, shared-memory fit)).
+ * Work items (the markets one CTA runs together) are taken longest first
+ * from a device ticket counter by the single persistent launch.
+ */
+typedef struct ks_bucket {
+  int32_t L_max;
+  int32_t A_max;
+  int32_t group_threads;      /* a (group_threads, agents_per_thread) pair listed by ks_batch_variants */
+  int32_t agents_per_thread;
+} ks_bucket;
+
+typedef struct ks_batch_info {
+  int32_t batched;       /* 1 = the batched kernel runs ks_step_n                  */
+  int32_t cta_threads;
+  int32_t n_items;       /* work items (batched) or markets (plain)                */
+  int32_t n_buckets;
+  int32_t grid;          /* persistent CTAs launched                               */
+  int32_t pad_;
+  int64_t smem_bytes;    /* dynamic shared memory per CTA                          */
+} ks_batch_info;
 
 /* Bytes of device workspace needed for `cfg`. */
 ks_status ks_workspace_size(const ks_config* cfg, size_t* bytes);
@@ -200,9 +228,26 @@ ks_status ks_sync(ks_ensemble* e, void* stream, uint32_t timeout_ms);
 /* Device error word (0 = none) after synchronising `stream`. */
 ks_status ks_error_word(ks_ensemble* e, void* stream, uint32_t* word);
 
-/* Sets / gets the persistent kernel's launch shape. */
+/* Sets / gets the plain persistent kernel's launch shape (one market per CTA,
+ * markets dealt round-robin).  ks_set_launch switches the ensemble to the
+ * plain kernel. */
 ks_status ks_set_launch(ks_ensemble* e, const ks_launch* l);
 ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l);
+
+/* Switches the ensemble to the batched kernel with the given plan; uploads the
+ * work list on `stream` and synchronises it.  cta_threads: 512 or 1024.
+ * Uneven ensembles start with a default plan (one bucket per power-of-two
+ * (L, A) class, about 8 agents per thread, 1024-thread CTAs). */
+ks_status ks_set_batch_plan(ks_ensemble* e, int32_t cta_threads, const ks_bucket* buckets, int32_t n_buckets,
+                            void* stream);
+
+/* The launch the next ks_step_n will make. */
+ks_status ks_get_batch_info(const ks_ensemble* e, ks_batch_info* info);
+
+/* (group_threads, agents_per_thread) pairs compiled into the batched kernel of
+ * `cta_threads` threads: writes up to `capacity` pairs to `pairs` (may be
+ * NULL) and their number to *count. */
+ks_status ks_batch_variants(int32_t cta_threads, int32_t* pairs, int32_t capacity, int32_t* count);
 
 /* Frees the host handle.  The workspace stays the caller's. */
 ks_status ks_destroy(ks_ensemble* e);

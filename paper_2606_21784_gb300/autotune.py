@@ -1,0 +1,177 @@
+"""Autotuner of the persistent kernels' launch shapes.
+
+Plain kernel: times every compiled (threads, agents/thread, register cap)
+candidate that covers the market size on the real ensemble and keeps the
+fastest.
+
+Batched kernel: splits the ensemble into power-of-two (L, A) buckets; for each
+bucket and each CTA size (512, 1024) it times every compiled (group threads,
+agents/thread) shape that covers the bucket on a sample of the bucket's own
+markets, keeps the fastest per bucket, then picks the CTA size whose plan has
+the smallest estimated total time.  Markets per CTA follow from the group
+size and the shared-memory fit; the tick tile is L / group threads.
+
+Results never change simulation outputs (only speed).  Plans are cached per
+device and ensemble shape in ``_tune_cache.json`` next to this file.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+from . import kineticsim as ks
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json")
+
+
+def _cache_load():
+    try:
+        return json.load(open(_CACHE))
+    except (OSError, ValueError):
+        return {}
+
+
+def _cache_store(key, value):
+    c = _cache_load()
+    c[key] = value
+    tmp = _CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(c, f, indent=1, sort_keys=True)
+    os.replace(tmp, _CACHE)
+
+
+def _device_tag():
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}:{p.multi_processor_count}"
+
+
+def _time_steps(ens, steps):
+    import torch
+    ens.step(max(1, steps // 4))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ens.step(steps)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _pow2(x):
+    return 1 << max(0, int(np.ceil(np.log2(max(int(x), 1)))))
+
+
+def plain_candidates(A):
+    out = []
+    for nt in (128, 256, 512, 1024):
+        for ak in (1, 2, 4, 8, 16):
+            if nt * ak < A or nt * ak > 4 * max(A, 32):
+                continue
+            for rc in (0, 1):
+                out.append(dict(threads=nt, agents_per_thread=ak, reg_cap=rc))
+    return out
+
+
+def tune_plain(w: dict, steps: int = 40, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Best plain-kernel launch for a uniform workload dict; applies nothing."""
+    M, L, A = int(w["M"]), int(w["L"]), int(w["A"])
+    key = f"plain|{_device_tag()}|L{L}|A{A}|M{M}|carry{w['params']['carry_book']}"
+    if use_cache:
+        c = _cache_load().get(key)
+        if c:
+            return c
+    ens = ks.Ensemble(w)
+    events = float(M) * A * steps
+    best = None
+    for cand in plain_candidates(A):
+        try:
+            ens.set_launch(**cand)
+        except ks.KsError:
+            continue
+        rate = events / _time_steps(ens, steps)
+        if verbose:
+            print("plain", cand, f"{rate:.3e}")
+        if best is None or rate > best[0]:
+            best = (rate, cand)
+    ens.close()
+    out = dict(best[1], events_per_s=best[0])
+    _cache_store(key, out)
+    return out
+
+
+def buckets_of(L, A):
+    """Power-of-two (L, A) classes of an ensemble: {(Lc, Ac): [market indices]}."""
+    out = {}
+    for m, (l, a) in enumerate(zip(L, A)):
+        out.setdefault((max(32, _pow2(l)), max(32, _pow2(a))), []).append(m)
+    return out
+
+
+def tune_batched(w: dict, L=None, A=None, steps: int = 20, max_sample: int = 1216, use_cache: bool = True,
+                 verbose: bool = False) -> dict:
+    """Returns {"cta_threads": nt, "buckets": [(L_max, A_max, gt, ak), ...]} for an uneven workload."""
+    from . import workloads
+    if L is None or A is None:
+        L, A = workloads.sizes(w)
+    L = np.asarray(L, np.int32)
+    A = np.asarray(A, np.int32)
+    h = hashlib.sha256(L.tobytes() + A.tobytes()).hexdigest()[:16]
+    key = f"batched|{_device_tag()}|{h}|carry{w['params']['carry_book']}"
+    if use_cache:
+        c = _cache_load().get(key)
+        if c:
+            return c
+    groups = buckets_of(L, A)
+    rng = np.random.default_rng(0)
+    plans = {}
+    for nt in (512, 1024):
+        variants = ks.ks_batch_variants(nt)
+        total = 0.0
+        chosen = []
+        for (Lc, Ac), members in sorted(groups.items()):
+            members = np.asarray(members)
+            if len(members) > max_sample:
+                members = np.sort(rng.choice(members, max_sample, replace=False))
+            sub = dict(w, M=len(members), market_base=0)
+            cands = [(g, k) for g, k in variants if Ac <= g * k <= 4 * Ac]
+            best = None
+            ens = ks.Ensemble(sub, L=L[members], A=A[members])
+            ev = float(A[members].astype(np.int64).sum()) * steps
+            for g, k in cands:
+                try:
+                    ens.set_batch_plan(nt, [(Lc, Ac, g, k)])
+                except ks.KsError:
+                    continue
+                rate = ev / _time_steps(ens, steps)
+                if verbose:
+                    print("batched", nt, (Lc, Ac), (g, k), f"{rate:.3e}")
+                if best is None or rate > best[0]:
+                    best = (rate, g, k)
+            ens.close()
+            if best is None:
+                total = float("inf")
+                break
+            bucket_events = float(A[groups[(Lc, Ac)]].astype(np.int64).sum())
+            total += bucket_events / best[0]
+            chosen.append((int(Lc), int(Ac), int(best[1]), int(best[2])))
+        plans[nt] = (total, chosen)
+    nt = min(plans, key=lambda k: plans[k][0])
+    out = {"cta_threads": nt, "buckets": plans[nt][1], "estimated_s_per_step": plans[nt][0]}
+    _cache_store(key, out)
+    return out
+
+
+def apply(ens, w: dict, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Tunes and applies the launch of an Ensemble built from workload dict ``w``."""
+    if ens.batch_info()["batched"]:
+        plan = tune_batched(w, ens.L, ens.A, use_cache=use_cache, verbose=verbose)
+        ens.set_batch_plan(plan["cta_threads"], plan["buckets"])
+        return plan
+    best = tune_plain(w, use_cache=use_cache, verbose=verbose)
+    ens.set_launch(best["threads"], best["agents_per_thread"], reg_cap=best["reg_cap"])
+    return best

@@ -76,7 +76,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None, p
             if log:
                 sys.stderr.write(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [cc, *ARCH, "-shared", "-Xlinker", "-z,defs", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -1,0 +1,65 @@
+// ks_batched.cuh -- one persistent launch over markets of uneven (L, A).
+//
+// The host sorts markets into (L, A) buckets, gives each bucket a group shape
+// (GT threads per market, AK agents per thread) and packs the markets of a
+// bucket into work items of up to G = min(NT / GT, shared-memory fit) markets.
+// Items are ordered longest first (LPT).  Every CTA repeatedly takes the next
+// item from a global ticket counter, splits itself into G groups that run one
+// market each (named barriers per group, __syncwarp for one-warp groups), and
+// moves on when all its groups are done.
+#pragma once
+
+#include "ks_market.cuh"
+
+namespace ks {
+
+struct BatchArgs {
+  const uint32_t* order;  // market indices grouped by item
+  const uint4* items;     // {first, count, variant, Lcap}
+  uint32_t n_items;
+  uint32_t* ticket;       // next item (reset to 0 after every launch)
+};
+
+template <int NT, int GT, int AK>
+__device__ __forceinline__ void run_item(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+                                         unsigned char* raw) {
+  static_assert(GT == 32 || GT == NT || NT / GT <= 15, "named barrier ids 1..15");
+  constexpr int G = NT / GT;
+  const int g = (int)threadIdx.x / GT;
+  if (g < G && g < (int)d.y) {
+    size_t o[5];
+    const size_t gsz = plain_smem_layout(GT, AK, (int)d.w, o);
+    const Smem sm = carve<GT, AK>(raw + (size_t)g * gsz, (int)d.w);
+    const int bar = (GT == NT) ? 0 : 1 + g;
+    run_market<GT, AK, false>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w);
+  }
+}
+
+// (variant id, GT, AK) lists; the host mirrors them in ks_batched_variants().
+#define KS_BATCH_VARIANTS_1024(X)                                                                          \
+  X(0, 32, 1) X(1, 32, 2) X(2, 32, 4) X(3, 32, 8) X(4, 128, 2) X(5, 128, 4) X(6, 128, 8) X(7, 256, 4) \
+  X(8, 256, 8) X(9, 256, 16) X(10, 512, 8) X(11, 512, 16) X(12, 1024, 8) X(13, 1024, 16)
+#define KS_BATCH_VARIANTS_512(X)                                                                        \
+  X(0, 32, 1) X(1, 32, 2) X(2, 32, 4) X(3, 32, 8) X(4, 64, 2) X(5, 64, 4) X(6, 64, 8) X(7, 128, 4) \
+  X(8, 128, 8) X(9, 256, 8) X(10, 256, 16) X(11, 512, 8) X(12, 512, 16) X(13, 512, 32)
+
+template <int NT>
+__device__ void dispatch_item(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+                              unsigned char* raw);
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) batched_kernel(DevParams P, uint32_t n_steps, BatchArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_item;
+  const uint32_t s0 = (uint32_t)(*P.step);
+  for (;;) {
+    __syncthreads();  // the previous item is finished and s_item has been read
+    if (threadIdx.x == 0) s_item = atomicAdd(B.ticket, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= B.n_items) break;
+    dispatch_item<NT>(P, B, B.items[it], s0, n_steps, smem_raw);
+  }
+}
+
+}  // namespace ks

@@ -12,27 +12,55 @@
 #include <vector>
 
 #include "kineticsim.h"
+#include "kineticsim_probe.h"
 #include "ks_device.cuh"
 #include "ks_internal.h"
+#include "ks_batched.cuh"
 #include "ks_plain.cuh"
 
 namespace ks {
-extern const PlainVariant kPlainNT64[5];
-extern const PlainVariant kPlainNT128[5];
-extern const PlainVariant kPlainNT256[5];
-extern const PlainVariant kPlainNT512[5];
-extern const PlainVariant kPlainNT1024[5];
+extern const PlainVariant kPlainNT128[];
+extern const PlainVariant kPlainNT256[];
+extern const PlainVariant kPlainNT512[];
+extern const PlainVariant kPlainNT1024[];
+extern const int kPlainNT128Count, kPlainNT256Count, kPlainNT512Count, kPlainNT1024Count;
+extern const int kBatchVariants512[][2];
+extern const int kBatchVariants1024[][2];
+extern const int kBatchVariants512Count, kBatchVariants1024Count;
+cudaError_t launch_batched_512(const DevParams& p, uint32_t n_steps, const BatchArgs& b, int grid, size_t smem,
+                               cudaStream_t st);
+cudaError_t launch_batched_1024(const DevParams& p, uint32_t n_steps, const BatchArgs& b, int grid, size_t smem,
+                                cudaStream_t st);
+const void* batched_kernel_512();
+const void* batched_kernel_1024();
 
-const PlainVariant* find_plain(int threads, int ak) {
-  const PlainVariant* tabs[5] = {kPlainNT64, kPlainNT128, kPlainNT256, kPlainNT512, kPlainNT1024};
-  for (auto* t : tabs)
-    for (int i = 0; i < 5; ++i)
-      if (t[i].threads == threads && t[i].ak == ak) return &t[i];
+const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy) {
+  const PlainVariant* tabs[4] = {kPlainNT128, kPlainNT256, kPlainNT512, kPlainNT1024};
+  const int counts[4] = {kPlainNT128Count, kPlainNT256Count, kPlainNT512Count, kPlainNT1024Count};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < counts[i]; ++j) {
+      const PlainVariant& v = tabs[i][j];
+      if (v.threads == threads && v.ak == ak && v.aggregate == (aggregate ? 1 : 0) && v.occupancy == occupancy)
+        return &v;
+    }
+  return nullptr;
+}
+
+static const int (*batch_table(int nt, int* count))[2] {
+  if (nt == 512) {
+    *count = kBatchVariants512Count;
+    return kBatchVariants512;
+  }
+  if (nt == 1024) {
+    *count = kBatchVariants1024Count;
+    return kBatchVariants1024;
+  }
+  *count = 0;
   return nullptr;
 }
 
 size_t plain_smem_bytes(int threads, int ak, int Lmax) {
-  size_t o[6];
+  size_t o[5];
   return plain_smem_layout(threads, ak, Lmax, o);
 }
 
@@ -68,7 +96,12 @@ __global__ void init_kernel(DevParams P) {
   }
 }
 
-__global__ void step_bump_kernel(uint64_t* step, uint32_t n) { *step += n; }
+// Advances the device step counter after a launch and re-arms the batched
+// kernel's work ticket for the next launch.
+__global__ void step_bump_kernel(uint64_t* step, uint32_t* ticket, uint32_t n) {
+  *step += n;
+  *ticket = 0u;
+}
 
 }  // namespace ks
 
@@ -108,16 +141,26 @@ struct ks_ensemble {
   unsigned char* ws;
   size_t ws_bytes;
   DevParams dp;
+  int mode;  // 0 plain kernel, 1 batched kernel
   ks_launch launch;
   const PlainVariant* var;
   int grid;
   size_t smem;
+  // batched mode
+  int b_threads;
+  std::vector<ks_bucket> b_plan;
+  std::vector<uint32_t> b_order;
+  std::vector<uint4> b_items;
+  BatchArgs b_args;
+  int b_grid;
+  size_t b_smem;
   int device;
   int num_sms;
+  size_t max_smem;
 };
 
 struct Layout {
-  size_t slot, inv, cash, mi32, mi64, aoff, Ls, As, trace, ctrl, total;
+  size_t slot, inv, cash, mi32, mi64, aoff, Ls, As, order, items, trace, ctrl, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -133,6 +176,8 @@ static Layout make_layout(uint32_t M, int64_t N, bool uniform, uint32_t tm, uint
   l.aoff = o; o = align256(o + (uniform ? 0 : (size_t)(M + 1) * 8));
   l.Ls = o; o = align256(o + (uniform ? 0 : (size_t)M * 4));
   l.As = o; o = align256(o + (uniform ? 0 : (size_t)M * 4));
+  l.order = o; o = align256(o + (size_t)M * 4);
+  l.items = o; o = align256(o + (size_t)M * 16);
   l.trace = o; o = align256(o + (size_t)tm * ts * 2 * 4);
   l.ctrl = o; o = align256(o + 64);  // err (u32) at +0, step (u64) at +8, ticket (u32) at +16
   l.total = o;
@@ -202,18 +247,16 @@ static int next_pow2(int x) {
 }
 
 // Default launch shape: with few markets, spread each market over many
-// threads; otherwise about 8 agents per thread.
+// threads; otherwise 16 agents per thread under the ~85-register cap (the
+// fastest shape measured on GB300 for 4096-agent markets).
 static ks_launch default_launch(int Amax, uint32_t M, int num_sms) {
   ks_launch l;
   memset(&l, 0, sizeof(l));
-  int nt, ak;
-  if ((int)M < 2 * num_sms) {
-    nt = std::min(1024, std::max(64, next_pow2(Amax)));
-  } else {
-    nt = std::min(1024, std::max(64, next_pow2((Amax + 7) / 8)));
-  }
-  ak = next_pow2(std::max(1, (Amax + nt - 1) / nt));
-  while (ak > 16) {
+  const bool few = (int)M < 2 * num_sms;
+  int nt = few ? next_pow2(std::max(Amax, 1)) : next_pow2((std::max(Amax, 1) + 15) / 16);
+  nt = std::min(1024, std::max(128, nt));
+  int ak = next_pow2(std::max(1, (Amax + nt - 1) / nt));
+  while (ak > 16 && nt < 1024) {
     nt *= 2;
     ak = next_pow2(std::max(1, (Amax + nt - 1) / nt));
   }
@@ -221,18 +264,19 @@ static ks_launch default_launch(int Amax, uint32_t M, int num_sms) {
   l.agents_per_thread = ak;
   l.ctas_per_sm = 0;
   l.aggregate = 0;
+  l.reg_cap = few ? 0 : 1;
   return l;
 }
 
 static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
-  const PlainVariant* v = find_plain(l->threads, l->agents_per_thread);
-  if (!v) return arg_fail(KS_ERR_INVALID_ARG, "no kernel for this (threads, agents_per_thread)");
+  const PlainVariant* v = find_plain(l->threads, l->agents_per_thread, l->aggregate, l->reg_cap);
+  if (!v) return arg_fail(KS_ERR_INVALID_ARG, "no kernel for this (threads, agents_per_thread, aggregate, reg_cap)");
   if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
     return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
   if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
   const size_t smem = plain_smem_bytes(l->threads, l->agents_per_thread, e->Lmax);
-  if (smem > 227 * 1024) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more than 227 KB shared memory");
-  const void* k = l->aggregate ? v->kernel_aggr : v->kernel_plain;
+  if (smem > e->max_smem) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more shared memory than a CTA has");
+  const void* k = v->kernel;
   KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, l->threads, smem));
@@ -242,7 +286,160 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   e->smem = smem;
   e->var = v;
   e->launch = *l;
+  e->mode = 0;
   return KS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched plans: buckets -> work items (markets per CTA, longest first)
+// ---------------------------------------------------------------------------
+static int batch_variant_id(int nt, int gt, int ak) {
+  int n = 0;
+  const int(*tab)[2] = batch_table(nt, &n);
+  for (int i = 0; i < n; ++i)
+    if (tab[i][0] == gt && tab[i][1] == ak) return i;
+  return -1;
+}
+
+// Groups of one bucket that fit one CTA: thread count, barrier ids, shared memory.
+static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz) {
+  *gsz = plain_smem_bytes(gt, ak, Lcap);
+  int g = nt / gt;
+  if (gt != 32 && gt != nt) g = std::min(g, 15);
+  g = std::min<int64_t>(g, (int64_t)(max_smem / *gsz));
+  return g;
+}
+
+// Default bucket shape: about 8 agents per thread.
+static bool default_shape(int nt, int Ac, int* gt, int* ak) {
+  int n = 0;
+  const int(*tab)[2] = batch_table(nt, &n);
+  int best = -1;
+  long best_score = 0;
+  for (int i = 0; i < n; ++i) {
+    const int g = tab[i][0], k = tab[i][1];
+    if ((long)g * k < Ac) continue;
+    const long waste = (long)g * k - Ac;
+    const long score = waste * 16 + std::abs(k - 8);
+    if (best < 0 || score < best_score) {
+      best = i;
+      best_score = score;
+    }
+  }
+  if (best < 0) return false;
+  *gt = tab[best][0];
+  *ak = tab[best][1];
+  return true;
+}
+
+static std::vector<ks_bucket> default_plan(const std::vector<int32_t>& L, const std::vector<int32_t>& A, int nt) {
+  std::vector<std::pair<int, int>> keys;
+  for (size_t m = 0; m < L.size(); ++m) {
+    const int Lc = std::max(32, next_pow2(L[m]));
+    const int Ac = std::max(32, next_pow2(std::max(A[m], 1)));
+    keys.emplace_back(Lc, Ac);
+  }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  std::vector<ks_bucket> plan;
+  for (auto& k : keys) {
+    ks_bucket b;
+    b.L_max = k.first;
+    b.A_max = k.second;
+    if (!default_shape(nt, k.second, &b.group_threads, &b.agents_per_thread)) continue;
+    plan.push_back(b);
+  }
+  return plan;
+}
+
+static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, int nb, cudaStream_t st) {
+  if (nt != 512 && nt != 1024) return arg_fail(KS_ERR_INVALID_ARG, "batched CTA size must be 512 or 1024");
+  if (nb <= 0 || !buckets) return arg_fail(KS_ERR_INVALID_ARG, "empty batch plan");
+  const void* kern = nt == 512 ? batched_kernel_512() : batched_kernel_1024();
+  const size_t max_dyn = e->max_smem - 1024;  // room for the kernel's static shared memory
+  std::vector<int> var(nb);
+  std::vector<int> G(nb);
+  std::vector<size_t> gsz(nb);
+  for (int b = 0; b < nb; ++b) {
+    const ks_bucket& k = buckets[b];
+    var[b] = batch_variant_id(nt, k.group_threads, k.agents_per_thread);
+    if (var[b] < 0) return arg_fail(KS_ERR_INVALID_ARG, "bucket shape not compiled into the batched kernel");
+    if ((int64_t)k.group_threads * k.agents_per_thread < k.A_max)
+      return arg_fail(KS_ERR_INVALID_ARG, "bucket group_threads * agents_per_thread below its A_max");
+    if (k.L_max < 2 || k.L_max > KS_MAX_TICKS) return arg_fail(KS_ERR_INVALID_ARG, "bucket L_max out of range");
+    G[b] = groups_per_cta(nt, k.group_threads, k.agents_per_thread, k.L_max, max_dyn, &gsz[b]);
+    if (G[b] < 1) return arg_fail(KS_ERR_UNSUPPORTED, "bucket does not fit the shared memory of one CTA");
+  }
+  std::vector<std::vector<uint32_t>> members(nb);
+  for (uint32_t m = 0; m < e->M; ++m) {
+    int b = 0;
+    while (b < nb && !(e->L[m] <= buckets[b].L_max && e->A[m] <= buckets[b].A_max)) ++b;
+    if (b == nb) return arg_fail(KS_ERR_INVALID_ARG, "a market matches no bucket of the plan");
+    members[b].push_back(m);
+  }
+  struct Item {
+    double cost;
+    int bucket;
+    std::vector<uint32_t> mk;
+  };
+  std::vector<Item> items;
+  size_t smem = 16;
+  for (int b = 0; b < nb; ++b) {
+    auto& mb = members[b];
+    if (mb.empty()) continue;
+    std::sort(mb.begin(), mb.end(), [&](uint32_t x, uint32_t y) {
+      return e->A[x] != e->A[y] ? e->A[x] > e->A[y] : x < y;
+    });
+    smem = std::max(smem, (size_t)std::min<size_t>(G[b], mb.size()) * gsz[b]);
+    for (size_t i = 0; i < mb.size(); i += G[b]) {
+      Item it;
+      it.bucket = b;
+      it.mk.assign(mb.begin() + i, mb.begin() + std::min(mb.size(), i + G[b]));
+      // cost of an item ~ its largest market: agent work plus the per-step tick work
+      it.cost = (double)e->A[it.mk[0]] + 0.25 * (double)buckets[b].L_max;
+      items.push_back(std::move(it));
+    }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
+  std::vector<uint32_t> order;
+  std::vector<uint4> ditems;
+  for (auto& it : items) {
+    uint4 d;
+    d.x = (uint32_t)order.size();
+    d.y = (uint32_t)it.mk.size();
+    d.z = (uint32_t)var[it.bucket];
+    d.w = (uint32_t)buckets[it.bucket].L_max;
+    order.insert(order.end(), it.mk.begin(), it.mk.end());
+    ditems.push_back(d);
+  }
+  KS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem));
+  if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "batched plan does not fit on an SM");
+  const Layout lay = make_layout(e->M, e->N, e->uniform, e->cfg.trace_markets, e->cfg.trace_steps);
+  KS_CUDA(cudaMemcpyAsync(e->ws + lay.order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, st));
+  KS_CUDA(cudaMemcpyAsync(e->ws + lay.items, ditems.data(), ditems.size() * 16, cudaMemcpyHostToDevice, st));
+  KS_CUDA(cudaStreamSynchronize(st));  // the host vectors feeding the copies may be reused
+  e->b_threads = nt;
+  e->b_plan.assign(buckets, buckets + nb);
+  e->b_order = std::move(order);
+  e->b_items = std::move(ditems);
+  e->b_args.order = (const uint32_t*)(e->ws + lay.order);
+  e->b_args.items = (const uint4*)(e->ws + lay.items);
+  e->b_args.n_items = (uint32_t)e->b_items.size();
+  e->b_args.ticket = (uint32_t*)(e->ws + lay.ctrl + 16);
+  e->b_smem = smem;
+  e->b_grid = (int)std::min<int64_t>((int64_t)occ * e->num_sms, std::max<int64_t>(1, (int64_t)e->b_items.size()));
+  e->mode = 1;
+  return KS_OK;
+}
+
+static cudaError_t launch_main(ks_ensemble* e, uint32_t n_steps, cudaStream_t st) {
+  if (e->mode == 1) {
+    return e->b_threads == 512 ? launch_batched_512(e->dp, n_steps, e->b_args, e->b_grid, e->b_smem, st)
+                               : launch_batched_1024(e->dp, n_steps, e->b_args, e->b_grid, e->b_smem, st);
+  }
+  return e->var->launch(e->dp, n_steps, e->grid, e->smem, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -306,6 +503,9 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
   e->ws_bytes = ws_bytes;
   cudaError_t ce = cudaGetDevice(&e->device);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+  int max_optin = 0;
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->device);
+  e->max_smem = (size_t)max_optin;
   if (ce != cudaSuccess) {
     delete e;
     return cuda_fail(ce, "device query");
@@ -346,10 +546,11 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
   p.trace = (int32_t*)(w + lay.trace);
   p.err = (uint32_t*)(w + lay.ctrl);
   p.step = (const uint64_t*)(w + lay.ctrl + 8);
+  e->b_args.ticket = (uint32_t*)(w + lay.ctrl + 16);
 
   ks_launch l = default_launch(e->Amax, e->M, e->num_sms);
   s = apply_launch(e, &l);
-  if (s != KS_OK) {
+  if (s != KS_OK && sz.uniform) {
     delete e;
     return s;
   }
@@ -375,6 +576,15 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
   // host copies above read pageable vectors owned by the handle; make sure they are done
   KS_CUDA_E(cudaStreamSynchronize(st));
 #undef KS_CUDA_E
+  if (!sz.uniform) {
+    // uneven ensembles default to the batched kernel with one bucket per (L, A) power-of-two class
+    std::vector<ks_bucket> plan = default_plan(e->L, e->A, 1024);
+    s = build_batch(e, 1024, plan.data(), (int)plan.size(), st);
+    if (s != KS_OK) {
+      delete e;
+      return s;
+    }
+  }
   *out = e;
   return KS_OK;
 }
@@ -383,8 +593,8 @@ ks_status ks_step_n(ks_ensemble* e, uint32_t n_steps, void* stream) {
   if (!e) return arg_fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
   if (n_steps == 0) return KS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  KS_CUDA(e->var->launch(e->dp, n_steps, e->grid, e->smem, st, e->launch.aggregate));
-  step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, n_steps);
+  KS_CUDA(launch_main(e, n_steps, st));
+  step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, e->b_args.ticket, n_steps);
   KS_CUDA(cudaGetLastError());
   return KS_OK;
 }
@@ -498,6 +708,48 @@ ks_status ks_set_launch(ks_ensemble* e, const ks_launch* l) {
 ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l) {
   if (!e || !l) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
   *l = e->launch;
+  return KS_OK;
+}
+
+ks_status ks_set_batch_plan(ks_ensemble* e, int32_t cta_threads, const ks_bucket* buckets, int32_t n_buckets,
+                            void* stream) {
+  if (!e || !buckets) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  return build_batch(e, cta_threads, buckets, n_buckets, (cudaStream_t)stream);
+}
+
+ks_status ks_get_batch_info(const ks_ensemble* e, ks_batch_info* info) {
+  if (!e || !info) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  memset(info, 0, sizeof(*info));
+  info->batched = e->mode == 1;
+  info->cta_threads = e->mode == 1 ? e->b_threads : e->launch.threads;
+  info->n_items = e->mode == 1 ? (int32_t)e->b_items.size() : (int32_t)e->M;
+  info->n_buckets = e->mode == 1 ? (int32_t)e->b_plan.size() : 1;
+  info->grid = e->mode == 1 ? e->b_grid : e->grid;
+  info->smem_bytes = (int64_t)(e->mode == 1 ? e->b_smem : e->smem);
+  return KS_OK;
+}
+
+ks_status ks_batch_variants(int32_t cta_threads, int32_t* pairs, int32_t capacity, int32_t* count) {
+  if (!count) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  int n = 0;
+  const int(*tab)[2] = batch_table(cta_threads, &n);
+  if (!tab) return arg_fail(KS_ERR_INVALID_ARG, "batched CTA size must be 512 or 1024");
+  *count = n;
+  if (pairs)
+    for (int i = 0; i < n && i < capacity; ++i) {
+      pairs[2 * i] = tab[i][0];
+      pairs[2 * i + 1] = tab[i][1];
+    }
+  return KS_OK;
+}
+
+ks_status ks_probe_state_io(ks_ensemble* e, void* stream, double* bytes) {
+  if (!e || !bytes) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  // zero steps: load every market, rebuild its book, store it back unchanged
+  KS_CUDA(launch_main(e, 0u, (cudaStream_t)stream));
+  step_bump_kernel<<<1, 1, 0, (cudaStream_t)stream>>>((uint64_t*)e->dp.step, e->b_args.ticket, 0u);
+  KS_CUDA(cudaGetLastError());
+  *bytes = (double)e->N * 32.0 + (double)e->M * 2.0 * (MI32_STRIDE * 4 + MI64_STRIDE * 8);
   return KS_OK;
 }
 

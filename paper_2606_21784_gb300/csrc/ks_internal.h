@@ -54,19 +54,19 @@ struct DevParams {
   const uint64_t* step;      // absolute step counter (device)
 };
 
-// A persistent launch of the plain kernel template (threads, agents/thread).
-using PlainLaunchFn = cudaError_t (*)(const DevParams& p, uint32_t n_steps, int grid, size_t smem,
-                                      cudaStream_t st, int aggregate);
+// A persistent launch of the plain kernel template.
+using PlainLaunchFn = cudaError_t (*)(const DevParams& p, uint32_t n_steps, int grid, size_t smem, cudaStream_t st);
 struct PlainVariant {
   int threads;
   int ak;
+  int aggregate;  // warp-aggregated book atomics
+  int occupancy;  // register-cap class (0 none, 1 ~85, 2 64 registers)
   PlainLaunchFn launch;
-  const void* kernel_plain;  // for occupancy queries
-  const void* kernel_aggr;
+  const void* kernel;  // for attribute and occupancy queries
 };
 
 // Registry filled by the instantiation translation units.
-const PlainVariant* plain_variants(int* count);
+const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy);
 
 // Shared memory bytes of the plain kernel for a launch shape and max L.
 size_t plain_smem_bytes(int threads, int ak, int Lmax);

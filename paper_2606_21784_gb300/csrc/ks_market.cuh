@@ -1,0 +1,491 @@
+// ks_market.cuh -- one market's persistent call-auction loop (sm_103a).
+//
+// A group of GT threads (a whole CTA, or a slice of one when several small
+// markets share a CTA) owns one market at a time and keeps it on chip for all n steps of a
+// call (the paper's Algorithm 1 and Sec. III-B residency, re-shaped for
+// GB300): thread t owns agents [t*AK, t*AK+AK) -- order words in registers,
+// inventory and cash in thread-private shared-memory columns -- and ticks
+// [t*LT, t*LT+LT) of the aggregated book in shared memory.
+//
+// Step s, between four group barriers:
+//   B1  all orders of step s are in the book (shared atomics)      (Alg. 1, Phase 3)
+//   B2  per-thread tick sums, warp shuffle scans; warp totals published
+//   B3  D_cum / S_cum / V = min per tick (Eq. 1-2); warp redux.sync of the
+//       best V and its lowest / highest tick; one 64-bit shared atomicMax per
+//       warp for each.  The lowest maximiser of V is p* (ties to the lowest
+//       tick, Sec. III-D) and the marginal sell tick; the highest maximiser is
+//       the marginal buy tick.                                    (Phase 4)
+//   B5  tick owners update the resting book without atomics and publish the
+//       rationed remainders at the marginal ticks; each thread sums its
+//       orders resting at the marginal ticks for one ordered block scan.
+//   then one pass per agent fills step s (price priority, then ascending
+//   agent index at the marginal ticks, Sec. IV-C) and draws step s+1's
+//   cancellation and new order (Philox4x32-10).                  (Phase 5)
+// Global memory is touched only when a market is loaded and stored, so the
+// traffic does not grow with the number of steps (Sec. III-E).
+#pragma once
+
+#include <stdint.h>
+
+#include "ks_device.cuh"
+
+namespace ks {
+
+struct Smem {
+  int64_t* cash;          // [AK][NT] thread-private columns
+  unsigned long long* kx; // [2 parities][4]: lowest / highest maximiser keys, tie key
+  int32_t* inv;           // [AK][NT]
+  int32_t* book;          // buy at [0, BL), sell at [BL, 2 BL), BL = book_len(Lmax)
+  int32_t* wD;            // [32] warp totals of BUY
+  int32_t* wS;            // [32] warp totals of SELL
+  uint32_t* wMB;          // [32] warp totals of marginal buy quantity
+  uint32_t* wMS;          // [32] warp totals of marginal sell quantity
+  int32_t* rem;           // [2]: R_b, R_s (units filled at the marginal buy / sell tick)
+};
+
+__host__ __device__ inline size_t plain_smem_layout(int nt, int ak, int Lmax, size_t* o) {
+  size_t off = 0;
+  o[0] = off; off += (size_t)8 * ak * nt;                // cash
+  o[1] = off; off += (size_t)8 * 8;                      // kx
+  o[2] = off; off += (size_t)4 * ak * nt;                // inv
+  o[3] = off; off += (size_t)4 * 2 * book_len(Lmax);     // book
+  o[4] = off; off += (size_t)4 * 32 * 4 + 4 * 4;         // wD, wS, wMB, wMS, rem
+  return (off + 15) & ~(size_t)15;
+}
+
+template <int NT, int AK>
+__device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
+  size_t o[5];
+  plain_smem_layout(NT, AK, Lmax, o);
+  Smem s;
+  s.cash = reinterpret_cast<int64_t*>(raw + o[0]);
+  s.kx = reinterpret_cast<unsigned long long*>(raw + o[1]);
+  s.inv = reinterpret_cast<int32_t*>(raw + o[2]);
+  s.book = reinterpret_cast<int32_t*>(raw + o[3]);
+  s.wD = reinterpret_cast<int32_t*>(raw + o[4]);
+  s.wS = s.wD + 32;
+  s.wMB = reinterpret_cast<uint32_t*>(s.wD + 64);
+  s.wMS = s.wMB + 32;
+  s.rem = s.wD + 128;
+  return s;
+}
+
+// Barrier of the GT threads owning a market: a warp-sized group uses
+// __syncwarp, larger groups a named barrier (id 0 only when the group is the
+// whole CTA).
+template <int GT>
+__device__ __forceinline__ void gsync(int bar) {
+  if constexpr (GT == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(GT) : "memory");
+  }
+}
+
+__device__ __forceinline__ int bidx(uint32_t sell, uint32_t tick, int sb) {
+  return (int)(tick + (tick >> 5)) + (sell ? sb : 0);
+}
+
+// Add the order word's quantity at its (side, tick).  With AGGR, lanes of the
+// warp holding the same (side, tick) first combine their quantities
+// (__match_any_sync + __reduce_add_sync) and one lane issues the atomic.
+template <bool AGGR>
+__device__ __forceinline__ void book_add(int32_t* book, int sb, bool valid, uint32_t w) {
+  const uint32_t sell = w_sell(w), tick = w_tick(w);
+  const int q = (int)w_qty(w);
+  if constexpr (AGGR) {
+    const uint32_t key = valid ? ((sell << 12) | tick) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int tot = (int)__reduce_add_sync(peers, (unsigned)q);
+    const int leader = __ffs(peers) - 1;
+    if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(book + bidx(sell, tick, sb), tot);
+  } else {
+    if (valid) atomicAdd(book + bidx(sell, tick, sb), q);
+  }
+}
+
+// Uniform per-step inputs of the agent rules.
+struct StepRules {
+  StepKey sk;
+  int last;
+  int side_mom;  // 0 buy, 1 sell, -1 undecided
+  int side_mr;
+};
+
+// Step-s order of one agent: cancellation of its working order (carried
+// books), then a new order if it has none.  Returns the new order word.
+template <bool AGGR>
+__device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, bool valid, const StepRules& sr, bool carry,
+                                                uint32_t cthr, int L, const RuleConsts& rc, int32_t* book, int sb) {
+  const uint4 w = step_draw(sr.sk, (uint32_t)a);
+  const uint32_t q = w_qty(sl);
+  const bool cancel = valid && carry && q != 0u && w.x < cthr;
+  if (cancel) atomicSub(book + bidx(w_sell(sl), w_tick(sl), sb), (int)q);
+  const bool dec = valid && (q == 0u || cancel) && !(sl & W_MLP);
+  const uint32_t ns = decide_rule(sl, w, sr.last, sr.side_mom, sr.side_mr, L, rc);
+  book_add<AGGR>(book, sb, dec, ns);
+  return dec ? ns : (cancel ? (sl & W_STATIC) : sl);
+}
+
+__device__ __forceinline__ StepRules step_rules(const DevParams& P, uint32_t s, uint32_t gm, int h0, int hlb, int last,
+                                                int fund) {
+  StepRules r;
+  r.sk = step_key(s, gm, 0u, P.key0, P.key1);
+  const int ret = h0 - hlb;
+  r.side_mom = ret > 0 ? 0 : (ret < 0 ? 1 : -1);
+  r.side_mr = last < fund ? 0 : (last > fund ? 1 : -1);
+  r.last = last;
+  return r;
+}
+
+// hist[lookback] with a compile-time index per candidate, so the history
+// stays in registers.
+__device__ __forceinline__ int hist_at(const int (&hist)[KS_HISTORY], int lb) {
+  int h = hist[1];
+#pragma unroll
+  for (int i = 2; i < KS_HISTORY; ++i) h = (lb == i) ? hist[i] : h;
+  return h;
+}
+
+// Signed distance of an order from its side's marginal tick: > 0 fills fully,
+// 0 is at the marginal tick, < 0 does not trade.
+__device__ __forceinline__ int fill_dist(uint32_t sl, int p_lo, int p_hi) {
+  const int tk = (int)w_tick(sl);
+  return w_sell(sl) ? (p_lo - tk) : (tk - p_hi);
+}
+
+// Runs steps [s0, s0 + n_steps) of market m.  t: thread index in the group,
+// bar: the group's barrier id, Lcap: the largest L the group's shared memory
+// (sm) was carved for.
+template <int NT, int AK, bool AGGR>
+__device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t n_steps, const Smem& sm, int t,
+                           int bar, int Lcap) {
+  const int lane = t & 31;
+  const int wid = t >> 5;
+  const int L = P.Ls ? P.Ls[m] : P.L_all;
+  const int A = P.As ? P.As[m] : P.A_all;
+  const int64_t aoff = P.agent_off ? P.agent_off[m] : (int64_t)m * (int64_t)P.A_all;
+  if (A > NT * AK || L > Lcap || L < 2 || A < 0) {
+    if (t == 0) atomicOr(P.err, ERR_SHAPE);
+    return;  // uniform across the group
+  }
+  const int LT = (L + NT - 1) / NT;
+  const int p0 = t * LT;
+  const int sb = book_len(Lcap);  // offset of the SELL half of the book
+  int32_t* book = sm.book;
+
+  // ---- load the market's state (128-bit accesses where aligned) -----------------
+  uint32_t slot[AK];
+  const int a0 = t * AK;
+  const bool vec = (AK % 4 == 0) && ((aoff + a0) % 4 == 0) && (a0 + AK <= A);
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < AK; k += 4) {
+      const uint4 sv = *reinterpret_cast<const uint4*>(P.slot + aoff + a0 + k);
+      const int4 iv = *reinterpret_cast<const int4*>(P.inv + aoff + a0 + k);
+      const longlong2 c0 = *reinterpret_cast<const longlong2*>(P.cash + aoff + a0 + k);
+      const longlong2 c1 = *reinterpret_cast<const longlong2*>(P.cash + aoff + a0 + k + 2);
+      slot[k] = sv.x; slot[k + 1] = sv.y; slot[k + 2] = sv.z; slot[k + 3] = sv.w;
+      sm.inv[(k + 0) * NT + t] = iv.x; sm.inv[(k + 1) * NT + t] = iv.y;
+      sm.inv[(k + 2) * NT + t] = iv.z; sm.inv[(k + 3) * NT + t] = iv.w;
+      sm.cash[(k + 0) * NT + t] = c0.x; sm.cash[(k + 1) * NT + t] = c0.y;
+      sm.cash[(k + 2) * NT + t] = c1.x; sm.cash[(k + 3) * NT + t] = c1.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < AK; ++k) {
+      const int a = a0 + k;
+      const bool v = a < A;
+      slot[k] = v ? P.slot[aoff + a] : 0u;
+      sm.inv[k * NT + t] = v ? P.inv[aoff + a] : 0;
+      sm.cash[k * NT + t] = v ? P.cash[aoff + a] : 0ll;
+    }
+  }
+  const int32_t* mi = P.mi32 + (size_t)m * MI32_STRIDE;
+  int hist[KS_HISTORY];
+#pragma unroll
+  for (int j = 0; j < KS_HISTORY; ++j) hist[j] = mi[MI_HIST + j];
+  int last = mi[MI_LAST];
+  const int fund = mi[MI_FUND];
+  int trades = mi[MI_TRADES];
+  int lastv = mi[MI_LASTV];
+  const int64_t* mi64 = P.mi64 + (size_t)m * MI64_STRIDE;
+  int64_t sump = mi64[MI_SUMP];
+  int64_t sumv = mi64[MI_SUMV];
+  uint64_t hash = (uint64_t)mi64[MI_HASH];
+
+  // rebuild the aggregated resting book from the working orders
+  for (int i = t; i < 2 * sb; i += NT) book[i] = 0;
+  if (t < 8) sm.kx[t] = 0ull;
+  gsync<NT>(bar);
+#pragma unroll
+  for (int k = 0; k < AK; ++k) {
+    // an order word written through ks_write_state may name a tick outside the grid
+    if (w_qty(slot[k]) != 0u && (int)w_tick(slot[k]) >= L) {
+      atomicOr(P.err, ERR_TICK);
+      slot[k] &= W_STATIC;
+    }
+    book_add<AGGR>(book, sb, w_qty(slot[k]) != 0u, slot[k]);
+  }
+
+  RuleConsts rc;
+  rc.zi_off = P.zi_off;
+  rc.zi_n = 2u * (uint32_t)P.zi_off + 1u;
+  rc.zi_qmax = (uint32_t)P.zi_qmax;
+  rc.mom_n = (uint32_t)P.mom_omax + 1u;
+  rc.mr_n = (uint32_t)P.mr_omax + 1u;
+  rc.rb_qmax = (uint32_t)P.rb_qmax;
+  const bool carry = P.carry != 0;
+  const uint32_t cthr = P.cancel_thr;
+  const bool traced = m < P.trace_markets;
+  const uint32_t gm = P.market_base + m;
+  const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
+
+  // orders of the first step
+  if (n_steps > 0) {
+    const StepRules sr = step_rules(P, s0, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+#pragma unroll
+    for (int k = 0; k < AK; ++k)
+      slot[k] = order_agent<AGGR>(slot[k], a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+  }
+
+  for (uint32_t j = 0; j < n_steps; ++j) {
+    const uint32_t s = s0 + j;
+    unsigned long long* kx = sm.kx + 4 * (j & 1);
+    gsync<NT>(bar);  // B1: all orders of step s are in the book
+
+    // ---- scans of the book -----------------------------------------------------------
+    int sumB = 0, sumS = 0;
+#pragma unroll 4
+    for (int i = 0; i < LT; ++i) {
+      const int p = p0 + i;
+      if (p < L) {
+        sumB += book[bidx(0, p, sb)];
+        sumS += book[bidx(1, p, sb)];
+      }
+    }
+    int sufB = sumB, preS = sumS;  // inclusive warp suffix (BUY) / prefix (SELL) scans
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int vb = __shfl_down_sync(0xffffffffu, sufB, d);
+      const int vs = __shfl_up_sync(0xffffffffu, preS, d);
+      if (lane + d < 32) sufB += vb;
+      if (lane >= d) preS += vs;
+    }
+    if (lane == 0) sm.wD[wid] = sufB;
+    if (lane == 31) sm.wS[wid] = preS;
+    gsync<NT>(bar);  // B2
+    const int offD = (int)__reduce_add_sync(0xffffffffu, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
+    const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
+    const int D0 = offD + sufB;          // D_cum at my first tick
+    const int Sb0 = offS + preS - sumS;  // S_cum just below my first tick
+    {
+      int D = D0, Sb = Sb0;
+      int bestV = -1, lo = 4095, hi = 0;
+      unsigned long long kT = 0ull;
+#pragma unroll 4
+      for (int i = 0; i < LT; ++i) {
+        const int p = p0 + i;
+        if (p < L) {
+          const int b = book[bidx(0, p, sb)];
+          const int S = Sb + book[bidx(1, p, sb)];
+          const int v = min(D, S);
+          if (v > bestV) { bestV = v; lo = p; }
+          if (v >= bestV) hi = p;
+          if (tie1) {
+            const int imb = min(abs(D - S), (1 << 22) - 1);
+            const unsigned long long tk = ((unsigned long long)(uint32_t)v << 34) |
+                                          ((unsigned long long)((1 << 22) - 1 - imb) << 12) | (4095u - p);
+            kT = tk > kT ? tk : kT;
+          }
+          D -= b;
+          Sb = S;
+        }
+      }
+      const int vw = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(bestV, 0));
+      const bool top = bestV == vw;
+      const uint32_t low = __reduce_min_sync(0xffffffffu, top ? (unsigned)lo : 4095u);
+      const uint32_t high = __reduce_max_sync(0xffffffffu, top ? (unsigned)hi : 0u);
+      if (tie1) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, kT, d);
+          kT = o > kT ? o : kT;
+        }
+      }
+      if (lane == 0) {
+        atomicMax(kx + 0, ((unsigned long long)(uint32_t)vw << 12) | (4095u - low));
+        atomicMax(kx + 1, ((unsigned long long)(uint32_t)vw << 12) | high);
+        if (tie1) atomicMax(kx + 2, kT);
+      }
+    }
+    gsync<NT>(bar);  // B3
+    const unsigned long long kLo = kx[0], kHi = kx[1];
+    const int vstar = (int)(kLo >> 12);
+    const int p_lo = 4095 - (int)(kLo & 4095u);
+    const int p_hi = (int)(kHi & 4095u);
+    const int pstar = tie1 ? 4095 - (int)(kx[2] & 4095u) : p_lo;
+    const bool trade = vstar > 0;
+    if (t < 4) sm.kx[4 * ((j + 1) & 1) + t] = 0ull;  // reset the other parity for step s+1
+
+    // ---- resting book per tick, marginal remainders -----------------------------------
+    // The owners of the marginal ticks publish R_b = V* - D_cum[p_hi + 1] and
+    // R_s = V* - S_cum[p_lo - 1]; a carried book keeps what did not trade
+    // (Phase 5), a discarded book is emptied.
+    if (trade || !carry) {
+      int D = D0, Sb = Sb0;
+#pragma unroll 4
+      for (int i = 0; i < LT; ++i) {
+        const int p = p0 + i;
+        if (p < L) {
+          const int bi = bidx(0, p, sb), si = bidx(1, p, sb);
+          const int b = book[bi];
+          const int sv = book[si];
+          const int rb = vstar - (D - b);
+          const int rs = vstar - Sb;
+          if (trade && p == p_hi) sm.rem[0] = rb;
+          if (trade && p == p_lo) sm.rem[1] = rs;
+          if (carry) {
+            if (p > p_hi) book[bi] = 0;
+            if (p == p_hi) book[bi] = b - rb;
+            if (p < p_lo) book[si] = 0;
+            if (p == p_lo) book[si] = sv - rs;
+          } else {
+            book[bi] = 0;
+            book[si] = 0;
+          }
+          D -= b;
+          Sb += sv;
+        }
+      }
+    }
+
+    // ---- marginal quantities in agent order --------------------------------------------
+    uint32_t exB = 0, exS = 0;
+    if (trade) {
+      uint32_t mB = 0, mS = 0;
+#pragma unroll
+      for (int k = 0; k < AK; ++k) {
+        const uint32_t sl = slot[k];
+        const uint32_t q = w_qty(sl);
+        const bool marg = q != 0u && fill_dist(sl, p_lo, p_hi) == 0;
+        mB += (marg && !w_sell(sl)) ? q : 0u;
+        mS += (marg && w_sell(sl)) ? q : 0u;
+      }
+      uint32_t iB = mB, iS = mS;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t ob = __shfl_up_sync(0xffffffffu, iB, d);
+        const uint32_t os = __shfl_up_sync(0xffffffffu, iS, d);
+        if (lane >= d) { iB += ob; iS += os; }
+      }
+      if (lane == 31) { sm.wMB[wid] = iB; sm.wMS[wid] = iS; }
+      exB = iB - mB;
+      exS = iS - mS;
+    }
+    gsync<NT>(bar);  // B5: book residual, remainders and marginal totals visible
+
+    // ---- market scalars of step s ---------------------------------------------------------
+    if (trade) last = pstar;
+#pragma unroll
+    for (int h = KS_HISTORY - 1; h > 0; --h) hist[h] = hist[h - 1];
+    hist[0] = last;
+    if (t == 0) {
+      const int pt = trade ? pstar : -1;
+      if (trade) {
+        sump += pstar;
+        trades += 1;
+      }
+      sumv += vstar;
+      lastv = vstar;
+      hash = trace_mix(hash, s, pt, vstar);
+      if (traced && s < P.trace_steps) {
+        int32_t* tr = P.trace + ((size_t)m * P.trace_steps + s) * 2;
+        tr[0] = pt;
+        tr[1] = vstar;
+      }
+    }
+
+    // ---- fills of step s, fused with the orders of step s+1 ------------------------------
+    const bool more = j + 1 < n_steps;
+    const StepRules sr = step_rules(P, s + 1, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+    if (trade) {
+      const int Rb = sm.rem[0], Rs = sm.rem[1];
+      int preB = (int)(exB + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMB[lane] : 0u));
+      int preS = (int)(exS + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMS[lane] : 0u));
+#pragma unroll
+      for (int k = 0; k < AK; ++k) {
+        uint32_t sl = slot[k];
+        const int q = (int)w_qty(sl);
+        const bool sell = w_sell(sl) != 0u;
+        const int d = fill_dist(sl, p_lo, p_hi);
+        const int pre = sell ? preS : preB;
+        const int R = sell ? Rs : Rb;
+        const int fm = min(max(R - pre, 0), q);
+        const int f = q == 0 ? 0 : (d > 0 ? q : (d == 0 ? fm : 0));
+        const int adv = (q != 0 && d == 0) ? q : 0;
+        preS += sell ? adv : 0;
+        preB += sell ? 0 : adv;
+        if (f) {
+          sm.inv[k * NT + t] += sell ? -f : f;
+          sm.cash[k * NT + t] += (int64_t)(sell ? pstar : -pstar) * f;
+        }
+        sl -= (uint32_t)f;
+        if (!carry) sl &= W_STATIC;
+        if (more) sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+        slot[k] = sl;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < AK; ++k) {
+        uint32_t sl = slot[k];
+        if (!carry) sl &= W_STATIC;
+        if (more) sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+        slot[k] = sl;
+      }
+    }
+  }
+
+  // ---- store ---------------------------------------------------------------------------
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < AK; k += 4) {
+      *reinterpret_cast<uint4*>(P.slot + aoff + a0 + k) = make_uint4(slot[k], slot[k + 1], slot[k + 2], slot[k + 3]);
+      *reinterpret_cast<int4*>(P.inv + aoff + a0 + k) =
+          make_int4(sm.inv[(k + 0) * NT + t], sm.inv[(k + 1) * NT + t], sm.inv[(k + 2) * NT + t],
+                    sm.inv[(k + 3) * NT + t]);
+      longlong2 c0, c1;
+      c0.x = sm.cash[(k + 0) * NT + t];
+      c0.y = sm.cash[(k + 1) * NT + t];
+      c1.x = sm.cash[(k + 2) * NT + t];
+      c1.y = sm.cash[(k + 3) * NT + t];
+      *reinterpret_cast<longlong2*>(P.cash + aoff + a0 + k) = c0;
+      *reinterpret_cast<longlong2*>(P.cash + aoff + a0 + k + 2) = c1;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < AK; ++k) {
+      const int a = a0 + k;
+      if (a < A) {
+        P.slot[aoff + a] = slot[k];
+        P.inv[aoff + a] = sm.inv[k * NT + t];
+        P.cash[aoff + a] = sm.cash[k * NT + t];
+      }
+    }
+  }
+  if (t == 0) {
+    int32_t* mo = P.mi32 + (size_t)m * MI32_STRIDE;
+    mo[MI_LAST] = last;
+#pragma unroll
+    for (int j = 0; j < KS_HISTORY; ++j) mo[MI_HIST + j] = hist[j];
+    mo[MI_TRADES] = trades;
+    mo[MI_LASTV] = lastv;
+    int64_t* m64 = P.mi64 + (size_t)m * MI64_STRIDE;
+    m64[MI_SUMP] = sump;
+    m64[MI_SUMV] = sumv;
+    m64[MI_HASH] = (int64_t)hash;
+  }
+  gsync<NT>(bar);  // shared memory is reused by the group's next market
+}
+
+}  // namespace ks

@@ -2,9 +2,10 @@
 #include "ks_plain.cuh"
 
 namespace ks {
-#define KS_VARIANT(NT, AK)                                                                   \
-  PlainVariant { NT, AK, &launch_plain<NT, AK>, (const void*)&plain_kernel<NT, AK, false>, \
-                 (const void*)&plain_kernel<NT, AK, true> }
-extern const PlainVariant kPlainNT128[5] = {KS_VARIANT(128, 1), KS_VARIANT(128, 2), KS_VARIANT(128, 4),
-                                        KS_VARIANT(128, 8), KS_VARIANT(128, 16)};
+#define KS_VARIANT(NT, AK, AG, OCC) \
+  PlainVariant { NT, AK, AG, OCC, &launch_plain<NT, AK, AG, OCC>, (const void*)&plain_kernel<NT, AK, AG, OCC> }
+#define KS_VARIANTS_AK(NT, AK) KS_VARIANT(NT, AK, false, 0), KS_VARIANT(NT, AK, false, 1)
+extern const PlainVariant kPlainNT128[] = {KS_VARIANTS_AK(128, 1), KS_VARIANTS_AK(128, 2), KS_VARIANTS_AK(128, 4),
+                                       KS_VARIANTS_AK(128, 8), KS_VARIANTS_AK(128, 16)};
+extern const int kPlainNT128Count = sizeof(kPlainNT128) / sizeof(kPlainNT128[0]);
 }  // namespace ks

@@ -2,9 +2,10 @@
 #include "ks_plain.cuh"
 
 namespace ks {
-#define KS_VARIANT(NT, AK)                                                                   \
-  PlainVariant { NT, AK, &launch_plain<NT, AK>, (const void*)&plain_kernel<NT, AK, false>, \
-                 (const void*)&plain_kernel<NT, AK, true> }
-extern const PlainVariant kPlainNT512[5] = {KS_VARIANT(512, 1), KS_VARIANT(512, 2), KS_VARIANT(512, 4),
-                                        KS_VARIANT(512, 8), KS_VARIANT(512, 16)};
+#define KS_VARIANT(NT, AK, AG, OCC) \
+  PlainVariant { NT, AK, AG, OCC, &launch_plain<NT, AK, AG, OCC>, (const void*)&plain_kernel<NT, AK, AG, OCC> }
+#define KS_VARIANTS_AK(NT, AK) KS_VARIANT(NT, AK, false, 0), KS_VARIANT(NT, AK, false, 1)
+extern const PlainVariant kPlainNT512[] = {KS_VARIANTS_AK(512, 1), KS_VARIANTS_AK(512, 2), KS_VARIANTS_AK(512, 4),
+                                       KS_VARIANTS_AK(512, 8), KS_VARIANTS_AK(512, 16), KS_VARIANT(512, 8, true, 0), KS_VARIANT(512, 16, true, 0)};
+extern const int kPlainNT512Count = sizeof(kPlainNT512) / sizeof(kPlainNT512[0]);
 }  // namespace ks

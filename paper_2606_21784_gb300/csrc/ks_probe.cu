@@ -1,0 +1,80 @@
+// ks_probe.cu -- roofline probe kernels (see kineticsim_probe.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kineticsim_probe.h"
+#include "ks_device.cuh"
+
+namespace ks {
+
+constexpr int PROBE_THREADS = 256;
+
+// Eight red.shared.add.u32 per iteration; lane l of every warp always hits
+// bank l, so no two lanes of a warp conflict.
+__global__ void __launch_bounds__(PROBE_THREADS) probe_smem_red(uint32_t iters, uint64_t* sink) {
+  __shared__ uint32_t buf[8][PROBE_THREADS];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) buf[j][threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&buf[j][threadIdx.x], it + (uint32_t)j);
+  }
+  __syncthreads();
+  uint64_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc += buf[j][threadIdx.x];
+  sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = acc;
+}
+
+// Eight independent chains acc = lo32(acc) * C + acc (one mad.wide.u32 each).
+__global__ void __launch_bounds__(PROBE_THREADS) probe_mul_wide(uint32_t iters, uint64_t* sink) {
+  uint64_t acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = (uint64_t)(threadIdx.x + 977u * j + blockIdx.x);
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = (uint64_t)(uint32_t)acc[j] * (uint64_t)PH_MA + acc[j];
+  }
+  uint64_t x = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x ^= acc[j];
+  sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = x;
+}
+
+// The persistent kernel's per-agent draw (StepKey + step_draw), one block per iteration.
+__global__ void __launch_bounds__(PROBE_THREADS) probe_philox(uint32_t iters, uint64_t* sink) {
+  const StepKey sk = step_key(7u, blockIdx.x, 0u, 0x1234567u, 0x89abcdefu);
+  uint32_t x = 0;
+  const uint32_t base = threadIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const uint4 w = step_draw(sk, base + it * PROBE_THREADS);
+    x ^= w.x ^ w.y ^ w.z ^ w.w;
+  }
+  sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = x;
+}
+
+}  // namespace ks
+
+extern "C" ks_status ks_probe(int kind, uint32_t blocks, uint32_t iters, void* sink, void* stream, double* ops) {
+  if (!sink || !ops || blocks == 0) return KS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double lanes = (double)blocks * ks::PROBE_THREADS * (double)iters;
+  switch (kind) {
+    case KS_PROBE_SMEM_RED:
+      ks::probe_smem_red<<<blocks, ks::PROBE_THREADS, 0, st>>>(iters, (uint64_t*)sink);
+      *ops = lanes * 8.0;
+      break;
+    case KS_PROBE_MUL_WIDE:
+      ks::probe_mul_wide<<<blocks, ks::PROBE_THREADS, 0, st>>>(iters, (uint64_t*)sink);
+      *ops = lanes * 8.0;
+      break;
+    case KS_PROBE_PHILOX:
+      ks::probe_philox<<<blocks, ks::PROBE_THREADS, 0, st>>>(iters, (uint64_t*)sink);
+      *ops = lanes;
+      break;
+    default:
+      return KS_ERR_INVALID_ARG;
+  }
+  return cudaGetLastError() == cudaSuccess ? KS_OK : KS_ERR_CUDA;
+}

@@ -28,7 +28,8 @@ _STATUS = {0: "KS_OK", 1: "KS_ERR_INVALID_ARG", 2: "KS_ERR_WORKSPACE_TOO_SMALL",
 # every entry point declared in include/kineticsim.h
 EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_state", "ks_write_state",
            "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
-           "ks_last_error", "ks_version")
+           "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
+           "ks_get_batch_info", "ks_batch_variants")
 
 
 class KsError(RuntimeError):
@@ -71,7 +72,18 @@ class ks_state_view(ctypes.Structure):
 
 class ks_launch(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("agents_per_thread", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("aggregate", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("aggregate", ctypes.c_int32), ("reg_cap", ctypes.c_int32)]
+
+
+class ks_bucket(ctypes.Structure):
+    _fields_ = [("L_max", ctypes.c_int32), ("A_max", ctypes.c_int32), ("group_threads", ctypes.c_int32),
+                ("agents_per_thread", ctypes.c_int32)]
+
+
+class ks_batch_info(ctypes.Structure):
+    _fields_ = [("batched", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("n_items", ctypes.c_int32),
+                ("n_buckets", ctypes.c_int32), ("grid", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -108,6 +120,11 @@ def load(build_if_missing: bool = True):
         "ks_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "ks_last_error": ([], ctypes.c_char_p),
         "ks_version": ([], ctypes.c_uint32),
+        "ks_probe": ([ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, vp, vp, P(ctypes.c_double)], ctypes.c_int),
+        "ks_probe_state_io": ([vp, vp, P(ctypes.c_double)], ctypes.c_int),
+        "ks_set_batch_plan": ([vp, ctypes.c_int32, P(ks_bucket), ctypes.c_int32, vp], ctypes.c_int),
+        "ks_get_batch_info": ([vp, P(ks_batch_info)], ctypes.c_int),
+        "ks_batch_variants": ([ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -211,8 +228,9 @@ def ks_error_word(h: int, stream=None) -> int:
     return int(w.value)
 
 
-def ks_set_launch(h: int, threads: int, agents_per_thread: int, ctas_per_sm: int = 0, aggregate: int = 0):
-    l = ks_launch(threads, agents_per_thread, ctas_per_sm, aggregate)
+def ks_set_launch(h: int, threads: int, agents_per_thread: int, ctas_per_sm: int = 0, aggregate: int = 0,
+                  reg_cap: int = 0):
+    l = ks_launch(threads, agents_per_thread, ctas_per_sm, aggregate, reg_cap)
     _check(load().ks_set_launch(h, ctypes.byref(l)), "ks_set_launch")
 
 
@@ -220,7 +238,42 @@ def ks_get_launch(h: int) -> dict:
     l = ks_launch()
     _check(load().ks_get_launch(h, ctypes.byref(l)), "ks_get_launch")
     return dict(threads=l.threads, agents_per_thread=l.agents_per_thread, ctas_per_sm=l.ctas_per_sm,
-                aggregate=l.aggregate)
+                aggregate=l.aggregate, reg_cap=l.reg_cap)
+
+
+def ks_set_batch_plan(h: int, cta_threads: int, buckets, stream=None):
+    """buckets: sequence of (L_max, A_max, group_threads, agents_per_thread)."""
+    arr = (ks_bucket * len(buckets))(*[ks_bucket(*map(int, b)) for b in buckets])
+    _check(load().ks_set_batch_plan(h, int(cta_threads), arr, len(buckets), _stream_ptr(stream)), "ks_set_batch_plan")
+
+
+def ks_get_batch_info(h: int) -> dict:
+    i = ks_batch_info()
+    _check(load().ks_get_batch_info(h, ctypes.byref(i)), "ks_get_batch_info")
+    return {f: getattr(i, f) for f, _ in ks_batch_info._fields_ if f != "pad_"}
+
+
+def ks_batch_variants(cta_threads: int):
+    n = ctypes.c_int32(0)
+    _check(load().ks_batch_variants(int(cta_threads), None, 0, ctypes.byref(n)), "ks_batch_variants")
+    buf = (ctypes.c_int32 * (2 * n.value))()
+    _check(load().ks_batch_variants(int(cta_threads), buf, n.value, ctypes.byref(n)), "ks_batch_variants")
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+
+KS_PROBE_SMEM_RED, KS_PROBE_MUL_WIDE, KS_PROBE_PHILOX = 0, 1, 2
+
+
+def ks_probe(kind: int, blocks: int, iters: int, sink_ptr: int, stream=None) -> float:
+    ops = ctypes.c_double(0)
+    _check(load().ks_probe(kind, blocks, iters, sink_ptr, _stream_ptr(stream), ctypes.byref(ops)), "ks_probe")
+    return float(ops.value)
+
+
+def ks_probe_state_io(h: int, stream=None) -> float:
+    b = ctypes.c_double(0)
+    _check(load().ks_probe_state_io(h, _stream_ptr(stream), ctypes.byref(b)), "ks_probe_state_io")
+    return float(b.value)
 
 
 def ks_destroy(h: int):
@@ -284,11 +337,17 @@ class Ensemble:
     def step(self, n: int, stream=None):
         ks_step_n(self.handle, n, stream)
 
-    def set_launch(self, threads, agents_per_thread, ctas_per_sm=0, aggregate=0):
-        ks_set_launch(self.handle, threads, agents_per_thread, ctas_per_sm, aggregate)
+    def set_launch(self, threads, agents_per_thread, ctas_per_sm=0, aggregate=0, reg_cap=0):
+        ks_set_launch(self.handle, threads, agents_per_thread, ctas_per_sm, aggregate, reg_cap)
 
     def get_launch(self):
         return ks_get_launch(self.handle)
+
+    def set_batch_plan(self, cta_threads, buckets, stream=None):
+        ks_set_batch_plan(self.handle, cta_threads, buckets, stream)
+
+    def batch_info(self):
+        return ks_get_batch_info(self.handle)
 
     def sync(self, timeout_ms: int = 0, stream=None) -> int:
         return ks_sync(self.handle, stream, timeout_ms)
