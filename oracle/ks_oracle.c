@@ -22,8 +22,11 @@
  *  - Philox4x32-10 is written from Salmon, Moraes, Dror and Shaw, "Parallel
  *    random numbers: as easy as 1, 2, 3", SC'11.
  *  - The trace hash uses the SplitMix64 finaliser printed in Sec. III-F.
- *  - The MLP policy forward/backward are plain fp64 loops (behaviour-cloning
- *    loss: cross-entropy on side and offset, squared error on log-quantity).
+ *  - The MLP policy (32 -> 64 -> 64 -> 3 side + 33 offset + 1 log-qty logits,
+ *    ReLU) forward and backward are plain fp64 loops; the behaviour-cloning
+ *    loss is cross-entropy on side and offset plus squared error on
+ *    log-quantity.  Features, sampling and the loss are the build's readings
+ *    of the learned-agent configuration (the paper has no learned agents).
  *
  * The clearing loops are the definitions evaluated directly; the allocation is
  * a greedy walk over price levels.  No blocking, fusion or reordering.
@@ -219,6 +222,184 @@ int ko_allocate(int32_t L, int32_t A, const int32_t* side, const int32_t* tick,
   return (buy_left == 0 && left == 0) ? 0 : -4;
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* MLP policy (fp64).  Parameter vector layout:                              */
+/*   W1[64][32], b1[64], W2[64][64], b2[64], W3[37][64], b3[37].            */
+/* ------------------------------------------------------------------------ */
+#define KO_IN 32
+#define KO_H 64
+#define KO_OUT 37
+#define KO_NSIDE 3
+#define KO_NOFF 33
+#define KO_OFF_MAX 16
+#define KO_NPARAM (KO_H * KO_IN + KO_H + KO_H * KO_H + KO_H + KO_OUT * KO_H + KO_OUT)
+#define KO_NRAW 18
+
+int32_t ko_mlp_nparam(void) { return KO_NPARAM; }
+
+typedef struct {
+  const double *W1, *b1, *W2, *b2, *W3, *b3;
+} ko_mlp_view;
+
+static ko_mlp_view ko_mlp_split(const double* w) {
+  ko_mlp_view v;
+  v.W1 = w;
+  v.b1 = v.W1 + KO_H * KO_IN;
+  v.W2 = v.b1 + KO_H;
+  v.b2 = v.W2 + KO_H * KO_H;
+  v.W3 = v.b2 + KO_H;
+  v.b3 = v.W3 + KO_OUT * KO_H;
+  return v;
+}
+
+/* One sample: a1 = W1 x + b1, h1 = relu(a1), a2 = W2 h1 + b2, h2 = relu(a2),
+ * z = W3 h2 + b3.  Hidden pre-activations are returned for the backward. */
+static void ko_mlp_fwd1(const ko_mlp_view* v, const double* x, double* a1, double* h1, double* a2, double* h2,
+                        double* z) {
+  for (int i = 0; i < KO_H; ++i) {
+    double acc = v->b1[i];
+    for (int k = 0; k < KO_IN; ++k) acc += v->W1[i * KO_IN + k] * x[k];
+    a1[i] = acc;
+    h1[i] = acc > 0.0 ? acc : 0.0;
+  }
+  for (int i = 0; i < KO_H; ++i) {
+    double acc = v->b2[i];
+    for (int k = 0; k < KO_H; ++k) acc += v->W2[i * KO_H + k] * h1[k];
+    a2[i] = acc;
+    h2[i] = acc > 0.0 ? acc : 0.0;
+  }
+  for (int i = 0; i < KO_OUT; ++i) {
+    double acc = v->b3[i];
+    for (int k = 0; k < KO_H; ++k) acc += v->W3[i * KO_H + k] * h2[k];
+    z[i] = acc;
+  }
+}
+
+/* Logits of n samples: X [n][32] -> Z [n][37]. */
+int ko_mlp_forward(const double* w, const double* X, int64_t n, double* Z) {
+  ko_mlp_view v = ko_mlp_split(w);
+  double a1[KO_H], h1[KO_H], a2[KO_H], h2[KO_H];
+  for (int64_t r = 0; r < n; ++r) ko_mlp_fwd1(&v, X + r * KO_IN, a1, h1, a2, h2, Z + r * KO_OUT);
+  return 0;
+}
+
+/* Behaviour-cloning loss of n samples and its gradient.  Labels per sample:
+ * side in {0 buy, 1 sell, 2 pass}, offset index in [0, 33) (tick offset + 16),
+ * target log-quantity.  loss = mean over samples of
+ *   -log softmax(z[0:3])[side] - log softmax(z[3:36])[offset] + (z[36] - logq)^2.
+ * grad (length ko_mlp_nparam) receives d loss / d w. */
+int ko_mlp_loss_grad(const double* w, const double* X, const int32_t* side, const int32_t* offset,
+                     const double* logq, int64_t n, double* loss, double* grad) {
+  if (n <= 0) return -1;
+  ko_mlp_view v = ko_mlp_split(w);
+  for (int i = 0; i < KO_NPARAM; ++i) grad[i] = 0.0;
+  double* gW1 = grad;
+  double* gb1 = gW1 + KO_H * KO_IN;
+  double* gW2 = gb1 + KO_H;
+  double* gb2 = gW2 + KO_H * KO_H;
+  double* gW3 = gb2 + KO_H;
+  double* gb3 = gW3 + KO_OUT * KO_H;
+  double a1[KO_H], h1[KO_H], a2[KO_H], h2[KO_H], z[KO_OUT], dz[KO_OUT], dh2[KO_H], dh1[KO_H];
+  double total = 0.0;
+  const double inv_n = 1.0 / (double)n;
+  for (int64_t r = 0; r < n; ++r) {
+    const double* x = X + r * KO_IN;
+    ko_mlp_fwd1(&v, x, a1, h1, a2, h2, z);
+    /* softmax cross-entropy on the side head */
+    double mx = z[0];
+    for (int i = 1; i < KO_NSIDE; ++i) mx = z[i] > mx ? z[i] : mx;
+    double se = 0.0;
+    for (int i = 0; i < KO_NSIDE; ++i) se += exp(z[i] - mx);
+    total += -(z[side[r]] - mx - log(se));
+    for (int i = 0; i < KO_NSIDE; ++i) dz[i] = exp(z[i] - mx) / se - (i == side[r] ? 1.0 : 0.0);
+    /* softmax cross-entropy on the offset head */
+    mx = z[KO_NSIDE];
+    for (int i = 1; i < KO_NOFF; ++i) mx = z[KO_NSIDE + i] > mx ? z[KO_NSIDE + i] : mx;
+    se = 0.0;
+    for (int i = 0; i < KO_NOFF; ++i) se += exp(z[KO_NSIDE + i] - mx);
+    total += -(z[KO_NSIDE + offset[r]] - mx - log(se));
+    for (int i = 0; i < KO_NOFF; ++i)
+      dz[KO_NSIDE + i] = exp(z[KO_NSIDE + i] - mx) / se - (i == offset[r] ? 1.0 : 0.0);
+    /* squared error on log-quantity */
+    const double e = z[KO_OUT - 1] - logq[r];
+    total += e * e;
+    dz[KO_OUT - 1] = 2.0 * e;
+    for (int i = 0; i < KO_OUT; ++i) dz[i] *= inv_n;
+    /* layer 3 */
+    for (int i = 0; i < KO_OUT; ++i) {
+      gb3[i] += dz[i];
+      for (int k = 0; k < KO_H; ++k) gW3[i * KO_H + k] += dz[i] * h2[k];
+    }
+    for (int k = 0; k < KO_H; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < KO_OUT; ++i) acc += v.W3[i * KO_H + k] * dz[i];
+      dh2[k] = a2[k] > 0.0 ? acc : 0.0;
+    }
+    /* layer 2 */
+    for (int i = 0; i < KO_H; ++i) {
+      gb2[i] += dh2[i];
+      for (int k = 0; k < KO_H; ++k) gW2[i * KO_H + k] += dh2[i] * h1[k];
+    }
+    for (int k = 0; k < KO_H; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < KO_H; ++i) acc += v.W2[i * KO_H + k] * dh2[i];
+      dh1[k] = a1[k] > 0.0 ? acc : 0.0;
+    }
+    /* layer 1 */
+    for (int i = 0; i < KO_H; ++i) {
+      gb1[i] += dh1[i];
+      for (int k = 0; k < KO_IN; ++k) gW1[i * KO_IN + k] += dh1[i] * x[k];
+    }
+  }
+  *loss = total * inv_n;
+  return 0;
+}
+
+/* Normalised policy input from the raw integer features of a decision:
+ * raw[0..7]   last eight clearing-tick returns hist[j] - hist[j+1], newest first
+ * raw[8]      the agent's inventory
+ * raw[9]      the market's last executed volume V*
+ * raw[10..13] resting sell quantity at ticks last+1 .. last+4
+ * raw[14..17] resting buy quantity at ticks last-1 .. last-4
+ * x = raw / (8, 256, 8A, 4A) per group, x[18..31] = 0. */
+void ko_mlp_features(const int32_t* raw, int32_t A, double* x) {
+  for (int j = 0; j < 8; ++j) x[j] = (double)raw[j] / 8.0;
+  x[8] = (double)raw[8] / 256.0;
+  x[9] = (double)raw[9] / (8.0 * (double)(A > 0 ? A : 1));
+  for (int j = 10; j < KO_NRAW; ++j) x[j] = (double)raw[j] / (4.0 * (double)(A > 0 ? A : 1));
+  for (int j = KO_NRAW; j < KO_IN; ++j) x[j] = 0.0;
+}
+
+/* Inverse-CDF draw from softmax(z[0..n)) with u = w / 2^32: the smallest i
+ * whose cumulative probability exceeds u (the last index if rounding leaves
+ * none). */
+static int ko_sample(const double* z, int n, uint32_t w) {
+  double mx = z[0];
+  for (int i = 1; i < n; ++i) mx = z[i] > mx ? z[i] : mx;
+  double se = 0.0;
+  for (int i = 0; i < n; ++i) se += exp(z[i] - mx);
+  const double u = (double)w / 4294967296.0;
+  double c = 0.0;
+  for (int i = 0; i < n; ++i) {
+    c += exp(z[i] - mx) / se;
+    if (u < c) return i;
+  }
+  return n - 1;
+}
+
+/* Action of the policy from logits z and the agent's stream-3 draw words:
+ * side from w0, offset index from w1, quantity clamp(round(exp(z[36])), 1, qmax). */
+void ko_mlp_action(const double* z, const uint32_t w[4], int32_t qmax, int32_t* side, int32_t* offset_idx,
+                   int32_t* qty) {
+  *side = ko_sample(z, KO_NSIDE, w[0]);
+  *offset_idx = ko_sample(z + KO_NSIDE, KO_NOFF, w[1]);
+  double q = floor(exp(z[KO_OUT - 1]) + 0.5);
+  if (!(q >= 1.0)) q = 1.0; /* also catches NaN */
+  if (q > (double)qmax) q = (double)qmax;
+  *qty = (int32_t)q;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Market simulation.                                                         */
 /* ------------------------------------------------------------------------ */
@@ -331,11 +512,61 @@ typedef struct {
   const int32_t* qty;
 } ko_replay;
 
+/* Further options of a run (all fields may be zero / NULL).
+ *  mlp_w:      fp64 policy parameters; MLP agents decide with them unless a
+ *              replay is given, in which case the replayed decisions are also
+ *              compared with the policy's (mlp_checked / mlp_mismatch);
+ *  rec_agents: rule decisions of agents a < rec_agents are recorded as
+ *              KO_REC_WORDS int32 each: raw features (KO_NRAW), side,
+ *              offset index (tick - last clamped to [-16, 16], plus 16), qty,
+ *              agent class. */
+#define KO_REC_WORDS (KO_NRAW + 4)
+typedef struct {
+  const double* mlp_w;
+  int32_t rec_agents;
+  int32_t pad_;
+  int32_t* rec_out;
+  int64_t rec_cap;
+  int64_t rec_count;
+  int64_t mlp_checked;
+  int64_t mlp_mismatch;
+} ko_options;
+
+/* Market-level raw features at the start of a step (see ko_mlp_features). */
+static void ko_raw_features(const ko_market_scalars* ms, int32_t L, const int64_t* buy, const int64_t* sell,
+                            int32_t* raw) {
+  for (int j = 0; j < 8; ++j) raw[j] = ms->hist[j] - ms->hist[j + 1];
+  raw[8] = 0;
+  raw[9] = ms->last_v;
+  for (int k = 1; k <= 4; ++k) {
+    int32_t pa = ms->last + k, pb = ms->last - k;
+    raw[9 + k] = (pa >= 0 && pa < L) ? (int32_t)sell[pa] : 0;
+    raw[13 + k] = (pb >= 0 && pb < L) ? (int32_t)buy[pb] : 0;
+  }
+}
+
+/* The policy's decision for agent a at step s (fp64). */
+static void ko_mlp_decide(const ko_params* P, const double* w, uint32_t m, int32_t L, int32_t A, uint32_t s,
+                          int32_t a, const int32_t* raw_mkt, int32_t inv, int32_t last, int32_t* side,
+                          int32_t* tick, int32_t* qty) {
+  int32_t raw[KO_NRAW];
+  memcpy(raw, raw_mkt, sizeof(raw));
+  raw[8] = inv;
+  double x[KO_IN], z[KO_OUT];
+  ko_mlp_features(raw, A, x);
+  ko_mlp_forward(w, x, 1, z);
+  uint32_t u[4];
+  ko_draw(P->seed, s, (uint32_t)a, m, 3u, u);
+  int32_t oi;
+  ko_mlp_action(z, u, P->rb_qmax, side, &oi, qty);
+  *tick = ko_clamp((int64_t)last + (oi - KO_OFF_MAX), 0, L - 1);
+}
+
 /* Run steps [s0, s0 + n) of market m.  trace_p / trace_v (nullable, length n)
  * receive p* (-1 for no trade) and V* per step.  Returns 0 on success. */
 int ko_run_market(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agents* ag,
                   ko_market_scalars* ms, uint32_t s0, uint32_t n, const ko_replay* replay,
-                  int32_t* trace_p, int32_t* trace_v) {
+                  int32_t* trace_p, int32_t* trace_v, ko_options* opt) {
   if (L < 2 || A < 0) return -1;
   int64_t* buy = (int64_t*)calloc((size_t)L, sizeof(int64_t));
   int64_t* sell = (int64_t*)calloc((size_t)L, sizeof(int64_t));
@@ -344,9 +575,24 @@ int ko_run_market(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agent
   int64_t* vol = (int64_t*)malloc(sizeof(int64_t) * (size_t)L);
   int32_t* fill = (int32_t*)malloc(sizeof(int32_t) * (size_t)(A > 0 ? A : 1));
   int rc = 0;
+  int any_mlp = 0;
+  for (int32_t a = 0; a < A; ++a) any_mlp |= ag->mlp[a];
+  const double* mlp_w = opt ? opt->mlp_w : NULL;
+  const int32_t rec_agents = opt ? opt->rec_agents : 0;
   if (!buy || !sell || !dcum || !scum || !vol || !fill) { rc = -2; goto done; }
   for (uint32_t j = 0; j < n; ++j) {
     uint32_t s = s0 + j;
+    /* resting book at the start of the step: the inputs of the policy features */
+    int32_t raw_mkt[KO_NRAW];
+    if (any_mlp || rec_agents > 0) {
+      for (int32_t p = 0; p < L; ++p) { buy[p] = 0; sell[p] = 0; }
+      for (int32_t a = 0; a < A; ++a) {
+        if (ag->qty[a] <= 0) continue;
+        if (ag->side[a] == 0) buy[ag->tick[a]] += ag->qty[a];
+        else sell[ag->tick[a]] += ag->qty[a];
+      }
+      ko_raw_features(ms, L, buy, sell, raw_mkt);
+    }
     /* 1-2. cancellation of working orders, then decisions of empty agents */
     for (int32_t a = 0; a < A; ++a) {
       uint32_t w[4];
@@ -354,18 +600,42 @@ int ko_run_market(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agent
       if (P->carry_book && ag->qty[a] > 0 && w[0] < P->cancel_thresh) ag->qty[a] = 0;
       if (ag->qty[a] > 0) continue;
       if (ag->mlp[a]) {
-        if (!replay) { rc = -5; goto done; }
-        size_t e = (size_t)j * (size_t)A + (size_t)a;
-        int32_t sd = replay->side[e];
+        int32_t sd, tk, q;
+        if (replay) {
+          size_t e = (size_t)j * (size_t)A + (size_t)a;
+          sd = replay->side[e];
+          tk = replay->tick[e];
+          q = replay->qty[e];
+          if (sd < 0 || sd > 2 || (sd < 2 && (tk < 0 || tk >= L || q <= 0))) { rc = -6; goto done; }
+          if (mlp_w) {
+            int32_t os, ot, oq;
+            ko_mlp_decide(P, mlp_w, m, L, A, s, a, raw_mkt, ag->inv[a], ms->last, &os, &ot, &oq);
+            opt->mlp_checked += 1;
+            if (os != sd || (sd < 2 && (ot != tk || oq != q))) opt->mlp_mismatch += 1;
+          }
+        } else {
+          if (!mlp_w) { rc = -5; goto done; }
+          ko_mlp_decide(P, mlp_w, m, L, A, s, a, raw_mkt, ag->inv[a], ms->last, &sd, &tk, &q);
+        }
         if (sd == 2) continue; /* pass: no order this step */
-        if (sd < 0 || sd > 1 || replay->tick[e] < 0 || replay->tick[e] >= L ||
-            replay->qty[e] <= 0) { rc = -6; goto done; }
         ag->side[a] = sd;
-        ag->tick[a] = replay->tick[e];
-        ag->qty[a] = replay->qty[e];
+        ag->tick[a] = tk;
+        ag->qty[a] = q;
         continue;
       }
       ko_decide_rule(P, L, ag->atype[a], ms, w, &ag->side[a], &ag->tick[a], &ag->qty[a]);
+      if (a < rec_agents && opt->rec_out && opt->rec_count < opt->rec_cap) {
+        int32_t* r = opt->rec_out + opt->rec_count * KO_REC_WORDS;
+        memcpy(r, raw_mkt, sizeof(raw_mkt));
+        r[8] = ag->inv[a];
+        int32_t off = ag->tick[a] - ms->last;
+        off = off < -KO_OFF_MAX ? -KO_OFF_MAX : (off > KO_OFF_MAX ? KO_OFF_MAX : off);
+        r[KO_NRAW + 0] = ag->side[a];
+        r[KO_NRAW + 1] = off + KO_OFF_MAX;
+        r[KO_NRAW + 2] = ag->qty[a];
+        r[KO_NRAW + 3] = ag->atype[a];
+        opt->rec_count += 1;
+      }
     }
     /* 3. aggregated book of all working orders */
     for (int32_t p = 0; p < L; ++p) { buy[p] = 0; sell[p] = 0; }

@@ -82,6 +82,15 @@ class _Replay(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("side", "tick", "qty")]
 
 
+class _Options(ctypes.Structure):
+    _fields_ = [("mlp_w", ctypes.c_void_p), ("rec_agents", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("rec_out", ctypes.c_void_p), ("rec_cap", ctypes.c_int64), ("rec_count", ctypes.c_int64),
+                ("mlp_checked", ctypes.c_int64), ("mlp_mismatch", ctypes.c_int64)]
+
+
+MLP_IN, MLP_H, MLP_OUT, N_RAW, REC_WORDS = 32, 64, 37, 18, 22
+
+
 class _ClearResult(ctypes.Structure):
     _fields_ = [
         ("vstar", ctypes.c_int64),
@@ -114,8 +123,20 @@ def _load():
             lib.ko_init_market.restype = ctypes.c_int
             lib.ko_run_market.argtypes = [P(Params), ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
                                           P(_Agents), P(MarketScalars), ctypes.c_uint32, ctypes.c_uint32,
-                                          P(_Replay), ctypes.c_void_p, ctypes.c_void_p]
+                                          P(_Replay), ctypes.c_void_p, ctypes.c_void_p, P(_Options)]
             lib.ko_run_market.restype = ctypes.c_int
+            lib.ko_mlp_nparam.argtypes = []
+            lib.ko_mlp_nparam.restype = ctypes.c_int32
+            lib.ko_mlp_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+            lib.ko_mlp_forward.restype = ctypes.c_int
+            lib.ko_mlp_loss_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_double), ctypes.c_void_p]
+            lib.ko_mlp_loss_grad.restype = ctypes.c_int
+            lib.ko_mlp_features.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+            lib.ko_mlp_features.restype = None
+            lib.ko_mlp_action.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32),
+                                          P(ctypes.c_int32), P(ctypes.c_int32)]
+            lib.ko_mlp_action.restype = None
             _lib = lib
     return _lib
 
@@ -250,11 +271,16 @@ def init_market(params: dict, m: int, L: int, A: int) -> Market:
     return mk
 
 
-def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trace: bool = True):
+def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trace: bool = True, mlp_w=None,
+               rec_agents: int = 0, rec_cap: int = 0, stats: dict | None = None):
     """Advance ``mk`` in place over steps [s0, s0+n).  Returns (trace_p, trace_v) or None.
 
     ``replay``: optional dict of int32 arrays ``side``, ``tick``, ``qty`` of shape (n, A)
-    holding the decisions of MLP agents (side 2 = pass).
+    holding the decisions of MLP agents (side 2 = pass).  ``mlp_w``: fp64 policy
+    parameters (MLP agents decide with them, or are checked against them when
+    replaying).  ``rec_agents`` / ``rec_cap``: record rule decisions of agents
+    a < rec_agents.  ``stats`` (optional dict) receives ``records`` (int32
+    [count, 22]), ``mlp_checked`` and ``mlp_mismatch``.
     """
     P = make_params(params)
     tp = np.zeros(max(n, 1), np.int32)
@@ -267,16 +293,96 @@ def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trac
             assert a.size == n * mk.A
         keep = arrs
         rp = ctypes.byref(_Replay(*[_ptr(a) for a in arrs]))
+    opt = _Options()
+    if mlp_w is not None:
+        w = np.ascontiguousarray(mlp_w, dtype=np.float64)
+        assert w.size == mlp_nparam()
+        keep.append(w)
+        opt.mlp_w = _ptr(w)
+    rec = None
+    if rec_agents > 0 and rec_cap > 0:
+        rec = np.zeros((rec_cap, REC_WORDS), np.int32)
+        opt.rec_agents = rec_agents
+        opt.rec_out = _ptr(rec)
+        opt.rec_cap = rec_cap
     rc = _load().ko_run_market(ctypes.byref(P), mk.m, mk.L, mk.A, ctypes.byref(mk._agents()), ctypes.byref(mk.sc),
-                               s0, n, rp, _ptr(tp) if want_trace else None, _ptr(tv) if want_trace else None)
+                               s0, n, rp, _ptr(tp) if want_trace else None, _ptr(tv) if want_trace else None,
+                               ctypes.byref(opt))
     del keep
     if rc != 0:
         raise ValueError(f"ko_run_market failed: {rc}")
+    if stats is not None:
+        stats["records"] = rec[: opt.rec_count] if rec is not None else np.zeros((0, REC_WORDS), np.int32)
+        stats["mlp_checked"] = int(opt.mlp_checked)
+        stats["mlp_mismatch"] = int(opt.mlp_mismatch)
     return (tp[:n], tv[:n]) if want_trace else None
 
 
-def simulate(params: dict, m: int, L: int, A: int, steps: int, replay=None):
+# ---------------------------------------------------------------------------
+# MLP policy (fp64)
+# ---------------------------------------------------------------------------
+def mlp_nparam() -> int:
+    return int(_load().ko_mlp_nparam())
+
+
+def mlp_pack(W1, b1, W2, b2, W3, b3) -> np.ndarray:
+    """fp64 parameter vector: W1[64,32], b1, W2[64,64], b2, W3[37,64], b3."""
+    return np.concatenate([np.asarray(a, np.float64).ravel() for a in (W1, b1, W2, b2, W3, b3)])
+
+
+def mlp_unpack(w):
+    w = np.asarray(w, np.float64)
+    shapes = [(MLP_H, MLP_IN), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_OUT, MLP_H), (MLP_OUT,)]
+    out, i = [], 0
+    for sh in shapes:
+        k = int(np.prod(sh))
+        out.append(w[i:i + k].reshape(sh))
+        i += k
+    return out
+
+
+def mlp_forward(w, X) -> np.ndarray:
+    """Logits [n, 37] of feature rows X [n, 32] (fp64)."""
+    w = np.ascontiguousarray(w, np.float64)
+    X = np.ascontiguousarray(X, np.float64)
+    Z = np.zeros((X.shape[0], MLP_OUT), np.float64)
+    _load().ko_mlp_forward(_ptr(w), _ptr(X), X.shape[0], _ptr(Z))
+    return Z
+
+
+def mlp_loss_grad(w, X, side, offset, logq):
+    """Mean behaviour-cloning loss and its gradient (fp64)."""
+    w = np.ascontiguousarray(w, np.float64)
+    X = np.ascontiguousarray(X, np.float64)
+    side = np.ascontiguousarray(side, np.int32)
+    offset = np.ascontiguousarray(offset, np.int32)
+    logq = np.ascontiguousarray(logq, np.float64)
+    g = np.zeros(mlp_nparam(), np.float64)
+    loss = ctypes.c_double(0)
+    rc = _load().ko_mlp_loss_grad(_ptr(w), _ptr(X), _ptr(side), _ptr(offset), _ptr(logq), X.shape[0],
+                                  ctypes.byref(loss), _ptr(g))
+    if rc != 0:
+        raise ValueError(rc)
+    return float(loss.value), g
+
+
+def mlp_features(raw, A: int) -> np.ndarray:
+    raw = np.ascontiguousarray(raw, np.int32)
+    x = np.zeros(MLP_IN, np.float64)
+    _load().ko_mlp_features(_ptr(raw), int(A), _ptr(x))
+    return x
+
+
+def mlp_action(z, words, qmax: int):
+    z = np.ascontiguousarray(z, np.float64)
+    w = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in words])
+    sd, oi, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _load().ko_mlp_action(_ptr(z), w, int(qmax), ctypes.byref(sd), ctypes.byref(oi), ctypes.byref(q))
+    return int(sd.value), int(oi.value), int(q.value)
+
+
+def simulate(params: dict, m: int, L: int, A: int, steps: int, replay=None, mlp_w=None):
     """Initialise market m and run ``steps`` steps from step 0; returns (market, trace_p, trace_v)."""
     mk = init_market(params, m, L, A)
-    tp, tv = run_market(params, mk, 0, steps, replay=replay)
+    tp, tv = run_market(params, mk, 0, steps, replay=replay, mlp_w=mlp_w)
     return mk, tp, tv

@@ -28,6 +28,13 @@ MUTANTS = {
     "mixer_shift": ("z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;", "z = (z ^ (z >> 28)) * 0x94d049bb133111ebull;"),
     "agent_priority_reversed": ("for (int32_t a = 0; a < A; ++a) {\n    if (qty[a] <= 0) continue;\n    order[",
                                 "for (int32_t a = A - 1; a >= 0; --a) {\n    if (qty[a] <= 0) continue;\n    order["),
+    "mlp_relu_mask_dropped": ("dh2[k] = a2[k] > 0.0 ? acc : 0.0;", "dh2[k] = acc;"),
+    "mlp_w2_transposed": ("acc += v->W2[i * KO_H + k] * h1[k];", "acc += v->W2[k * KO_H + i] * h1[k];"),
+    "mlp_w1_transposed_back": ("acc += v.W2[i * KO_H + k] * dh2[i];", "acc += v.W2[k * KO_H + i] * dh2[i];"),
+    "mlp_bias_dropped": ("double acc = v->b3[i];", "double acc = 0.0;"),
+    "mlp_mse_factor": ("dz[KO_OUT - 1] = 2.0 * e;", "dz[KO_OUT - 1] = e;"),
+    "mlp_sample_le": ("if (u < c) return i;", "if (u <= c) return i;"),
+    "mlp_qty_rounding": ("double q = floor(exp(z[KO_OUT - 1]) + 0.5);", "double q = floor(exp(z[KO_OUT - 1]));"),
 }
 
 
@@ -43,6 +50,7 @@ def test_pins_catch_mutant(name):
         subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", so, c, "-lm"], check=True)
         env = dict(os.environ, KS_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_mlp_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
