@@ -45,15 +45,20 @@ def parse():
     ap.add_argument("--no-probes", action="store_true")
     ap.add_argument("--sim-steps", type=int, default=0, help="override S (profiling small cases)")
     ap.add_argument("--markets", type=int, default=0, help="override M (profiling small cases)")
+    ap.add_argument("--launch", default="", help="threads,agents_per_thread,reg_cap (skip the autotuner)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / learned comparison runs")
     return ap.parse_args()
 
 
+PLAIN_SOURCES = ("ks_device.cuh", "ks_internal.h", "ks_market.cuh", "ks_plain.cuh")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources; ncu counters are only valid for the kernel they were taken on."""
+    """Hash of the plain kernel's sources; ncu counters are only valid for the kernel they were taken on."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2606_21784_gb300", "csrc")
     for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")):
+        if fn in PLAIN_SOURCES or fn.startswith("ks_plain_nt"):
             h.update(fn.encode())
             h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]
@@ -225,6 +230,45 @@ def time_probe(ks, kind, blocks, iters, sink, stream, reps=3):
     return ops / (best / 1e3)
 
 
+def _time_ensemble(ens, steps, stream):
+    import torch
+    ens.step(max(1, steps // 10), stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step(steps, stream)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def compare_forms(ks, workloads, stream, plain_rate):
+    """Throughput of the other forms of the method on the same GPU, beside the
+    plain persistent kernel: the batched uneven ensemble (one launch, default
+    and cached tuned plan) and the learned-agent ensembles when built."""
+    import numpy as np
+    out = {"plain_mix_8192": {"events_per_s": plain_rate}}
+    w = workloads.workload("batched_20000")
+    L, A = workloads.sizes(w)
+    steps = 200
+    ens = ks.Ensemble(w, L=L, A=A)
+    ev = float(A.astype(np.int64).sum()) * steps
+    info = ens.batch_info()
+    out["batched_20000"] = {"events_per_s": ev / _time_ensemble(ens, steps, stream), "steps": steps,
+                            "plan": "default", "items": info["n_items"], "buckets": info["n_buckets"]}
+    try:
+        from paper_2606_21784_gb300 import autotune
+        plan = autotune.tune_batched(w, L, A)
+        ens.set_batch_plan(plan["cta_threads"], plan["buckets"])
+        out["batched_20000_tuned"] = {"events_per_s": ev / _time_ensemble(ens, steps, stream), "steps": steps,
+                                      "cta_threads": plan["cta_threads"]}
+    except Exception as e:  # the tuned plan is optional; the default plan was measured above
+        out["batched_20000_tuned"] = {"error": str(e)[:200]}
+    ens.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -245,6 +289,12 @@ def run_ours(args):
     w = sharding.shard(w, rank, world)
     S = int(w["S"])
     ens = ks.Ensemble(w)
+    if args.launch:
+        nt, ak, rc = (int(x) for x in args.launch.split(","))
+        ens.set_launch(nt, ak, reg_cap=rc)
+    else:
+        from paper_2606_21784_gb300 import autotune
+        autotune.apply(ens, w)
     launch = ens.get_launch()
     L, A = ens.L, ens.A
     events_per_step = float(A.astype(np.int64).sum()) * S
@@ -349,6 +399,9 @@ def run_ours(args):
             rooflines["state_io_hbm"] = {"achieved": probes["state_io_gbs"], "peak": hbm, "unit": "GB/s",
                                          "frac": probes["state_io_gbs"] / hbm,
                                          "note": "zero-step launch: load + store of 32 B per agent"}
+        forms = {}
+        if not args.no_forms and world == 1:
+            forms = compare_forms(ks, workloads, stream, ev_rate_launch)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             v, cores, sample, _ = oracle_sample(w, 2)
@@ -369,6 +422,7 @@ def run_ours(args):
             "rooflines": rooflines,
             "probes": probes,
             "cpu_baseline": cpu,
+            "forms": forms,
             "clocks": clocks,
             "paper_context": {"value": 5.47e10, "hardware": "RTX 5090 (sm_120), L=128, S=500, M=8192, A=1024"},
         }
