@@ -255,6 +255,29 @@ ks_status ks_destroy(ks_ensemble* e);
 const char* ks_status_string(ks_status s);
 const char* ks_last_error(void);
 
+/*
+ * Agent policy (learned agents).  A 32 -> 64 -> 64 -> 37 ReLU network: logits
+ * 0-2 are the side (buy, sell, pass), 3-35 the tick offset -16..+16 relative to
+ * the last clearing tick, 36 the log-quantity.  Parameter blob (device memory,
+ * 16-byte aligned, KS_MLP_PARAM_BYTES bytes):
+ *   offset     0: W1 bf16 [64][32]  (row = output unit, column = input)
+ *   offset  4096: W2 bf16 [64][64]
+ *   offset 12288: W3 bf16 [37][64]
+ *   offset 17024: b1 f32 [64], 17280: b2 f32 [64], 17536: b3 f32 [37]
+ * Inputs (fp32): the last eight clearing-tick returns / 8 (newest first), the
+ * agent's inventory / 256, the market's last executed volume / (8 A), resting
+ * sell quantity at ticks last+1..last+4 and buy quantity at last-1..last-4,
+ * each / (4 A), then 14 zeros.
+ */
+#define KS_MLP_PARAM_BYTES 17696
+
+/* Logits Z [n][37] (fp32) of feature rows X [n][32] (fp32), all device
+ * pointers: layer 1 in FP32, layers 2-3 on the BF16 tcgen05 path the step
+ * loop uses (BF16 weights, activations passed as high + low BF16 parts,
+ * FP32 accumulation).  `err` (device uint32) receives error bits (a bounded
+ * tensor-core wait that gave up). */
+ks_status ks_mlp_forward(const void* params, const float* X, int64_t n, float* Z, uint32_t* err, void* stream);
+
 /* Library version, e.g. 0x000100 for 0.1.0. */
 uint32_t ks_version(void);
 

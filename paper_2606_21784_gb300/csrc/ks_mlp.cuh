@@ -1,0 +1,240 @@
+// ks_mlp.cuh -- the agent policy network on sm_103a tensor cores.
+//
+// Policy 32 -> 64 -> 64 -> 37 (3 side logits, 33 tick-offset logits, 1
+// log-quantity), ReLU hidden layers, BF16 weights, FP32 accumulation.
+// Layer 1 runs in FP32 on the CUDA cores (inside the step loop it is a
+// rank-1 update per agent: only the inventory input differs between the
+// agents of a market).  Layers 2 and 3 are dense 64-wide contractions on the
+// tensor cores: one warpgroup (128 threads) evaluates a tile of 128 agents,
+// thread r owning row r; each layer is a chain of M=128, K=16 tcgen05.mma
+// (kind::f16, BF16 x BF16 -> FP32 in tensor memory) on K-major no-swizzle
+// operands in shared memory, committed to an mbarrier.  The activation
+// operand is passed as a high and a low BF16 part (a = hi + lo, two MMAs per
+// K chunk into the same accumulator), so the only rounding left in the
+// contraction is that of the BF16 weights themselves.  The epilogue reads the
+// accumulator rows with tcgen05.ld and adds the bias.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "kineticsim.h"
+#include "ks_internal.h"
+#include "ks_tc.cuh"
+
+namespace ks {
+
+constexpr int MLP_IN = 32;
+constexpr int MLP_H = 64;
+constexpr int MLP_OUT = 37;
+constexpr int MLP_OUT_PAD = 48;
+constexpr int MLP_NSIDE = 3;
+constexpr int MLP_NOFF = 33;
+constexpr int MLP_OFF_MAX = 16;
+
+// Parameter blob (see kineticsim.h): row-major (out, in) BF16 weights, FP32 biases.
+constexpr uint32_t MLP_OFF_W1 = 0;
+constexpr uint32_t MLP_OFF_W2 = MLP_OFF_W1 + 2 * MLP_H * MLP_IN;
+constexpr uint32_t MLP_OFF_W3 = MLP_OFF_W2 + 2 * MLP_H * MLP_H;
+constexpr uint32_t MLP_OFF_B1 = MLP_OFF_W3 + 2 * MLP_OUT * MLP_H;
+constexpr uint32_t MLP_OFF_B2 = MLP_OFF_B1 + 4 * MLP_H;
+constexpr uint32_t MLP_OFF_B3 = MLP_OFF_B2 + 4 * MLP_H;
+constexpr uint32_t MLP_PARAM_BYTES_RAW = MLP_OFF_B3 + 4 * MLP_OUT;
+static_assert(MLP_PARAM_BYTES_RAW <= KS_MLP_PARAM_BYTES, "parameter blob size");
+
+// Shared memory of the weights (per CTA): W1 as FP32 row-major for the CUDA
+// cores, W2 and W3 as BF16 tensor-core operands.
+constexpr uint32_t MLP_SM_W1 = 0;                               // f32 [64][32]
+constexpr uint32_t MLP_SM_W2 = MLP_SM_W1 + 4 * MLP_H * MLP_IN;    // bf16 [64 x 64] operand layout
+constexpr uint32_t MLP_SM_W3 = MLP_SM_W2 + 2 * MLP_H * MLP_H;     // bf16 [48 x 64], rows 37..47 zero
+constexpr uint32_t MLP_SM_B = MLP_SM_W3 + 2 * MLP_OUT_PAD * MLP_H;  // f32 b1[64] b2[64] b3[48]
+constexpr uint32_t MLP_SM_BYTES = MLP_SM_B + 4 * (MLP_H + MLP_H + MLP_OUT_PAD);
+// Per warpgroup: the hidden activations as two [128 x 64] BF16 operands (high, low part).
+constexpr uint32_t MLP_ACT_HALF = 2 * 128 * MLP_H;
+constexpr uint32_t MLP_ACT_BYTES = 2 * MLP_ACT_HALF;
+constexpr uint32_t MLP_TMEM_COLS = 64;  // per warpgroup
+constexpr uint32_t MLP_WAIT_LIMIT = 1u << 22;
+
+// Loads the blob into the operand layout; all threads of the CTA take part.
+__device__ __forceinline__ void mlp_load_weights(const unsigned char* blob, unsigned char* sw, int tid, int nthr) {
+  const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(blob + MLP_OFF_W1);
+  const __nv_bfloat16* W2 = reinterpret_cast<const __nv_bfloat16*>(blob + MLP_OFF_W2);
+  const __nv_bfloat16* W3 = reinterpret_cast<const __nv_bfloat16*>(blob + MLP_OFF_W3);
+  float* w1f = reinterpret_cast<float*>(sw + MLP_SM_W1);
+  for (int i = tid; i < MLP_H * MLP_IN; i += nthr) w1f[i] = __bfloat162float(W1[i]);
+  for (int i = tid; i < MLP_H * MLP_H; i += nthr) {
+    const int r = i / MLP_H, k = i % MLP_H;
+    *reinterpret_cast<__nv_bfloat16*>(sw + MLP_SM_W2 + cm_offset(r, k, MLP_H)) = W2[i];
+  }
+  for (int i = tid; i < MLP_OUT_PAD * MLP_H; i += nthr) {
+    const int r = i / MLP_H, k = i % MLP_H;
+    *reinterpret_cast<__nv_bfloat16*>(sw + MLP_SM_W3 + cm_offset(r, k, MLP_H)) =
+        r < MLP_OUT ? W3[r * MLP_H + k] : __float2bfloat16(0.0f);
+  }
+  const float* b1 = reinterpret_cast<const float*>(blob + MLP_OFF_B1);
+  const float* b2 = reinterpret_cast<const float*>(blob + MLP_OFF_B2);
+  const float* b3 = reinterpret_cast<const float*>(blob + MLP_OFF_B3);
+  float* sb = reinterpret_cast<float*>(sw + MLP_SM_B);
+  for (int i = tid; i < MLP_H + MLP_H + MLP_OUT_PAD; i += nthr) {
+    float v;
+    if (i < MLP_H) v = b1[i];
+    else if (i < 2 * MLP_H) v = b2[i - MLP_H];
+    else v = (i - 2 * MLP_H) < MLP_OUT ? b3[i - 2 * MLP_H] : 0.0f;
+    sb[i] = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// Barrier of `count` threads that also ORs a predicate over them.
+__device__ __forceinline__ bool named_sync_or(int id, int count, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.b32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return out != 0;
+}
+
+// State of one warpgroup's tile pipeline.
+struct MlpWG {
+  unsigned char* act;  // MLP_ACT_BYTES
+  uint64_t* bar;       // mbarrier (count 1)
+  uint32_t tmem;       // TMEM address of this warpgroup's 64 columns
+  int bar_id;          // named barrier of the 128 threads
+  uint32_t phase;      // parity of the next mbarrier completion
+  bool abort;          // a bounded wait gave up: no further MMAs
+};
+
+// Issues one layer: for each 16-wide K chunk, acc += hi * W and acc += lo * W;
+// then commits the chain to the warpgroup's mbarrier.
+__device__ __forceinline__ void mlp_issue(const MlpWG& g, uint32_t act_addr, uint32_t b_addr, int N) {
+  tc_fence_after();
+  const uint32_t idesc = idesc_bf16_f32(128, N);
+  const uint32_t sbo = (uint32_t)MLP_H * 16;
+  for (int kk = 0; kk < MLP_H / 16; ++kk) {
+    const uint64_t bd = smem_desc(b_addr + 256u * kk, 128u, sbo);
+    mma_bf16(g.tmem, smem_desc(act_addr + 256u * kk, 128u, sbo), bd, idesc, kk > 0);
+    mma_bf16(g.tmem, smem_desc(act_addr + MLP_ACT_HALF + 256u * kk, 128u, sbo), bd, idesc, true);
+  }
+  mma_commit(g.bar);
+}
+
+// Waits for the layer's MMAs; the warpgroup agrees on a timeout.
+__device__ __forceinline__ void mlp_wait(MlpWG& g, uint32_t* err) {
+  bool ok = g.abort ? false : mbar_wait_bounded(g.bar, g.phase, MLP_WAIT_LIMIT);
+  const bool any_fail = named_sync_or(g.bar_id, 128, !ok);
+  if (any_fail && !g.abort) {
+    g.abort = true;
+    if ((threadIdx.x & 127) == 0) atomicOr(err, ERR_MLP_WAIT);
+  }
+  g.phase ^= 1u;
+  tc_fence_after();
+}
+
+// Reads `ncols` accumulator columns of this thread's row (multiple of 16).
+__device__ __forceinline__ void mlp_read(const MlpWG& g, int ncols, float* v) {
+  const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) & 3) * 32u;
+  for (int c = 0; c < ncols; c += 16) tmem_ld16(g.tmem + (lane_base << 16) + (uint32_t)c, v + c);
+  tmem_wait_ld();
+}
+
+// Writes row r of the activation operand: h = hi + lo with hi = bf16(h) and
+// lo = bf16(h - hi), both in the core-matrix layout.
+__device__ __forceinline__ void mlp_store_split(unsigned char* act, int r, const float* h) {
+#pragma unroll
+  for (int kc = 0; kc < MLP_H / 8; ++kc) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float a = h[8 * kc + 2 * j], b = h[8 * kc + 2 * j + 1];
+      hi[j] = pack_bf16x2(a, b);
+      const float ah = __uint_as_float(hi[j] << 16), bh = __uint_as_float(hi[j] & 0xFFFF0000u);
+      lo[j] = pack_bf16x2(a - ah, b - bh);
+    }
+    *reinterpret_cast<uint4*>(act + cm_offset(r, 8 * kc, MLP_H)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(act + MLP_ACT_HALF + cm_offset(r, 8 * kc, MLP_H)) =
+        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+// Layers 2 and 3 of one 128-row tile.  h1: this thread's 64 first-layer
+// activations (after ReLU); z: its 37 logits.  All 128 threads of the
+// warpgroup call it together.
+__device__ __forceinline__ void mlp_tile_forward(MlpWG& g, const unsigned char* sw, const float* h1, float* z,
+                                                 uint32_t* err) {
+  const int r = (int)(threadIdx.x & 127);
+  const float* sb = reinterpret_cast<const float*>(sw + MLP_SM_B);
+  const uint32_t act_addr = smem_u32(g.act);
+  const uint32_t w_addr = smem_u32(sw);
+  float acc[MLP_H];
+  mlp_store_split(g.act, r, h1);
+  fence_async_smem();
+  tc_fence_before();
+  named_sync(g.bar_id, 128);
+  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W2, MLP_H);
+  mlp_wait(g, err);
+  mlp_read(g, MLP_H, acc);
+#pragma unroll
+  for (int i = 0; i < MLP_H; ++i) acc[i] = fmaxf(acc[i] + sb[MLP_H + i], 0.0f);
+  mlp_store_split(g.act, r, acc);  // layer 2 is complete: its operand may be overwritten
+  fence_async_smem();
+  tc_fence_before();
+  named_sync(g.bar_id, 128);
+  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W3, MLP_OUT_PAD);
+  mlp_wait(g, err);
+  mlp_read(g, MLP_OUT_PAD, acc);
+#pragma unroll
+  for (int i = 0; i < MLP_OUT; ++i) z[i] = g.abort ? 0.0f : acc[i] + sb[2 * MLP_H + i];
+  tc_fence_before();
+}
+
+// First layer in FP32 from a full input row (W1 row-major in shared memory).
+__device__ __forceinline__ void mlp_layer1(const unsigned char* sw, const float* x, float* h1) {
+  const float* w1 = reinterpret_cast<const float*>(sw + MLP_SM_W1);
+  const float* b1 = reinterpret_cast<const float*>(sw + MLP_SM_B);
+#pragma unroll 4
+  for (int i = 0; i < MLP_H; ++i) {
+    float a = b1[i];
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) a = fmaf(w1[i * MLP_IN + k], x[k], a);
+    h1[i] = fmaxf(a, 0.0f);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Decision of an MLP agent from its logits and its Philox stream-3 words:
+// inverse-CDF draws of side (w0) and tick offset (w1) from the softmax of
+// their heads, quantity clamp(round(exp(z[36])), 1, qmax).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int mlp_sample(const float* z, int n, uint32_t w) {
+  float mx = z[0];
+  for (int i = 1; i < n; ++i) mx = fmaxf(mx, z[i]);
+  float se = 0.0f;
+  for (int i = 0; i < n; ++i) se += __expf(z[i] - mx);
+  const float u = (float)w * 2.3283064365386963e-10f * se;  // u * sum, compared with the running sum
+  float c = 0.0f;
+  int pick = n - 1;
+  bool found = false;
+  for (int i = 0; i < n; ++i) {
+    c += __expf(z[i] - mx);
+    if (!found && u < c) {
+      pick = i;
+      found = true;
+    }
+  }
+  return pick;
+}
+
+}  // namespace ks

@@ -29,7 +29,10 @@ _STATUS = {0: "KS_OK", 1: "KS_ERR_INVALID_ARG", 2: "KS_ERR_WORKSPACE_TOO_SMALL",
 EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_state", "ks_write_state",
            "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
            "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
-           "ks_get_batch_info", "ks_batch_variants")
+           "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward")
+
+KS_MLP_PARAM_BYTES = 17696
+MLP_IN, MLP_H, MLP_OUT = 32, 64, 37
 
 
 class KsError(RuntimeError):
@@ -125,6 +128,7 @@ def load(build_if_missing: bool = True):
         "ks_set_batch_plan": ([vp, ctypes.c_int32, P(ks_bucket), ctypes.c_int32, vp], ctypes.c_int),
         "ks_get_batch_info": ([vp, P(ks_batch_info)], ctypes.c_int),
         "ks_batch_variants": ([ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32)], ctypes.c_int),
+        "ks_mlp_forward": ([vp, vp, ctypes.c_int64, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +263,50 @@ def ks_batch_variants(cta_threads: int):
     buf = (ctypes.c_int32 * (2 * n.value))()
     _check(load().ks_batch_variants(int(cta_threads), buf, n.value, ctypes.byref(n)), "ks_batch_variants")
     return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+
+def pack_mlp_params(W1, b1, W2, b2, W3, b3, device="cuda"):
+    """Device parameter blob of the policy (layout in kineticsim.h): BF16
+    weights (rounded to nearest even from the given values), FP32 biases."""
+    import torch
+    blob = torch.zeros(KS_MLP_PARAM_BYTES, dtype=torch.uint8)
+    off = 0
+    for W in (W1, W2, W3):
+        t = torch.as_tensor(np.asarray(W, np.float32)).to(torch.bfloat16).contiguous()
+        b = t.view(torch.uint8).reshape(-1)
+        blob[off:off + b.numel()] = b
+        off += b.numel()
+    for bias in (b1, b2, b3):
+        t = torch.as_tensor(np.asarray(bias, np.float32)).contiguous()
+        b = t.view(torch.uint8).reshape(-1)
+        blob[off:off + b.numel()] = b
+        off += b.numel()
+    return blob.to(device)
+
+
+def mlp_params_as_used(W1, b1, W2, b2, W3, b3):
+    """The parameter values the kernels compute with (BF16-rounded weights, FP32 biases), as float64."""
+    import torch
+    out = []
+    for i, a in enumerate((W1, b1, W2, b2, W3, b3)):
+        t = torch.as_tensor(np.asarray(a, np.float32))
+        if i % 2 == 0:
+            t = t.to(torch.bfloat16).float()
+        out.append(t.double().numpy())
+    return out
+
+
+def ks_mlp_forward(params_blob, X, err=None, stream=None):
+    """Logits [n, 37] (fp32, device) of feature rows X [n, 32] (fp32, device)."""
+    import torch
+    X = X.contiguous()
+    n = X.shape[0]
+    Z = torch.empty((n, MLP_OUT), dtype=torch.float32, device=X.device)
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=X.device)
+    _check(load().ks_mlp_forward(params_blob.data_ptr(), X.data_ptr(), n, Z.data_ptr(), err.data_ptr(),
+                                 _stream_ptr(stream)), "ks_mlp_forward")
+    return Z, err
 
 
 KS_PROBE_SMEM_RED, KS_PROBE_MUL_WIDE, KS_PROBE_PHILOX = 0, 1, 2
