@@ -278,6 +278,32 @@ const char* ks_last_error(void);
  * tensor-core wait that gave up). */
 ks_status ks_mlp_forward(const void* params, const float* X, int64_t n, float* Z, uint32_t* err, void* stream);
 
+/*
+ * ks_step_n for callers that cannot allocate device memory for the batched
+ * kernel's scratch.  The paper has no counterpart: this is a deployment
+ * variant of the batched launch.
+ *
+ * ks_step_n keeps the batched kernel's scratch -- its work schedule (markets
+ * grouped into work items, longest first) and the ticket counter the CTAs
+ * take items from -- in the caller's workspace.  This entry point runs the
+ * same kernel with that scratch in a static device array owned by the
+ * library instead, of fixed size (KS_NOALLOC_MAX_MARKETS markets: about
+ * 640 KB), which every GPU that loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - The ensemble must run the batched kernel (an uneven ensemble, or any
+ *    ensemble after ks_set_batch_plan): else KS_ERR_INVALID_ARG.
+ *  - More than KS_NOALLOC_MAX_MARKETS markets: KS_ERR_UNSUPPORTED.
+ *  - The ensemble's device must be current: else KS_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the array and overwrites it (it clears the ticket and
+ *    copies the schedule from the host on `stream` before the launch), so
+ *    calls that overlap on the GPU, on any streams, race.
+ * Otherwise as ks_step_n: steps [s, s + n_steps), results identical.
+ */
+#define KS_NOALLOC_MAX_MARKETS 32768
+ks_status ks_step_n_noalloc(ks_ensemble* e, uint32_t n_steps, void* stream);
+
 /* Library version, e.g. 0x000100 for 0.1.0. */
 uint32_t ks_version(void);
 

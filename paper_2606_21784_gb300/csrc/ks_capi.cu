@@ -753,6 +753,36 @@ ks_status ks_probe_state_io(ks_ensemble* e, void* stream, double* bytes) {
   return KS_OK;
 }
 
+}  // extern "C"
+
+// Internal accessors for ks_noalloc.cu (no public ABI).
+namespace ks {
+ks_status internal_batched_schedule(const ks_ensemble* e, const uint32_t** order, const uint4** items,
+                                    uint32_t* n_markets, uint32_t* n_items) {
+  if (!e) return KS_ERR_INVALID_ARG;
+  if (e->mode != 1) return arg_fail(KS_ERR_INVALID_ARG, "the ensemble does not run the batched kernel");
+  *order = e->b_order.data();
+  *items = e->b_items.data();
+  *n_markets = (uint32_t)e->b_order.size();
+  *n_items = (uint32_t)e->b_items.size();
+  return KS_OK;
+}
+
+ks_status internal_launch_batched(ks_ensemble* e, uint32_t n_steps, const BatchArgs& b, cudaStream_t st) {
+  cudaError_t ce = e->b_threads == 512 ? launch_batched_512(e->dp, n_steps, b, e->b_grid, e->b_smem, st)
+                                        : launch_batched_1024(e->dp, n_steps, b, e->b_grid, e->b_smem, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "batched launch");
+  step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, e->b_args.ticket, n_steps);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return cuda_fail(ce, "step counter");
+  return KS_OK;
+}
+
+int internal_device(const ks_ensemble* e) { return e ? e->device : -1; }
+}  // namespace ks
+
+extern "C" {
+
 ks_status ks_destroy(ks_ensemble* e) {
   delete e;
   return KS_OK;
