@@ -271,6 +271,37 @@ const char* ks_last_error(void);
  */
 #define KS_MLP_PARAM_BYTES 17696
 
+/*
+ * Captures (learned-agent workflows; device buffers owned by the caller).
+ *  - Rule-decision records, the behaviour-cloning data: every new order of a
+ *    rule agent with index a < record_agents is appended as
+ *    KS_RECORD_WORDS int32: the policy's 18 raw inputs (eight clearing-tick
+ *    returns, newest first; inventory; last executed volume; resting sell
+ *    quantity at last+1..+4; resting buy quantity at last-1..-4), side,
+ *    offset index (tick - last clamped to [-16, 16], plus 16), qty, agent
+ *    class.  Records are appended in no particular order; *record_count
+ *    counts every attempt, records beyond `record_capacity` are dropped.
+ *  - Policy decisions of the traced markets: decisions[s * traced_agents + g]
+ *    for absolute step s < trace_steps and global agent id g of a market
+ *    m < trace_markets: an order word (qty, side, tick) of the order the
+ *    policy placed, KS_DECISION_PASS if it passed, untouched if the agent made
+ *    no policy decision at step s.
+ */
+#define KS_RECORD_WORDS 22
+#define KS_DECISION_PASS 0x01000000u
+typedef struct ks_capture {
+  int32_t* records;
+  uint64_t record_capacity;
+  uint32_t record_agents;
+  uint32_t pad_;
+  unsigned long long* record_count;
+  uint32_t* decisions;
+} ks_capture;
+
+/* Sets the ensemble's captures (NULL fields switch a capture off).  Capturing
+ * runs the policy-capable kernels. */
+ks_status ks_set_capture(ks_ensemble* e, const ks_capture* c);
+
 /* Logits Z [n][37] (fp32) of feature rows X [n][32] (fp32), all device
  * pointers: layer 1 in FP32, layers 2-3 on the BF16 tcgen05 path the step
  * loop uses (BF16 weights, activations passed as high + low BF16 parts,

@@ -35,6 +35,64 @@ __device__ __forceinline__ void run_item(const DevParams& P, const BatchArgs& B,
   }
 }
 
+// Policy-capable variant: each group also owns an activation buffer after
+// its market shared memory, an mbarrier and 64 TMEM columns of the CTA.
+template <int NT, int GT, int AK>
+__device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+                                             unsigned char* raw, const MlpCta& mc) {
+  static_assert(GT >= 128 && GT % 128 == 0, "policy groups are whole warpgroups");
+  constexpr int G = NT / GT;
+  const int g = (int)threadIdx.x / GT;
+  if (g < G && g < (int)d.y) {
+    size_t o[8];
+    const size_t mbytes = market_smem_layout(GT, AK, (int)d.w, true, o);
+    const size_t gsz = mbytes + MLP_ACT_BYTES;
+    unsigned char* graw = raw + (size_t)g * gsz;
+    const Smem sm = carve<GT, AK, true>(graw, (int)d.w);
+    const int bar = (GT == NT) ? 0 : 1 + g;
+    MlpWG mw;
+    mw.act = graw + mbytes;
+    mw.bar = &mc.bars[g];
+    mw.tmem = *mc.tslot + (uint32_t)(g * MLP_TMEM_COLS);
+    mw.bar_id = (GT == 128) ? bar : 8 + g;
+    mw.phase = 0;
+    mw.abort = false;
+    run_market<GT, AK, false, true>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w, &mw,
+                                    mc.sw);
+  }
+}
+
+#define KS_BATCH_MLP_VARIANTS_512(X) \
+  X(0, 128, 4) X(1, 128, 8) X(2, 128, 16) X(3, 256, 8) X(4, 256, 16) X(5, 512, 8) X(6, 512, 16) X(7, 512, 32)
+
+template <int NT>
+__device__ void dispatch_item_mlp(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+                                  unsigned char* raw, const MlpCta& mc);
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) batched_mlp_kernel(DevParams P, uint32_t n_steps, BatchArgs B) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint32_t s_item;
+  const uint32_t s0 = (uint32_t)(*P.step);
+  const MlpCta mc = mlp_cta_carve(smem_raw, (uint32_t)(NT / 128) * MLP_TMEM_COLS);
+  mlp_cta_setup(mc, P.mlp);
+  unsigned char* raw = smem_raw + mlp_cta_bytes();
+  for (;;) {
+    __syncthreads();  // the previous item is finished and s_item has been read
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(B.ticket, 1u);
+      // every group starts the item at mbarrier phase 0 (no MMA is in flight here)
+      for (int i = 0; i < MLP_MAX_GROUPS; ++i) mbar_init(&mc.bars[i], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= B.n_items) break;
+    dispatch_item_mlp<NT>(P, B, B.items[it], s0, n_steps, raw, mc);
+  }
+  mlp_cta_teardown(mc);
+}
+
 // (variant id, GT, AK) lists; the host mirrors them in ks_batched_variants().
 #define KS_BATCH_VARIANTS_1024(X)                                                                          \
   X(0, 32, 1) X(1, 32, 2) X(2, 32, 4) X(3, 32, 8) X(4, 128, 2) X(5, 128, 4) X(6, 128, 8) X(7, 256, 4) \
@@ -49,7 +107,7 @@ __device__ void dispatch_item(const DevParams& P, const BatchArgs& B, uint4 d, u
 
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) batched_kernel(DevParams P, uint32_t n_steps, BatchArgs B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint32_t s_item;
   const uint32_t s0 = (uint32_t)(*P.step);
   for (;;) {

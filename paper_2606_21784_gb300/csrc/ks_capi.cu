@@ -33,8 +33,20 @@ cudaError_t launch_batched_1024(const DevParams& p, uint32_t n_steps, const Batc
                                 cudaStream_t st);
 const void* batched_kernel_512();
 const void* batched_kernel_1024();
+extern const PlainVariant kPlainMlp[];
+extern const int kPlainMlpCount;
+extern const int kBatchMlpVariants512[][2];
+extern const int kBatchMlpVariants512Count;
+cudaError_t launch_batched_mlp_512(const DevParams& p, uint32_t n_steps, const BatchArgs& b, int grid, size_t smem,
+                                   cudaStream_t st);
+const void* batched_mlp_kernel_512();
 
-const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy) {
+const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy, bool mlp) {
+  if (mlp) {
+    for (int j = 0; j < kPlainMlpCount; ++j)
+      if (kPlainMlp[j].threads == threads && kPlainMlp[j].ak == ak) return &kPlainMlp[j];
+    return nullptr;
+  }
   const PlainVariant* tabs[4] = {kPlainNT128, kPlainNT256, kPlainNT512, kPlainNT1024};
   const int counts[4] = {kPlainNT128Count, kPlainNT256Count, kPlainNT512Count, kPlainNT1024Count};
   for (int i = 0; i < 4; ++i)
@@ -46,7 +58,15 @@ const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy
   return nullptr;
 }
 
-static const int (*batch_table(int nt, int* count))[2] {
+static const int (*batch_table(int nt, int* count, bool mlp = false))[2] {
+  if (mlp) {
+    if (nt == 512) {
+      *count = kBatchMlpVariants512Count;
+      return kBatchMlpVariants512;
+    }
+    *count = 0;  // the policy batched kernel is compiled for 512-thread CTAs only
+    return nullptr;
+  }
   if (nt == 512) {
     *count = kBatchVariants512Count;
     return kBatchVariants512;
@@ -60,7 +80,7 @@ static const int (*batch_table(int nt, int* count))[2] {
 }
 
 size_t plain_smem_bytes(int threads, int ak, int Lmax) {
-  size_t o[5];
+  size_t o[8];
   return plain_smem_layout(threads, ak, Lmax, o);
 }
 
@@ -157,6 +177,7 @@ struct ks_ensemble {
   int device;
   int num_sms;
   size_t max_smem;
+  bool mlp;  // the policy-capable kernels run (policy agents or captures)
 };
 
 struct Layout {
@@ -211,7 +232,9 @@ static ks_status validate(const ks_config* c, Sizes* sz) {
   if (c->tie_rule != KS_TIE_LOWEST_TICK && c->tie_rule != KS_TIE_MIN_IMBALANCE)
     return arg_fail(KS_ERR_INVALID_ARG, "unknown tie_rule");
   if (c->mlp_pct > 100u) return arg_fail(KS_ERR_INVALID_ARG, "mlp_pct above 100");
-  if (c->mlp_pct > 0u) return arg_fail(KS_ERR_UNSUPPORTED, "MLP-driven agents need the learned-policy build");
+  if (c->mlp_pct > 0u && !c->mlp_params) return arg_fail(KS_ERR_INVALID_ARG, "mlp_pct > 0 needs mlp_params");
+  if (c->mlp_params && ((uintptr_t)c->mlp_params & 15u) != 0)
+    return arg_fail(KS_ERR_INVALID_ARG, "mlp_params not 16-byte aligned");
   if (c->trace_markets > c->n_markets) return arg_fail(KS_ERR_INVALID_ARG, "trace_markets above n_markets");
   if ((c->trace_markets == 0) != (c->trace_steps == 0) && c->trace_markets != 0)
     return arg_fail(KS_ERR_INVALID_ARG, "trace_steps must be > 0 when tracing");
@@ -249,9 +272,22 @@ static int next_pow2(int x) {
 // Default launch shape: with few markets, spread each market over many
 // threads; otherwise 16 agents per thread under the ~85-register cap (the
 // fastest shape measured on GB300 for 4096-agent markets).
-static ks_launch default_launch(int Amax, uint32_t M, int num_sms) {
+static ks_launch default_launch(int Amax, uint32_t M, int num_sms, bool mlp = false) {
   ks_launch l;
   memset(&l, 0, sizeof(l));
+  if (mlp) {
+    // the smallest compiled policy shape that holds the largest market
+    int best = -1;
+    for (int j = 0; j < kPlainMlpCount; ++j) {
+      const PlainVariant& v = kPlainMlp[j];
+      if ((int64_t)v.threads * v.ak < Amax) continue;
+      if (best < 0 || (int64_t)v.threads * v.ak < (int64_t)kPlainMlp[best].threads * kPlainMlp[best].ak) best = j;
+    }
+    if (best < 0) best = kPlainMlpCount - 1;
+    l.threads = kPlainMlp[best].threads;
+    l.agents_per_thread = kPlainMlp[best].ak;
+    return l;
+  }
   const bool few = (int)M < 2 * num_sms;
   int nt = few ? next_pow2(std::max(Amax, 1)) : next_pow2((std::max(Amax, 1) + 15) / 16);
   nt = std::min(1024, std::max(128, nt));
@@ -269,18 +305,22 @@ static ks_launch default_launch(int Amax, uint32_t M, int num_sms) {
 }
 
 static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
-  const PlainVariant* v = find_plain(l->threads, l->agents_per_thread, l->aggregate, l->reg_cap);
-  if (!v) return arg_fail(KS_ERR_INVALID_ARG, "no kernel for this (threads, agents_per_thread, aggregate, reg_cap)");
+  const PlainVariant* v = find_plain(l->threads, l->agents_per_thread, l->aggregate, l->reg_cap, e->mlp);
+  if (!v)
+    return arg_fail(KS_ERR_INVALID_ARG, e->mlp ? "no policy-capable kernel for this (threads, agents_per_thread)"
+                                               : "no kernel for this (threads, agents_per_thread, aggregate, reg_cap)");
   if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
     return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
   if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
-  const size_t smem = plain_smem_bytes(l->threads, l->agents_per_thread, e->Lmax);
+  const size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, e->Lmax, e->mlp);
   if (smem > e->max_smem) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more shared memory than a CTA has");
   const void* k = v->kernel;
   KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, l->threads, smem));
   if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+  // resident CTAs must not ask for more TMEM than an SM has (512 columns)
+  if (e->mlp && occ * (int)MLP_TMEM_COLS > 512) return arg_fail(KS_ERR_UNSUPPORTED, "policy launch oversubscribes TMEM");
   const int per_sm = l->ctas_per_sm > 0 ? std::min(occ, l->ctas_per_sm) : occ;
   e->grid = (int)std::min<int64_t>((int64_t)e->M, (int64_t)per_sm * e->num_sms);
   e->smem = smem;
@@ -293,17 +333,19 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
 // ---------------------------------------------------------------------------
 // Batched plans: buckets -> work items (markets per CTA, longest first)
 // ---------------------------------------------------------------------------
-static int batch_variant_id(int nt, int gt, int ak) {
+static int batch_variant_id(int nt, int gt, int ak, bool mlp) {
   int n = 0;
-  const int(*tab)[2] = batch_table(nt, &n);
+  const int(*tab)[2] = batch_table(nt, &n, mlp);
   for (int i = 0; i < n; ++i)
     if (tab[i][0] == gt && tab[i][1] == ak) return i;
   return -1;
 }
 
 // Groups of one bucket that fit one CTA: thread count, barrier ids, shared memory.
-static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz) {
-  *gsz = plain_smem_bytes(gt, ak, Lcap);
+static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz, bool mlp) {
+  size_t o[8];
+  *gsz = market_smem_layout(gt, ak, Lcap, mlp, o) + (mlp ? MLP_ACT_BYTES : 0);
+  if (mlp) max_smem = max_smem > mlp_cta_bytes() ? max_smem - mlp_cta_bytes() : 0;
   int g = nt / gt;
   if (gt != 32 && gt != nt) g = std::min(g, 15);
   g = std::min<int64_t>(g, (int64_t)(max_smem / *gsz));
@@ -311,9 +353,9 @@ static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, siz
 }
 
 // Default bucket shape: about 8 agents per thread.
-static bool default_shape(int nt, int Ac, int* gt, int* ak) {
+static bool default_shape(int nt, int Ac, int* gt, int* ak, bool mlp) {
   int n = 0;
-  const int(*tab)[2] = batch_table(nt, &n);
+  const int(*tab)[2] = batch_table(nt, &n, mlp);
   int best = -1;
   long best_score = 0;
   for (int i = 0; i < n; ++i) {
@@ -332,7 +374,8 @@ static bool default_shape(int nt, int Ac, int* gt, int* ak) {
   return true;
 }
 
-static std::vector<ks_bucket> default_plan(const std::vector<int32_t>& L, const std::vector<int32_t>& A, int nt) {
+static std::vector<ks_bucket> default_plan(const std::vector<int32_t>& L, const std::vector<int32_t>& A, int nt,
+                                           bool mlp) {
   std::vector<std::pair<int, int>> keys;
   for (size_t m = 0; m < L.size(); ++m) {
     const int Lc = std::max(32, next_pow2(L[m]));
@@ -346,7 +389,7 @@ static std::vector<ks_bucket> default_plan(const std::vector<int32_t>& L, const 
     ks_bucket b;
     b.L_max = k.first;
     b.A_max = k.second;
-    if (!default_shape(nt, k.second, &b.group_threads, &b.agents_per_thread)) continue;
+    if (!default_shape(nt, k.second, &b.group_threads, &b.agents_per_thread, mlp)) continue;
     plan.push_back(b);
   }
   return plan;
@@ -355,19 +398,23 @@ static std::vector<ks_bucket> default_plan(const std::vector<int32_t>& L, const 
 static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, int nb, cudaStream_t st) {
   if (nt != 512 && nt != 1024) return arg_fail(KS_ERR_INVALID_ARG, "batched CTA size must be 512 or 1024");
   if (nb <= 0 || !buckets) return arg_fail(KS_ERR_INVALID_ARG, "empty batch plan");
-  const void* kern = nt == 512 ? batched_kernel_512() : batched_kernel_1024();
+  const bool mlp = e->mlp;
+  if (mlp && nt != 512) return arg_fail(KS_ERR_INVALID_ARG, "the policy batched kernel uses 512-thread CTAs");
+  const void* kern = mlp ? batched_mlp_kernel_512() : (nt == 512 ? batched_kernel_512() : batched_kernel_1024());
   const size_t max_dyn = e->max_smem - 1024;  // room for the kernel's static shared memory
   std::vector<int> var(nb);
   std::vector<int> G(nb);
   std::vector<size_t> gsz(nb);
   for (int b = 0; b < nb; ++b) {
     const ks_bucket& k = buckets[b];
-    var[b] = batch_variant_id(nt, k.group_threads, k.agents_per_thread);
-    if (var[b] < 0) return arg_fail(KS_ERR_INVALID_ARG, "bucket shape not compiled into the batched kernel");
+    var[b] = batch_variant_id(nt, k.group_threads, k.agents_per_thread, mlp);
+    if (var[b] < 0)
+      return arg_fail(KS_ERR_INVALID_ARG, mlp ? "bucket shape not compiled into the policy batched kernel"
+                                              : "bucket shape not compiled into the batched kernel");
     if ((int64_t)k.group_threads * k.agents_per_thread < k.A_max)
       return arg_fail(KS_ERR_INVALID_ARG, "bucket group_threads * agents_per_thread below its A_max");
     if (k.L_max < 2 || k.L_max > KS_MAX_TICKS) return arg_fail(KS_ERR_INVALID_ARG, "bucket L_max out of range");
-    G[b] = groups_per_cta(nt, k.group_threads, k.agents_per_thread, k.L_max, max_dyn, &gsz[b]);
+    G[b] = groups_per_cta(nt, k.group_threads, k.agents_per_thread, k.L_max, max_dyn, &gsz[b], mlp);
     if (G[b] < 1) return arg_fail(KS_ERR_UNSUPPORTED, "bucket does not fit the shared memory of one CTA");
   }
   std::vector<std::vector<uint32_t>> members(nb);
@@ -401,6 +448,7 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
     }
   }
   std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
+  if (mlp) smem += mlp_cta_bytes();
   std::vector<uint32_t> order;
   std::vector<uint4> ditems;
   for (auto& it : items) {
@@ -416,6 +464,8 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
   int occ = 0;
   KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem));
   if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "batched plan does not fit on an SM");
+  if (mlp && occ * (nt / 128) * (int)MLP_TMEM_COLS > 512)
+    return arg_fail(KS_ERR_UNSUPPORTED, "policy batched launch oversubscribes TMEM");
   const Layout lay = make_layout(e->M, e->N, e->uniform, e->cfg.trace_markets, e->cfg.trace_steps);
   KS_CUDA(cudaMemcpyAsync(e->ws + lay.order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, st));
   KS_CUDA(cudaMemcpyAsync(e->ws + lay.items, ditems.data(), ditems.size() * 16, cudaMemcpyHostToDevice, st));
@@ -436,6 +486,7 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
 
 static cudaError_t launch_main(ks_ensemble* e, uint32_t n_steps, cudaStream_t st) {
   if (e->mode == 1) {
+    if (e->mlp) return launch_batched_mlp_512(e->dp, n_steps, e->b_args, e->b_grid, e->b_smem, st);
     return e->b_threads == 512 ? launch_batched_512(e->dp, n_steps, e->b_args, e->b_grid, e->b_smem, st)
                                : launch_batched_1024(e->dp, n_steps, e->b_args, e->b_grid, e->b_smem, st);
   }
@@ -544,11 +595,14 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
   p.Ls = sz.uniform ? nullptr : (const int32_t*)(w + lay.Ls);
   p.As = sz.uniform ? nullptr : (const int32_t*)(w + lay.As);
   p.trace = (int32_t*)(w + lay.trace);
+  p.mlp = (const unsigned char*)cfg->mlp_params;
+  p.dec_trace_agents = (uint64_t)sz.off[cfg->trace_markets];
+  e->mlp = cfg->mlp_pct > 0;
   p.err = (uint32_t*)(w + lay.ctrl);
   p.step = (const uint64_t*)(w + lay.ctrl + 8);
   e->b_args.ticket = (uint32_t*)(w + lay.ctrl + 16);
 
-  ks_launch l = default_launch(e->Amax, e->M, e->num_sms);
+  ks_launch l = default_launch(e->Amax, e->M, e->num_sms, e->mlp);
   s = apply_launch(e, &l);
   if (s != KS_OK && sz.uniform) {
     delete e;
@@ -578,8 +632,9 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
 #undef KS_CUDA_E
   if (!sz.uniform) {
     // uneven ensembles default to the batched kernel with one bucket per (L, A) power-of-two class
-    std::vector<ks_bucket> plan = default_plan(e->L, e->A, 1024);
-    s = build_batch(e, 1024, plan.data(), (int)plan.size(), st);
+    const int nt = e->mlp ? 512 : 1024;
+    std::vector<ks_bucket> plan = default_plan(e->L, e->A, nt, e->mlp);
+    s = build_batch(e, nt, plan.data(), (int)plan.size(), st);
     if (s != KS_OK) {
       delete e;
       return s;
@@ -729,6 +784,31 @@ ks_status ks_get_batch_info(const ks_ensemble* e, ks_batch_info* info) {
   return KS_OK;
 }
 
+ks_status ks_set_capture(ks_ensemble* e, const ks_capture* c) {
+  if (!e || !c) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
+  if (c->records && (!c->record_count || c->record_capacity == 0))
+    return arg_fail(KS_ERR_INVALID_ARG, "records need record_count and a capacity");
+  if (c->decisions && (e->cfg.trace_markets == 0 || e->cfg.trace_steps == 0))
+    return arg_fail(KS_ERR_INVALID_ARG, "decision capture needs trace_markets and trace_steps");
+  DevParams& p = e->dp;
+  p.rec = c->records;
+  p.rec_count = c->record_count;
+  p.rec_cap = c->records ? c->record_capacity : 0;
+  p.rec_agents = c->records ? c->record_agents : 0;
+  p.dec_trace = c->decisions;
+  const bool want = e->cfg.mlp_pct > 0 || c->records != nullptr || c->decisions != nullptr;
+  if (want == e->mlp) return KS_OK;
+  // switch between the rule-only and the policy-capable kernels, keeping the mode
+  e->mlp = want;
+  if (e->mode == 1) {
+    const int nt = e->mlp ? 512 : 1024;
+    std::vector<ks_bucket> plan = default_plan(e->L, e->A, nt, e->mlp);
+    return build_batch(e, nt, plan.data(), (int)plan.size(), nullptr);
+  }
+  ks_launch l = default_launch(e->Amax, e->M, e->num_sms, e->mlp);
+  return apply_launch(e, &l);
+}
+
 ks_status ks_batch_variants(int32_t cta_threads, int32_t* pairs, int32_t capacity, int32_t* count) {
   if (!count) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
   int n = 0;
@@ -769,8 +849,9 @@ ks_status internal_batched_schedule(const ks_ensemble* e, const uint32_t** order
 }
 
 ks_status internal_launch_batched(ks_ensemble* e, uint32_t n_steps, const BatchArgs& b, cudaStream_t st) {
-  cudaError_t ce = e->b_threads == 512 ? launch_batched_512(e->dp, n_steps, b, e->b_grid, e->b_smem, st)
-                                        : launch_batched_1024(e->dp, n_steps, b, e->b_grid, e->b_smem, st);
+  cudaError_t ce = e->mlp ? launch_batched_mlp_512(e->dp, n_steps, b, e->b_grid, e->b_smem, st)
+                   : e->b_threads == 512 ? launch_batched_512(e->dp, n_steps, b, e->b_grid, e->b_smem, st)
+                                         : launch_batched_1024(e->dp, n_steps, b, e->b_grid, e->b_smem, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "batched launch");
   step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, e->b_args.ticket, n_steps);
   ce = cudaGetLastError();

@@ -52,6 +52,15 @@ struct DevParams {
   int32_t* trace;            // [trace_markets][trace_steps][2]
   uint32_t* err;
   const uint64_t* step;      // absolute step counter (device)
+
+  // learned agents and captures (used by the kernels compiled with the policy path)
+  const unsigned char* mlp;  // policy parameter blob or nullptr
+  int32_t* rec;              // rule-decision records [rec_cap][KS_RECORD_WORDS]
+  unsigned long long* rec_count;
+  uint64_t rec_cap;
+  uint32_t rec_agents;       // record agents a < rec_agents of every market
+  uint32_t* dec_trace;       // [trace_steps][dec_trace_agents] policy decisions of traced markets
+  uint64_t dec_trace_agents; // agents of markets 0..trace_markets-1
 };
 
 // A persistent launch of the plain kernel template.
@@ -63,6 +72,7 @@ struct PlainVariant {
   int occupancy;  // register-cap class (0 none, 1 ~85, 2 64 registers)
   PlainLaunchFn launch;
   const void* kernel;  // for attribute and occupancy queries
+  int mlp = 0;         // policy path compiled in
 };
 
 // Registry filled by the instantiation translation units.

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "ks_device.cuh"
+#include "ks_mlp.cuh"
 
 namespace ks {
 
@@ -41,22 +42,34 @@ struct Smem {
   uint32_t* wMB;          // [32] warp totals of marginal buy quantity
   uint32_t* wMS;          // [32] warp totals of marginal sell quantity
   int32_t* rem;           // [2]: R_b, R_s (units filled at the marginal buy / sell tick)
+  int32_t* feat;          // [8]: resting sell qty at last+1..+4, buy qty at last-1..-4 (policy inputs)
+  int32_t* wR;            // [32] warp totals of policy rows
+  float* cvec;            // [64] layer-1 pre-activation shared by the market's agents (policy kernels)
+  uint32_t* rowbuf;       // [NT * AK] policy rows: agent index, then the decision (policy kernels)
 };
 
-__host__ __device__ inline size_t plain_smem_layout(int nt, int ak, int Lmax, size_t* o) {
+// Shared memory of one market group; `mlp` adds the policy rows.
+__host__ __device__ inline size_t market_smem_layout(int nt, int ak, int Lmax, bool mlp, size_t* o) {
   size_t off = 0;
   o[0] = off; off += (size_t)8 * ak * nt;                // cash
   o[1] = off; off += (size_t)8 * 8;                      // kx
   o[2] = off; off += (size_t)4 * ak * nt;                // inv
   o[3] = off; off += (size_t)4 * 2 * book_len(Lmax);     // book
   o[4] = off; off += (size_t)4 * 32 * 4 + 4 * 4;         // wD, wS, wMB, wMS, rem
+  o[5] = off; off += (size_t)4 * 8 + 4 * 32;             // feat, wR
+  o[6] = off; off += mlp ? (size_t)4 * 64 : 0;           // cvec
+  o[7] = off; off += mlp ? (size_t)4 * ak * nt : 0;      // rowbuf
   return (off + 15) & ~(size_t)15;
 }
 
-template <int NT, int AK>
+__host__ __device__ inline size_t plain_smem_layout(int nt, int ak, int Lmax, size_t* o) {
+  return market_smem_layout(nt, ak, Lmax, false, o);
+}
+
+template <int NT, int AK, bool MLP = false>
 __device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
-  size_t o[5];
-  plain_smem_layout(NT, AK, Lmax, o);
+  size_t o[8];
+  market_smem_layout(NT, AK, Lmax, MLP, o);
   Smem s;
   s.cash = reinterpret_cast<int64_t*>(raw + o[0]);
   s.kx = reinterpret_cast<unsigned long long*>(raw + o[1]);
@@ -67,6 +80,10 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
   s.wMB = reinterpret_cast<uint32_t*>(s.wD + 64);
   s.wMS = s.wMB + 32;
   s.rem = s.wD + 128;
+  s.feat = reinterpret_cast<int32_t*>(raw + o[5]);
+  s.wR = s.feat + 8;
+  s.cvec = reinterpret_cast<float*>(raw + o[6]);
+  s.rowbuf = reinterpret_cast<uint32_t*>(raw + o[7]);
   return s;
 }
 
@@ -112,18 +129,52 @@ struct StepRules {
   int side_mr;
 };
 
+// Market-level policy inputs of a step: clearing-tick returns, last volume
+// (registers) and resting depth around the last tick (shared memory).
+struct StepFeat {
+  int h[8];
+  int lastv;
+  const int32_t* depth;
+};
+
+// Appends one rule-decision record (the behaviour-cloning data).
+__device__ __forceinline__ void record_decision(const DevParams& P, const StepFeat& f, int inv, uint32_t w, int last) {
+  const unsigned long long i = atomicAdd(P.rec_count, 1ull);
+  if (i >= P.rec_cap) return;
+  int32_t* r = P.rec + i * KS_RECORD_WORDS;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = f.h[j];
+  r[8] = inv;
+  r[9] = f.lastv;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[10 + j] = f.depth[j];
+  r[18] = (int)w_sell(w);
+  r[19] = min(max((int)w_tick(w) - last, -MLP_OFF_MAX), MLP_OFF_MAX) + MLP_OFF_MAX;
+  r[20] = (int)w_qty(w);
+  r[21] = (int)w_class(w);
+}
+
 // Step-s order of one agent: cancellation of its working order (carried
 // books), then a new order if it has none.  Returns the new order word.
-template <bool AGGR>
+// With MLP, a policy-driven agent without an order sets `policy` instead of
+// deciding, and rule decisions of recorded agents are appended.
+template <bool AGGR, bool MLP = false>
 __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, bool valid, const StepRules& sr, bool carry,
-                                                uint32_t cthr, int L, const RuleConsts& rc, int32_t* book, int sb) {
+                                                uint32_t cthr, int L, const RuleConsts& rc, int32_t* book, int sb,
+                                                bool* policy = nullptr, const DevParams* P = nullptr,
+                                                const StepFeat* f = nullptr, int inv = 0) {
   const uint4 w = step_draw(sr.sk, (uint32_t)a);
   const uint32_t q = w_qty(sl);
   const bool cancel = valid && carry && q != 0u && w.x < cthr;
   if (cancel) atomicSub(book + bidx(w_sell(sl), w_tick(sl), sb), (int)q);
-  const bool dec = valid && (q == 0u || cancel) && !(sl & W_MLP);
+  const bool empty = valid && (q == 0u || cancel);
+  const bool dec = empty && !(sl & W_MLP);
   const uint32_t ns = decide_rule(sl, w, sr.last, sr.side_mom, sr.side_mr, L, rc);
   book_add<AGGR>(book, sb, dec, ns);
+  if constexpr (MLP) {
+    *policy = empty && (sl & W_MLP);
+    if (dec && (uint32_t)a < P->rec_agents) record_decision(*P, *f, inv, ns, sr.last);
+  }
   return dec ? ns : (cancel ? (sl & W_STATIC) : sl);
 }
 
@@ -154,12 +205,106 @@ __device__ __forceinline__ int fill_dist(uint32_t sl, int p_lo, int p_hi) {
   return w_sell(sl) ? (p_lo - tk) : (tk - p_hi);
 }
 
+// Policy decisions of one step for the agents flagged in `pflags` (bit k =
+// agent a0 + k): rows are compacted in agent order, the group's first
+// warpgroup evaluates them 128 at a time on the tensor cores and samples the
+// actions (Philox stream 3 of step sdec), then the owners place the orders.
+template <int NT, int AK>
+__device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm, MlpWG& mw, const unsigned char* sw,
+                                             uint32_t (&slot)[AK], uint32_t pflags, int t, int bar, int a0, int A,
+                                             int L, uint32_t sdec, uint32_t gm, const StepFeat& f, int last,
+                                             int64_t aoff, bool traced, int32_t* book, int sb) {
+  constexpr int NW = NT / 32;
+  const int lane = t & 31;
+  const int wid = t >> 5;
+  const int cnt = __popc(pflags);
+  int inc = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) sm.wR[wid] = inc;
+  if (t < MLP_H) {
+    // layer-1 pre-activation of everything but the inventory input
+    const float* w1 = reinterpret_cast<const float*>(sw + MLP_SM_W1) + t * MLP_IN;
+    const float* b1 = reinterpret_cast<const float*>(sw + MLP_SM_B);
+    const float inv8A = 1.0f / (8.0f * (float)max(A, 1));
+    const float inv4A = 1.0f / (4.0f * (float)max(A, 1));
+    float c = b1[t];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c = fmaf(w1[j], (float)f.h[j] * 0.125f, c);
+    c = fmaf(w1[9], (float)f.lastv * inv8A, c);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c = fmaf(w1[10 + j], (float)f.depth[j] * inv4A, c);
+    sm.cvec[t] = c;
+  }
+  gsync<NT>(bar);
+  const int before = inc - cnt + (int)__reduce_add_sync(0xffffffffu, lane < wid ? (unsigned)sm.wR[lane] : 0u);
+  const int total = (int)__reduce_add_sync(0xffffffffu, lane < NW ? (unsigned)sm.wR[lane] : 0u);
+  int r = before;
+#pragma unroll
+  for (int k = 0; k < AK; ++k)
+    if ((pflags >> k) & 1u) sm.rowbuf[r++] = (uint32_t)(a0 + k);
+  gsync<NT>(bar);
+  if (total > 0 && t < 128) {
+    for (int tile = 0; tile * 128 < total; ++tile) {
+      const int row = tile * 128 + t;
+      const bool valid = row < total;
+      const int a = valid ? (int)sm.rowbuf[row] : 0;
+      const int inv = valid ? sm.inv[(a % AK) * NT + a / AK] : 0;
+      float z[MLP_OUT];
+      mlp_tile_logits(mw, sw, sm.cvec, (float)inv * (1.0f / 256.0f), z, P.err);
+      if (valid) {
+        const uint4 w = philox(sdec, (uint32_t)a, gm, 3u, P.key0, P.key1);
+        sm.rowbuf[row] = mlp_decision(z, w, last, L, P.rb_qmax);
+      }
+    }
+  }
+  gsync<NT>(bar);
+  r = before;
+#pragma unroll
+  for (int k = 0; k < AK; ++k) {
+    if ((pflags >> k) & 1u) {
+      const uint32_t d = sm.rowbuf[r++];
+      if (!(d & KS_DECISION_PASS)) {
+        slot[k] = (slot[k] & W_STATIC) | d;
+        atomicAdd(book + bidx(w_sell(d), w_tick(d), sb), (int)w_qty(d));
+      }
+      if (traced && P.dec_trace && sdec < P.trace_steps)
+        P.dec_trace[(size_t)sdec * P.dec_trace_agents + (size_t)(aoff + a0 + k)] = d;
+    }
+  }
+}
+
+// Resting depth around tick nl from the book (the policy inputs): each entry
+// has exactly one writer, the owner of its tick or thread 0 off the grid.
+__device__ __forceinline__ void publish_depth(const Smem& sm, const int32_t* book, int sb, int L, int nl, int p0,
+                                              int LT, int t) {
+  for (int i = 0; i < LT; ++i) {
+    const int p = p0 + i;
+    if (p < L) {
+      if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = book[bidx(1, p, sb)];
+      if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = book[bidx(0, p, sb)];
+    }
+  }
+  if (t == 0) {
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+      if (nl + k >= L) sm.feat[k - 1] = 0;
+      if (nl - k < 0) sm.feat[4 + k - 1] = 0;
+    }
+  }
+}
+
 // Runs steps [s0, s0 + n_steps) of market m.  t: thread index in the group,
 // bar: the group's barrier id, Lcap: the largest L the group's shared memory
 // (sm) was carved for.
-template <int NT, int AK, bool AGGR>
+template <int NT, int AK, bool AGGR, bool MLP = false>
 __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t n_steps, const Smem& sm, int t,
-                           int bar, int Lcap) {
+                           int bar, int Lcap, MlpWG* mw = nullptr, const unsigned char* sw = nullptr) {
+  static_assert(!(MLP && AGGR), "policy kernels use plain shared atomics");
+  static_assert(!MLP || (NT >= 128 && NT % 128 == 0), "policy groups are whole warpgroups");
   const int lane = t & 31;
   const int wid = t >> 5;
   const int L = P.Ls ? P.Ls[m] : P.L_all;
@@ -241,12 +386,39 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   const uint32_t gm = P.market_base + m;
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
 
+  const bool policy_on = MLP && P.mlp != nullptr && P.mlp_pct > 0;
+  StepFeat sf;
+  if constexpr (MLP) {
+    // the policy inputs of the first step read the rebuilt book
+    gsync<NT>(bar);
+    publish_depth(sm, book, sb, L, last, p0, LT, t);
+    gsync<NT>(bar);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sf.h[j] = hist[j] - hist[j + 1];
+    sf.lastv = lastv;
+    sf.depth = sm.feat;
+  }
+
   // orders of the first step
   if (n_steps > 0) {
     const StepRules sr = step_rules(P, s0, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+    uint32_t pflags = 0;
 #pragma unroll
-    for (int k = 0; k < AK; ++k)
-      slot[k] = order_agent<AGGR>(slot[k], a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+    for (int k = 0; k < AK; ++k) {
+      if constexpr (MLP) {
+        bool pol = false;
+        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb, &pol, &P,
+                                          &sf, sm.inv[k * NT + t]);
+        pflags |= pol ? (1u << k) : 0u;
+      } else {
+        slot[k] = order_agent<AGGR>(slot[k], a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+      }
+    }
+    if constexpr (MLP) {
+      if (policy_on)
+        policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s0, gm, sf, last, aoff, traced, book,
+                             sb);
+    }
   }
 
   for (uint32_t j = 0; j < n_steps; ++j) {
@@ -359,6 +531,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
         }
       }
     }
+    if constexpr (MLP) publish_depth(sm, book, sb, L, trade ? pstar : last, p0, LT, t);  // own ticks only
 
     // ---- marginal quantities in agent order --------------------------------------------
     uint32_t exB = 0, exS = 0;
@@ -409,6 +582,12 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     // ---- fills of step s, fused with the orders of step s+1 ------------------------------
     const bool more = j + 1 < n_steps;
     const StepRules sr = step_rules(P, s + 1, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+    if constexpr (MLP) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sf.h[q] = hist[q] - hist[q + 1];
+      sf.lastv = vstar;
+    }
+    uint32_t pflags = 0;
     if (trade) {
       const int Rb = sm.rem[0], Rs = sm.rem[1];
       int preB = (int)(exB + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMB[lane] : 0u));
@@ -432,7 +611,16 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
         }
         sl -= (uint32_t)f;
         if (!carry) sl &= W_STATIC;
-        if (more) sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+        if (more) {
+          if constexpr (MLP) {
+            bool pol = false;
+            sl = order_agent<AGGR, true>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb, &pol, &P, &sf,
+                                         sm.inv[k * NT + t]);
+            pflags |= pol ? (1u << k) : 0u;
+          } else {
+            sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+          }
+        }
         slot[k] = sl;
       }
     } else {
@@ -440,9 +628,23 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       for (int k = 0; k < AK; ++k) {
         uint32_t sl = slot[k];
         if (!carry) sl &= W_STATIC;
-        if (more) sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+        if (more) {
+          if constexpr (MLP) {
+            bool pol = false;
+            sl = order_agent<AGGR, true>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb, &pol, &P, &sf,
+                                         sm.inv[k * NT + t]);
+            pflags |= pol ? (1u << k) : 0u;
+          } else {
+            sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+          }
+        }
         slot[k] = sl;
       }
+    }
+    if constexpr (MLP) {
+      if (policy_on && more)
+        policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s + 1, gm, sf, last, aoff, traced,
+                             book, sb);
     }
   }
 

@@ -214,6 +214,60 @@ __device__ __forceinline__ void mlp_layer1(const unsigned char* sw, const float*
 }
 
 // ---------------------------------------------------------------------------------------------
+// CTA-level resources of the policy path: the weights (loaded once per
+// launch), one mbarrier per market group and the CTA's TMEM allocation
+// (64 columns per group).  Each group's activation buffer sits after its
+// market shared memory.
+// ---------------------------------------------------------------------------------------------
+constexpr int MLP_MAX_GROUPS = 16;
+__host__ __device__ constexpr uint32_t mlp_cta_bytes() {
+  return ((MLP_SM_BYTES + 127u) & ~127u) + 8u * MLP_MAX_GROUPS + 16u;
+}
+
+struct MlpCta {
+  unsigned char* sw;
+  uint64_t* bars;
+  uint32_t* tslot;
+  uint32_t cols;
+};
+
+__device__ __forceinline__ MlpCta mlp_cta_carve(unsigned char* raw, uint32_t cols) {
+  MlpCta c;
+  c.sw = raw;
+  c.bars = reinterpret_cast<uint64_t*>(raw + ((MLP_SM_BYTES + 127u) & ~127u));
+  c.tslot = reinterpret_cast<uint32_t*>(c.bars + MLP_MAX_GROUPS);
+  c.cols = cols;
+  return c;
+}
+
+// Whole CTA: TMEM allocation (warp 0), mbarriers (thread 0), weights.
+__device__ __forceinline__ void mlp_cta_setup(const MlpCta& c, const unsigned char* blob) {
+  if (threadIdx.x < 32) {
+    tmem_alloc(c.tslot, c.cols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < MLP_MAX_GROUPS; ++i) mbar_init(&c.bars[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (blob) mlp_load_weights(blob, c.sw, (int)threadIdx.x, (int)blockDim.x);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// Whole CTA: frees the TMEM columns once every group is done.
+__device__ __forceinline__ void mlp_cta_teardown(const MlpCta& c) {
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tmem_dealloc(*c.tslot, c.cols);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Decision of an MLP agent from its logits and its Philox stream-3 words:
 // inverse-CDF draws of side (w0) and tick offset (w1) from the softmax of
 // their heads, quantity clamp(round(exp(z[36])), 1, qmax).
@@ -235,6 +289,86 @@ __device__ __forceinline__ int mlp_sample(const float* z, int n, uint32_t w) {
     }
   }
   return pick;
+}
+
+
+// Writes columns [8 kc, 8 kc + 8) of row r of the activation operand as
+// high and low BF16 parts.
+__device__ __forceinline__ void mlp_store_split8(unsigned char* act, int r, int kc, const float* h) {
+  uint32_t hi[4], lo[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float a = h[2 * j], b = h[2 * j + 1];
+    hi[j] = pack_bf16x2(a, b);
+    const float ah = __uint_as_float(hi[j] << 16), bh = __uint_as_float(hi[j] & 0xFFFF0000u);
+    lo[j] = pack_bf16x2(a - ah, b - bh);
+  }
+  *reinterpret_cast<uint4*>(act + cm_offset(r, 8 * kc, MLP_H)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(act + MLP_ACT_HALF + cm_offset(r, 8 * kc, MLP_H)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+// Step-loop policy tile: layer 1 is c + W1[:, 8] * x_inv (c: the 64
+// pre-activations shared by the market's agents, x_inv: this row's inventory
+// input), layers 2-3 on the tensor cores, 16 accumulator columns at a time.
+// Returns the 37 logits of this thread's row.
+__device__ __forceinline__ void mlp_tile_logits(MlpWG& g, const unsigned char* sw, const float* cvec, float x_inv,
+                                                float* z, uint32_t* err) {
+  const int r = (int)(threadIdx.x & 127);
+  const float* w1 = reinterpret_cast<const float*>(sw + MLP_SM_W1);
+  const float* sb = reinterpret_cast<const float*>(sw + MLP_SM_B);
+  const uint32_t act_addr = smem_u32(g.act);
+  const uint32_t w_addr = smem_u32(sw);
+  const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) & 3) * 32u;
+#pragma unroll 1
+  for (int kc = 0; kc < MLP_H / 8; ++kc) {
+    float h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = fmaxf(fmaf(w1[(8 * kc + j) * MLP_IN + 8], x_inv, cvec[8 * kc + j]), 0.0f);
+    mlp_store_split8(g.act, r, kc, h);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  named_sync(g.bar_id, 128);
+  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W2, MLP_H);
+  mlp_wait(g, err);
+#pragma unroll 1
+  for (int c = 0; c < MLP_H / 16; ++c) {
+    float v[16];
+    tmem_ld16(g.tmem + (lane_base << 16) + (uint32_t)(16 * c), v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + sb[MLP_H + 16 * c + j], 0.0f);
+    mlp_store_split8(g.act, r, 2 * c, v);
+    mlp_store_split8(g.act, r, 2 * c + 1, v + 8);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  named_sync(g.bar_id, 128);
+  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W3, MLP_OUT_PAD);
+  mlp_wait(g, err);
+#pragma unroll
+  for (int c = 0; c < MLP_OUT_PAD / 16; ++c) {
+    float v[16];
+    tmem_ld16(g.tmem + (lane_base << 16) + (uint32_t)(16 * c), v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (16 * c + j < MLP_OUT) z[16 * c + j] = g.abort ? 0.0f : v[j] + sb[2 * MLP_H + 16 * c + j];
+  }
+  tc_fence_before();
+}
+
+// Order word of a policy decision (qty | side << 8 | tick << 9), or
+// KS_DECISION_PASS.  w: the agent's Philox stream-3 block for the step.
+__device__ __forceinline__ uint32_t mlp_decision(const float* z, uint4 w, int last, int L, int qmax) {
+  const int side = mlp_sample(z, MLP_NSIDE, w.x);
+  if (side == 2) return KS_DECISION_PASS;
+  const int oi = mlp_sample(z + MLP_NSIDE, MLP_NOFF, w.y);
+  float q = floorf(expf(z[MLP_OUT - 1]) + 0.5f);
+  q = (q >= 1.0f) ? q : 1.0f;  // also maps NaN to 1
+  q = fminf(q, (float)qmax);
+  const int tick = min(max(last + oi - MLP_OFF_MAX, 0), L - 1);
+  return (uint32_t)q | ((uint32_t)side << 8) | ((uint32_t)tick << 9);
 }
 
 }  // namespace ks

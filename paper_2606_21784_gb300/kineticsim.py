@@ -29,7 +29,11 @@ _STATUS = {0: "KS_OK", 1: "KS_ERR_INVALID_ARG", 2: "KS_ERR_WORKSPACE_TOO_SMALL",
 EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_state", "ks_write_state",
            "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
            "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
-           "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward")
+           "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward", "ks_set_capture")
+
+KS_RECORD_WORDS = 22
+KS_DECISION_PASS = 0x01000000
+KS_DECISION_NONE = 0xFFFFFFFF
 
 KS_MLP_PARAM_BYTES = 17696
 MLP_IN, MLP_H, MLP_OUT = 32, 64, 37
@@ -83,6 +87,12 @@ class ks_bucket(ctypes.Structure):
                 ("agents_per_thread", ctypes.c_int32)]
 
 
+class ks_capture(ctypes.Structure):
+    _fields_ = [("records", ctypes.c_void_p), ("record_capacity", ctypes.c_uint64),
+                ("record_agents", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
+                ("record_count", ctypes.c_void_p), ("decisions", ctypes.c_void_p)]
+
+
 class ks_batch_info(ctypes.Structure):
     _fields_ = [("batched", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("n_items", ctypes.c_int32),
                 ("n_buckets", ctypes.c_int32), ("grid", ctypes.c_int32), ("pad_", ctypes.c_int32),
@@ -129,6 +139,7 @@ def load(build_if_missing: bool = True):
         "ks_get_batch_info": ([vp, P(ks_batch_info)], ctypes.c_int),
         "ks_batch_variants": ([ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32)], ctypes.c_int),
         "ks_mlp_forward": ([vp, vp, ctypes.c_int64, vp, vp, vp], ctypes.c_int),
+        "ks_set_capture": ([vp, P(ks_capture)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -151,7 +162,7 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream
 
 
-def make_config(w: dict, trace_markets: int = 0, trace_steps: int = 0, L=None, A=None):
+def make_config(w: dict, trace_markets: int = 0, trace_steps: int = 0, L=None, A=None, mlp_params=None):
     """ks_config from a workload dict (see ``workloads``).  Returns (config, keepalive)."""
     from . import workloads
     p = w["params"]
@@ -183,7 +194,7 @@ def make_config(w: dict, trace_markets: int = 0, trace_steps: int = 0, L=None, A
     c.mr_offset_max = int(p["mr_offset_max"])
     c.rb_qmax = int(p["rb_qmax"])
     c.mlp_pct = int(p.get("mlp_pct", 0))
-    c.mlp_params = None
+    c.mlp_params = mlp_params.data_ptr() if mlp_params is not None else None
     c.tie_rule = int(p.get("tie_rule", 0))
     c.trace_markets = int(trace_markets)
     c.trace_steps = int(trace_steps)
@@ -358,10 +369,12 @@ class Ensemble:
     device workspace is a torch uint8 tensor held by this object.
     """
 
-    def __init__(self, workload: dict, trace_markets: int = 0, trace_steps: int = 0, stream=None, L=None, A=None):
+    def __init__(self, workload: dict, trace_markets: int = 0, trace_steps: int = 0, stream=None, L=None, A=None,
+                 mlp_params=None):
         import torch
         self.workload = workload
-        self.cfg, (self._keep, self.L, self.A) = make_config(workload, trace_markets, trace_steps, L, A)
+        self.mlp_params = mlp_params  # device blob kept alive for the kernels
+        self.cfg, (self._keep, self.L, self.A) = make_config(workload, trace_markets, trace_steps, L, A, mlp_params)
         self.M = int(workload["M"])
         self.N = int(self.A.astype(np.int64).sum())
         self.offsets = np.concatenate([[0], np.cumsum(self.A.astype(np.int64))])
@@ -396,6 +409,32 @@ class Ensemble:
 
     def batch_info(self):
         return ks_get_batch_info(self.handle)
+
+    def set_capture(self, record_agents: int = 0, record_capacity: int = 0, decisions: bool = False):
+        """Allocates capture buffers (torch, device) and enables them; returns them."""
+        import torch
+        c = ks_capture()
+        self.capture = {}
+        if record_agents > 0 and record_capacity > 0:
+            rec = torch.zeros((record_capacity, KS_RECORD_WORDS), dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            c.records, c.record_capacity, c.record_agents, c.record_count = \
+                rec.data_ptr(), record_capacity, record_agents, cnt.data_ptr()
+            self.capture.update(records=rec, record_count=cnt)
+        if decisions:
+            n_tr = int(self.offsets[self.trace_markets])
+            dec = torch.full((self.trace_steps, max(n_tr, 1)), -1, dtype=torch.int32, device="cuda")
+            c.decisions = dec.data_ptr()
+            self.capture["decisions"] = dec
+        _check(load().ks_set_capture(self.handle, ctypes.byref(c)), "ks_set_capture")
+        return self.capture
+
+    def records(self):
+        """Recorded rule decisions so far (numpy int32 [n, 22])."""
+        import torch
+        torch.cuda.synchronize()
+        n = min(int(self.capture["record_count"].item()), self.capture["records"].shape[0])
+        return self.capture["records"][:n].cpu().numpy()
 
     def sync(self, timeout_ms: int = 0, stream=None) -> int:
         return ks_sync(self.handle, stream, timeout_ms)
