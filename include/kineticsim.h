@@ -257,8 +257,9 @@ const char* ks_last_error(void);
 
 /*
  * Agent policy (learned agents).  A 32 -> 64 -> 64 -> 37 ReLU network: logits
- * 0-2 are the side (buy, sell, pass), 3-35 the tick offset -16..+16 relative to
- * the last clearing tick, 36 the log-quantity.  Parameter blob (device memory,
+ * 0-2 are the side (buy, sell, pass), 3-35 the tick offset k = -16..+16 from
+ * the last clearing tick counted toward the opposite side (a buy at last + k,
+ * a sell at last - k), 36 the log-quantity.  Parameter blob (device memory,
  * 16-byte aligned, KS_MLP_PARAM_BYTES bytes):
  *   offset     0: W1 bf16 [64][32]  (row = output unit, column = input)
  *   offset  4096: W2 bf16 [64][64]
@@ -278,8 +279,9 @@ const char* ks_last_error(void);
  *    KS_RECORD_WORDS int32: the policy's 18 raw inputs (eight clearing-tick
  *    returns, newest first; inventory; last executed volume; resting sell
  *    quantity at last+1..+4; resting buy quantity at last-1..-4), side,
- *    offset index (tick - last clamped to [-16, 16], plus 16), qty, agent
- *    class.  Records are appended in no particular order; *record_count
+ *    offset index (the tick offset toward the opposite side, tick - last for
+ *    a buy and last - tick for a sell, clamped to [-16, 16], plus 16), qty,
+ *    agent class.  Records are appended in no particular order; *record_count
  *    counts every attempt, records beyond `record_capacity` are dropped.
  *  - Policy decisions of the traced markets: decisions[s * traced_agents + g]
  *    for absolute step s < trace_steps and global agent id g of a market
@@ -334,6 +336,31 @@ ks_status ks_mlp_forward(const void* params, const float* X, int64_t n, float* Z
  */
 #define KS_NOALLOC_MAX_MARKETS 32768
 ks_status ks_step_n_noalloc(ks_ensemble* e, uint32_t n_steps, void* stream);
+
+/*
+ * Behaviour-cloning training of the policy (hand-written FP32 kernels).
+ * Parameter vector (FP32, device, KS_MLP_NPARAM floats):
+ *   W1[64][32], b1[64], W2[64][64], b2[64], W3[37][64], b3[37].
+ * Samples are rule-decision records (KS_RECORD_WORDS int32 each, see
+ * ks_capture) of markets with A agents; the inputs are normalised as in the
+ * step loop.  Per-sample loss: cross-entropy of the side (label record[18]),
+ * cross-entropy of the offset index (record[19]) and the squared error of the
+ * log-quantity (log record[20]).
+ */
+#define KS_MLP_NPARAM 8677
+
+/* grad += scale * d(sum of per-sample losses)/d params; *loss += scale * sum of
+ * the losses (both device FP32; the caller zeroes them). */
+ks_status ks_bc_grad(const float* params, const int32_t* records, int64_t n, int32_t A, float* grad, float* loss,
+                     float scale, void* stream);
+
+/* One Adam update (Kingma and Ba, 2015) with bias correction for step >= 1;
+ * m and v are the moment vectors; zeroes grad. */
+ks_status ks_adam_step(float* params, float* grad, float* m, float* v, int32_t step, float lr, float beta1,
+                       float beta2, float eps, void* stream);
+
+/* Writes the policy blob the step loop reads (BF16 weights, FP32 biases). */
+ks_status ks_mlp_export(const float* params, void* blob, void* stream);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 uint32_t ks_version(void);

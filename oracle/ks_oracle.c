@@ -356,6 +356,19 @@ int ko_mlp_loss_grad(const double* w, const double* X, const int32_t* side, cons
   return 0;
 }
 
+/* One Adam step (Kingma and Ba, ICLR 2015) with bias correction, step t >= 1:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * w -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void ko_adam_step(double* w, const double* g, double* m, double* v, int32_t n, int32_t t, double lr, double b1,
+                  double b2, double eps) {
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (int32_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
+
 /* Normalised policy input from the raw integer features of a decision:
  * raw[0..7]   last eight clearing-tick returns hist[j] - hist[j+1], newest first
  * raw[8]      the agent's inventory
@@ -389,7 +402,8 @@ static int ko_sample(const double* z, int n, uint32_t w) {
 }
 
 /* Action of the policy from logits z and the agent's stream-3 draw words:
- * side from w0, offset index from w1, quantity clamp(round(exp(z[36])), 1, qmax). */
+ * side from w0, offset index from w1 (offset = index - 16 ticks toward the
+ * opposite side), quantity clamp(round(exp(z[36])), 1, qmax). */
 void ko_mlp_action(const double* z, const uint32_t w[4], int32_t qmax, int32_t* side, int32_t* offset_idx,
                    int32_t* qty) {
   *side = ko_sample(z, KO_NSIDE, w[0]);
@@ -518,8 +532,9 @@ typedef struct {
  *              compared with the policy's (mlp_checked / mlp_mismatch);
  *  rec_agents: rule decisions of agents a < rec_agents are recorded as
  *              KO_REC_WORDS int32 each: raw features (KO_NRAW), side,
- *              offset index (tick - last clamped to [-16, 16], plus 16), qty,
- *              agent class. */
+ *              offset index, qty, agent class.  The offset counts toward
+ *              the opposite side (tick - last for a buy, last - tick for a
+ *              sell), clamped to [-16, 16], plus 16. */
 #define KO_REC_WORDS (KO_NRAW + 4)
 typedef struct {
   const double* mlp_w;
@@ -559,7 +574,9 @@ static void ko_mlp_decide(const ko_params* P, const double* w, uint32_t m, int32
   ko_draw(P->seed, s, (uint32_t)a, m, 3u, u);
   int32_t oi;
   ko_mlp_action(z, u, P->rb_qmax, side, &oi, qty);
-  *tick = ko_clamp((int64_t)last + (oi - KO_OFF_MAX), 0, L - 1);
+  /* the offset counts toward the opposite side: up for a buy, down for a sell */
+  const int32_t k = oi - KO_OFF_MAX;
+  *tick = ko_clamp((int64_t)last + (*side == 1 ? -k : k), 0, L - 1);
 }
 
 /* Run steps [s0, s0 + n) of market m.  trace_p / trace_v (nullable, length n)
@@ -628,7 +645,7 @@ int ko_run_market(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agent
         int32_t* r = opt->rec_out + opt->rec_count * KO_REC_WORDS;
         memcpy(r, raw_mkt, sizeof(raw_mkt));
         r[8] = ag->inv[a];
-        int32_t off = ag->tick[a] - ms->last;
+        int32_t off = ag->side[a] == 1 ? ms->last - ag->tick[a] : ag->tick[a] - ms->last;
         off = off < -KO_OFF_MAX ? -KO_OFF_MAX : (off > KO_OFF_MAX ? KO_OFF_MAX : off);
         r[KO_NRAW + 0] = ag->side[a];
         r[KO_NRAW + 1] = off + KO_OFF_MAX;

@@ -137,6 +137,10 @@ def _load():
             lib.ko_mlp_action.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32),
                                           P(ctypes.c_int32), P(ctypes.c_int32)]
             lib.ko_mlp_action.restype = None
+            lib.ko_adam_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double]
+            lib.ko_adam_step.restype = None
             _lib = lib
     return _lib
 
@@ -364,6 +368,13 @@ def mlp_loss_grad(w, X, side, offset, logq):
     if rc != 0:
         raise ValueError(rc)
     return float(loss.value), g
+
+
+def adam_step(w, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One fp64 Adam step in place on w, m, v."""
+    for a in (w, g, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    _load().ko_adam_step(_ptr(w), _ptr(g), _ptr(m), _ptr(v), w.size, int(t), lr, b1, b2, eps)
 
 
 def mlp_features(raw, A: int) -> np.ndarray:

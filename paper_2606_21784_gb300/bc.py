@@ -1,0 +1,150 @@
+"""Behaviour cloning of the agent policy from the rule-based simulator.
+
+1. ``generate``: runs the rule-based 8192-market configuration (L=1024,
+   A=4096, 60/20/20 agent mix, carried book) with seed 7 on the GPU and
+   records the new orders of the first ``record_agents`` agents of every
+   market (features and action) until ``n_pairs`` records are collected.
+2. ``train``: minibatch Adam on the records with the library's hand-written
+   forward/backward kernels (``ks_bc_grad``, ``ks_adam_step``).
+3. ``evaluate`` / ``action_match``: held-out loss, and agreement of the
+   policy's most likely side and offset with the rule agents' choices.
+4. ``export``: the BF16 blob the step loop reads.
+
+Python only orchestrates: every forward, backward and update runs in the
+CUDA kernels of the library.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import kineticsim as ks
+from . import workloads
+
+DECISIONS_PER_AGENT_STEP = 0.25  # lower bound of the rule agents' order rate (measured ~0.29)
+
+
+def generate(n_pairs: int = 20_000_000, seed: int = 7, record_agents: int = 64, steps: int = 2000,
+             markets: int | None = None):
+    """Records of rule decisions (device int32 [n, 22]) and the workload used."""
+    import torch
+    w = workloads.workload("plain_mix_8192", seed=seed)
+    if markets is None:
+        markets = int(math.ceil(n_pairs / (DECISIONS_PER_AGENT_STEP * record_agents * steps)))
+    w["M"] = markets
+    w["S"] = steps
+    ens = ks.Ensemble(w)
+    cap = ens.set_capture(record_agents=record_agents, record_capacity=n_pairs)
+    ens.step(steps)
+    if ens.sync(timeout_ms=600_000) != ks.KS_OK:
+        raise RuntimeError("data generation run reported a device error")
+    torch.cuda.synchronize()
+    n = min(int(cap["record_count"].item()), n_pairs)
+    rec = cap["records"][:n]
+    ens.close()
+    return rec, w
+
+
+def init_params(seed: int = 0, device="cuda"):
+    """He-normal weights, zero biases (log-quantity bias at log 30)."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    parts = []
+    for fan_out, fan_in in ((64, 32), (64, 64), (37, 64)):
+        parts.append(torch.randn(fan_out * fan_in, generator=g) * math.sqrt(2.0 / fan_in))
+        b = torch.zeros(fan_out)
+        if fan_out == 37:
+            b[36] = math.log(30.0)
+        parts.append(b)
+    return torch.cat(parts).float().to(device).contiguous()
+
+
+def marginal_params(records, device="cuda"):
+    """Zero weights; biases = log label frequencies and the mean log-quantity:
+    the best policy that ignores its inputs."""
+    import torch
+    r = records.long()
+    side = torch.bincount(r[:, 18], minlength=3).double() + 1e-3
+    off = torch.bincount(r[:, 19], minlength=33).double() + 1e-3
+    b3 = torch.cat([torch.log(side / side.sum()), torch.log(off / off.sum()),
+                    torch.log(r[:, 20].double()).mean().reshape(1)])
+    p = torch.zeros(ks.KS_MLP_NPARAM, dtype=torch.float64)
+    p[-37:] = b3.cpu()
+    return p.float().to(device).contiguous()
+
+
+def evaluate(params, records, A: int, chunk: int = 1 << 20) -> float:
+    """Mean loss of ``params`` over ``records``."""
+    import torch
+    n = records.shape[0]
+    grad = torch.zeros(ks.KS_MLP_NPARAM, dtype=torch.float32, device=params.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+    for i in range(0, n, chunk):
+        ks.ks_bc_grad(params, records[i:i + chunk].contiguous(), A, grad, loss, 1.0 / n)
+    torch.cuda.synchronize()
+    return float(loss.item())
+
+
+def features(records, A: int):
+    """Normalised policy inputs of records (device float32 [n, 32])."""
+    import torch
+    r = records.float()
+    X = torch.zeros((records.shape[0], 32), dtype=torch.float32, device=records.device)
+    X[:, :8] = r[:, :8] / 8.0
+    X[:, 8] = r[:, 8] / 256.0
+    X[:, 9] = r[:, 9] / (8.0 * A)
+    X[:, 10:18] = r[:, 10:18] / (4.0 * A)
+    return X
+
+
+def action_match(blob, records, A: int) -> dict:
+    """Agreement of the policy's most likely side / offset with the recorded actions
+    (logits from the tensor-core forward)."""
+    Z, err = ks.ks_mlp_forward(blob, features(records, A))
+    side = Z[:, :3].argmax(1)
+    off = Z[:, 3:36].argmax(1)
+    r = records.long()
+    return {"side": float((side == r[:, 18]).float().mean()), "offset": float((off == r[:, 19]).float().mean()),
+            "error_word": int(err.item())}
+
+
+def train(records, A: int, epochs: int = 2, batch: int = 16384, lr: float = 2e-3, val_frac: float = 0.02,
+          seed: int = 0, params=None, log=None):
+    """Adam on the records; returns (params, history)."""
+    import torch
+    dev = records.device
+    n = records.shape[0]
+    g = torch.Generator(device=dev).manual_seed(seed)
+    perm = torch.randperm(n, generator=g, device=dev)
+    n_val = max(1, int(n * val_frac))
+    val = records[perm[:n_val]].contiguous()
+    tr_idx = perm[n_val:]
+    params = init_params(seed, dev) if params is None else params.clone()
+    grad = torch.zeros_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    hist = {"val_loss": [evaluate(params, val, A)], "train_loss": []}
+    step = 0
+    for ep in range(epochs):
+        order = tr_idx[torch.randperm(tr_idx.shape[0], generator=g, device=dev)]
+        loss.zero_()
+        seen = 0
+        for i in range(0, order.shape[0], batch):
+            idx = order[i:i + batch]
+            bs = idx.shape[0]
+            ks.ks_bc_grad(params, records[idx].contiguous(), A, grad, loss, 1.0 / bs)
+            step += 1
+            ks.ks_adam_step(params, grad, m, v, step, lr)
+            seen += 1
+        torch.cuda.synchronize()
+        hist["train_loss"].append(float(loss.item()) / max(seen, 1))
+        hist["val_loss"].append(evaluate(params, val, A))
+        if log:
+            log(f"epoch {ep}: train {hist['train_loss'][-1]:.4f} val {hist['val_loss'][-1]:.4f}")
+    return params, hist, val
+
+
+def export(params):
+    return ks.ks_mlp_export(params)

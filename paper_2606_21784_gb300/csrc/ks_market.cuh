@@ -149,7 +149,8 @@ __device__ __forceinline__ void record_decision(const DevParams& P, const StepFe
 #pragma unroll
   for (int j = 0; j < 8; ++j) r[10 + j] = f.depth[j];
   r[18] = (int)w_sell(w);
-  r[19] = min(max((int)w_tick(w) - last, -MLP_OFF_MAX), MLP_OFF_MAX) + MLP_OFF_MAX;
+  const int toward = w_sell(w) ? last - (int)w_tick(w) : (int)w_tick(w) - last;  // toward the opposite side
+  r[19] = min(max(toward, -MLP_OFF_MAX), MLP_OFF_MAX) + MLP_OFF_MAX;
   r[20] = (int)w_qty(w);
   r[21] = (int)w_class(w);
 }

@@ -367,7 +367,8 @@ __device__ __forceinline__ uint32_t mlp_decision(const float* z, uint4 w, int la
   float q = floorf(expf(z[MLP_OUT - 1]) + 0.5f);
   q = (q >= 1.0f) ? q : 1.0f;  // also maps NaN to 1
   q = fminf(q, (float)qmax);
-  const int tick = min(max(last + oi - MLP_OFF_MAX, 0), L - 1);
+  const int k = oi - MLP_OFF_MAX;  // ticks toward the opposite side: up for a buy, down for a sell
+  const int tick = min(max(last + (side ? -k : k), 0), L - 1);
   return (uint32_t)q | ((uint32_t)side << 8) | ((uint32_t)tick << 9);
 }
 

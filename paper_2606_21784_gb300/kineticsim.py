@@ -29,7 +29,9 @@ _STATUS = {0: "KS_OK", 1: "KS_ERR_INVALID_ARG", 2: "KS_ERR_WORKSPACE_TOO_SMALL",
 EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_state", "ks_write_state",
            "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
            "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
-           "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward", "ks_set_capture")
+           "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward", "ks_set_capture", "ks_bc_grad",
+           "ks_adam_step", "ks_mlp_export")
+KS_MLP_NPARAM = 8677
 
 KS_RECORD_WORDS = 22
 KS_DECISION_PASS = 0x01000000
@@ -140,6 +142,10 @@ def load(build_if_missing: bool = True):
         "ks_batch_variants": ([ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32)], ctypes.c_int),
         "ks_mlp_forward": ([vp, vp, ctypes.c_int64, vp, vp, vp], ctypes.c_int),
         "ks_set_capture": ([vp, P(ks_capture)], ctypes.c_int),
+        "ks_bc_grad": ([vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "ks_adam_step": ([vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, vp], ctypes.c_int),
+        "ks_mlp_export": ([vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -318,6 +324,24 @@ def ks_mlp_forward(params_blob, X, err=None, stream=None):
     _check(load().ks_mlp_forward(params_blob.data_ptr(), X.data_ptr(), n, Z.data_ptr(), err.data_ptr(),
                                  _stream_ptr(stream)), "ks_mlp_forward")
     return Z, err
+
+
+def ks_bc_grad(params, records, A: int, grad, loss, scale: float, stream=None):
+    _check(load().ks_bc_grad(params.data_ptr(), records.data_ptr(), records.shape[0], int(A), grad.data_ptr(),
+                             loss.data_ptr(), float(scale), _stream_ptr(stream)), "ks_bc_grad")
+
+
+def ks_adam_step(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().ks_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), _stream_ptr(stream)), "ks_adam_step")
+
+
+def ks_mlp_export(params, blob=None, stream=None):
+    import torch
+    if blob is None:
+        blob = torch.zeros(KS_MLP_PARAM_BYTES, dtype=torch.uint8, device=params.device)
+    _check(load().ks_mlp_export(params.data_ptr(), blob.data_ptr(), _stream_ptr(stream)), "ks_mlp_export")
+    return blob
 
 
 KS_PROBE_SMEM_RED, KS_PROBE_MUL_WIDE, KS_PROBE_PHILOX = 0, 1, 2

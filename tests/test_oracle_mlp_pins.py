@@ -124,7 +124,12 @@ def test_recorded_rule_decisions_describe_the_new_orders():
         assert len(rec) == len(new)
         for r, a in zip(rec, new):
             assert list(r[:8]) == [int(hist[j] - hist[j + 1]) for j in range(8)]
-            assert r[18] in (0, 1) and 0 <= r[19] <= 32 and 1 <= r[20] <= 100
             assert r[21] == mk.atype[a]
-            off = int(np.clip(r[19] - 16, -16, 16))
-            assert r[19] - 16 == off
+            # a recorded order that rested is still the agent's working order
+            if mk.qty[a] > 0 and mk.qty[a] == r[20]:
+                assert r[18] == mk.side[a]
+                toward = (last - mk.tick[a]) if mk.side[a] == 1 else (mk.tick[a] - last)
+                assert r[19] == int(np.clip(toward, -16, 16)) + 16
+            assert r[18] in (0, 1) and 0 <= r[19] <= 32 and 1 <= r[20] <= 100
+            if r[21] != o.ZI:  # momentum / mean-reversion orders go through the price
+                assert 16 <= r[19] <= 24
