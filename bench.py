@@ -266,6 +266,54 @@ def compare_forms(ks, workloads, stream, plain_rate):
     except Exception as e:  # the tuned plan is optional; the default plan was measured above
         out["batched_20000_tuned"] = {"error": str(e)[:200]}
     ens.close()
+    out.update(learned_forms(ks, workloads, stream))
+    return out
+
+
+def learned_forms(ks, workloads, stream):
+    """The learned-agent forms: a policy trained by behaviour cloning on 2M
+    (state, action) pairs of the rule-based seed-7 run (a reduced data budget
+    to keep the bench short; the full 20M-pair run is `python -m
+    paper_2606_21784_gb300.bc`), then (a) the 4096-market all-policy ensemble
+    and (b) the 32768-market uneven ensemble with 25% policy agents beside the
+    same instances with rule agents only."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2606_21784_gb300 import bc
+    out = {}
+    t0 = time.time()
+    rec, wd = bc.generate(2_000_000)
+    params, hist, _ = bc.train(rec, wd["A"], epochs=1)
+    blob = bc.export(params)
+    del rec
+    torch.cuda.synchronize()
+    out["bc"] = {"pairs": 2_000_000, "seconds": time.time() - t0, "val_loss": hist["val_loss"]}
+    steps = 200
+    w = workloads.workload("learned_4096")
+    ens = ks.Ensemble(w, mlp_params=blob)
+    cap = ens.set_capture(count_policy=True)
+    ev = float(w["M"]) * w["A"] * steps
+    ens.step(20, stream)
+    torch.cuda.synchronize()
+    cap["policy_count"].zero_()
+    dt = _time_ensemble(ens, steps, stream)
+    dec = float(cap["policy_count"].item()) * steps / (steps + steps // 10)  # warm-up steps excluded
+    flop = dec * 2 * 2 * (64 * 64 + 64 * 48)  # layers 2-3, high + low operand parts
+    out["learned_4096"] = {"events_per_s": ev / dt, "steps": steps, "policy_decisions_per_s": dec / dt,
+                           "tensor_tflops": flop / dt / 1e12, "launch": ens.get_launch()}
+    ens.close()
+    w = workloads.workload("mixed_32768")
+    L, A = workloads.sizes(w)
+    ev = float(A.astype(np.int64).sum()) * steps
+    for pct in (25, 0):
+        ww = workloads.workload("mixed_32768", mlp_pct=pct)
+        e2 = ks.Ensemble(ww, L=L, A=A, mlp_params=blob if pct else None)
+        out[f"mixed_32768_policy{pct}"] = {"events_per_s": ev / _time_ensemble(e2, steps, stream), "steps": steps,
+                                           "cta_threads": e2.batch_info()["cta_threads"]}
+        e2.close()
     return out
 
 

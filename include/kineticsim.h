@@ -298,6 +298,7 @@ typedef struct ks_capture {
   uint32_t pad_;
   unsigned long long* record_count;
   uint32_t* decisions;
+  unsigned long long* policy_count;  /* device counter += policy decisions evaluated (NULL = off) */
 } ks_capture;
 
 /* Sets the ensemble's captures (NULL fields switch a capture off).  Capturing

@@ -148,3 +148,41 @@ def train(records, A: int, epochs: int = 2, batch: int = 16384, lr: float = 2e-3
 
 def export(params):
     return ks.ks_mlp_export(params)
+
+
+def main(argv=None):
+    """Full pipeline: 20M pairs from the seed-7 rule-based run, training, report."""
+    import argparse
+    import json
+    import time
+
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--pairs", type=int, default=20_000_000)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--out", default="")
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    rec, w = generate(a.pairs)
+    t1 = time.time()
+    params, hist, val = train(rec, w["A"], epochs=a.epochs, batch=a.batch, lr=a.lr, log=print)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    blob = export(params)
+    rep = {"pairs": int(rec.shape[0]), "markets": w["M"], "generate_s": t1 - t0, "train_s": t2 - t1,
+           "history": hist, "held_out_loss": {"trained": evaluate(params, val, w["A"]),
+                                              "marginal": evaluate(marginal_params(rec), val, w["A"]),
+                                              "untrained": evaluate(init_params(0), val, w["A"])},
+           "action_match": {"trained": action_match(blob, val, w["A"]),
+                            "marginal": action_match(export(marginal_params(rec)), val, w["A"])}}
+    print(json.dumps(rep))
+    if a.out:
+        with open(a.out, "wb") as f:
+            f.write(blob.cpu().numpy().tobytes())
+    return rep
+
+
+if __name__ == "__main__":
+    main()

@@ -796,6 +796,7 @@ ks_status ks_set_capture(ks_ensemble* e, const ks_capture* c) {
   p.rec_cap = c->records ? c->record_capacity : 0;
   p.rec_agents = c->records ? c->record_agents : 0;
   p.dec_trace = c->decisions;
+  p.pol_count = c->policy_count;
   const bool want = e->cfg.mlp_pct > 0 || c->records != nullptr || c->decisions != nullptr;
   if (want == e->mlp) return KS_OK;
   // switch between the rule-only and the policy-capable kernels, keeping the mode

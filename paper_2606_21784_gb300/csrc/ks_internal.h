@@ -60,6 +60,7 @@ struct DevParams {
   uint64_t rec_cap;
   uint32_t rec_agents;       // record agents a < rec_agents of every market
   uint32_t* dec_trace;       // [trace_steps][dec_trace_agents] policy decisions of traced markets
+  unsigned long long* pol_count;  // policy decisions evaluated
   uint64_t dec_trace_agents; // agents of markets 0..trace_markets-1
 };
 

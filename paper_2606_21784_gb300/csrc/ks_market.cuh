@@ -248,6 +248,7 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
   for (int k = 0; k < AK; ++k)
     if ((pflags >> k) & 1u) sm.rowbuf[r++] = (uint32_t)(a0 + k);
   gsync<NT>(bar);
+  if (t == 0 && total > 0 && P.pol_count) atomicAdd(P.pol_count, (unsigned long long)total);
   if (total > 0 && t < 128) {
     for (int tile = 0; tile * 128 < total; ++tile) {
       const int row = tile * 128 + t;

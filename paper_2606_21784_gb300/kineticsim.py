@@ -92,7 +92,8 @@ class ks_bucket(ctypes.Structure):
 class ks_capture(ctypes.Structure):
     _fields_ = [("records", ctypes.c_void_p), ("record_capacity", ctypes.c_uint64),
                 ("record_agents", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
-                ("record_count", ctypes.c_void_p), ("decisions", ctypes.c_void_p)]
+                ("record_count", ctypes.c_void_p), ("decisions", ctypes.c_void_p),
+                ("policy_count", ctypes.c_void_p)]
 
 
 class ks_batch_info(ctypes.Structure):
@@ -434,7 +435,8 @@ class Ensemble:
     def batch_info(self):
         return ks_get_batch_info(self.handle)
 
-    def set_capture(self, record_agents: int = 0, record_capacity: int = 0, decisions: bool = False):
+    def set_capture(self, record_agents: int = 0, record_capacity: int = 0, decisions: bool = False,
+                    count_policy: bool = False):
         """Allocates capture buffers (torch, device) and enables them; returns them."""
         import torch
         c = ks_capture()
@@ -445,6 +447,10 @@ class Ensemble:
             c.records, c.record_capacity, c.record_agents, c.record_count = \
                 rec.data_ptr(), record_capacity, record_agents, cnt.data_ptr()
             self.capture.update(records=rec, record_count=cnt)
+        if count_policy:
+            pc = torch.zeros(1, dtype=torch.int64, device="cuda")
+            c.policy_count = pc.data_ptr()
+            self.capture["policy_count"] = pc
         if decisions:
             n_tr = int(self.offsets[self.trace_markets])
             dec = torch.full((self.trace_steps, max(n_tr, 1)), -1, dtype=torch.int32, device="cuda")
