@@ -24,10 +24,11 @@ __device__ __forceinline__ uint32_t w_sell(uint32_t w) { return (w >> 8) & 1u; }
 __device__ __forceinline__ uint32_t w_tick(uint32_t w) { return (w >> W_TICK_SHIFT) & W_TICK; }
 __device__ __forceinline__ uint32_t w_class(uint32_t w) { return (w >> W_CLASS_SHIFT) & 3u; }
 
-// Book index with one pad word per 32 ticks, so that threads owning
-// contiguous power-of-two tick ranges hit distinct shared-memory banks.
-__device__ __forceinline__ int book_idx(int p) { return p + (p >> 5); }
-__host__ __device__ __forceinline__ int book_len(int L) { return L + (L >> 5) + 1; }
+// Length of one half (BUY or SELL) of a market's book in shared memory:
+// rounded to 16 ticks so that both halves start 64-byte aligned and a thread
+// can load its contiguous ticks with vector accesses (contiguous vector
+// accesses across a warp are free of bank conflicts).
+__host__ __device__ __forceinline__ int book_len(int L) { return (L + 15) & ~15; }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Round: with products

@@ -99,9 +99,7 @@ __device__ __forceinline__ void gsync(int bar) {
   }
 }
 
-__device__ __forceinline__ int bidx(uint32_t sell, uint32_t tick, int sb) {
-  return (int)(tick + (tick >> 5)) + (sell ? sb : 0);
-}
+__device__ __forceinline__ int bidx(uint32_t sell, uint32_t tick, int sb) { return (int)tick + (sell ? sb : 0); }
 
 // Add the order word's quantity at its (side, tick).  With AGGR, lanes of the
 // warp holding the same (side, tick) first combine their quantities
@@ -199,12 +197,6 @@ __device__ __forceinline__ int hist_at(const int (&hist)[KS_HISTORY], int lb) {
   return h;
 }
 
-// Signed distance of an order from its side's marginal tick: > 0 fills fully,
-// 0 is at the marginal tick, < 0 does not trade.
-__device__ __forceinline__ int fill_dist(uint32_t sl, int p_lo, int p_hi) {
-  const int tk = (int)w_tick(sl);
-  return w_sell(sl) ? (p_lo - tk) : (tk - p_hi);
-}
 
 // Policy decisions of one step for the agents flagged in `pflags` (bit k =
 // agent a0 + k): rows are compacted in agent order, the group's first
@@ -299,6 +291,242 @@ __device__ __forceinline__ void publish_depth(const Smem& sm, const int32_t* boo
   }
 }
 
+// ---------------------------------------------------------------------------
+// One clearing of the book (Eq. 1-2, Phase 4) and the residual update
+// (Phase 5).  The thread owns ticks [p0, p0 + LT).  LTC > 0: LT == LTC and
+// the ticks are loaded once with vector accesses and kept in registers;
+// LTC == 0: any LT, scalar accesses.
+// ---------------------------------------------------------------------------
+struct ClearOut {
+  int vstar, p_lo, p_hi, pstar;
+};
+
+template <int N>
+__device__ __forceinline__ void ld_ticks(const int32_t* src, int* v) {
+  if constexpr (N == 1) {
+    v[0] = src[0];
+  } else if constexpr (N == 2) {
+    const int2 a = *reinterpret_cast<const int2*>(src);
+    v[0] = a.x; v[1] = a.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      const int4 a = *reinterpret_cast<const int4*>(src + i);
+      v[i] = a.x; v[i + 1] = a.y; v[i + 2] = a.z; v[i + 3] = a.w;
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void st_ticks(int32_t* dst, const int* v) {
+  if constexpr (N == 1) {
+    dst[0] = v[0];
+  } else if constexpr (N == 2) {
+    *reinterpret_cast<int2*>(dst) = make_int2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i += 4) *reinterpret_cast<int4*>(dst + i) = make_int4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  }
+}
+
+template <int NT, int LTC, bool FEAT>
+__device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, int sb, int L, int LT, int p0, int t,
+                                               int bar, unsigned long long* kx, unsigned long long* kx_next,
+                                               bool tie1, bool carry, int last) {
+  const int lane = t & 31;
+  const int wid = t >> 5;
+  constexpr int R = LTC > 0 ? LTC : 1;
+  int bv[R], sv[R];
+  const bool mine = p0 < L;  // vector path: all LTC ticks of an owning thread lie in the grid
+  int sumB = 0, sumS = 0;
+  if constexpr (LTC > 0) {
+    if (mine) {
+      ld_ticks<LTC>(book + p0, bv);
+      ld_ticks<LTC>(book + sb + p0, sv);
+    } else {
+#pragma unroll
+      for (int i = 0; i < LTC; ++i) bv[i] = sv[i] = 0;
+    }
+#pragma unroll
+    for (int i = 0; i < LTC; ++i) {
+      sumB += bv[i];
+      sumS += sv[i];
+    }
+  } else {
+    for (int i = 0; i < LT; ++i) {
+      const int p = p0 + i;
+      if (p < L) {
+        sumB += book[p];
+        sumS += book[sb + p];
+      }
+    }
+  }
+  int sufB = sumB, preS = sumS;  // inclusive warp suffix (BUY) / prefix (SELL) scans
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int vb = __shfl_down_sync(0xffffffffu, sufB, d);
+    const int vs = __shfl_up_sync(0xffffffffu, preS, d);
+    if (lane + d < 32) sufB += vb;
+    if (lane >= d) preS += vs;
+  }
+  if (lane == 0) sm.wD[wid] = sufB;
+  if (lane == 31) sm.wS[wid] = preS;
+  gsync<NT>(bar);  // B2
+  const int offD = (int)__reduce_add_sync(0xffffffffu, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
+  const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
+  const int D0 = offD + sufB;          // D_cum at my first tick
+  const int Sb0 = offS + preS - sumS;  // S_cum just below my first tick
+  {
+    int D = D0, Sb = Sb0;
+    int bestV = -1, lo = 4095, hi = 0;
+    unsigned long long kT = 0ull;
+    const int n = LTC > 0 ? (mine ? LTC : 0) : LT;
+#pragma unroll
+    for (int i = 0; i < (LTC > 0 ? LTC : 1); ++i) {
+      // LTC == 0 runs this body in the loop below instead
+      if (LTC > 0 && i < n) {
+        const int p = p0 + i;
+        const int S = Sb + sv[i];
+        const int v = min(D, S);
+        if (v > bestV) { bestV = v; lo = p; }
+        if (v >= bestV) hi = p;
+        if (tie1) {
+          const int imb = min(abs(D - S), (1 << 22) - 1);
+          const unsigned long long tk = ((unsigned long long)(uint32_t)v << 34) |
+                                        ((unsigned long long)((1 << 22) - 1 - imb) << 12) | (4095u - p);
+          kT = tk > kT ? tk : kT;
+        }
+        D -= bv[i];
+        Sb = S;
+      }
+    }
+    if constexpr (LTC == 0) {
+      for (int i = 0; i < LT; ++i) {
+        const int p = p0 + i;
+        if (p < L) {
+          const int b = book[p];
+          const int S = Sb + book[sb + p];
+          const int v = min(D, S);
+          if (v > bestV) { bestV = v; lo = p; }
+          if (v >= bestV) hi = p;
+          if (tie1) {
+            const int imb = min(abs(D - S), (1 << 22) - 1);
+            const unsigned long long tk = ((unsigned long long)(uint32_t)v << 34) |
+                                          ((unsigned long long)((1 << 22) - 1 - imb) << 12) | (4095u - p);
+            kT = tk > kT ? tk : kT;
+          }
+          D -= b;
+          Sb = S;
+        }
+      }
+    }
+    const int vw = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(bestV, 0));
+    const bool top = bestV == vw;
+    const uint32_t low = __reduce_min_sync(0xffffffffu, top ? (unsigned)lo : 4095u);
+    const uint32_t high = __reduce_max_sync(0xffffffffu, top ? (unsigned)hi : 0u);
+    if (tie1) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, kT, d);
+        kT = o > kT ? o : kT;
+      }
+    }
+    if (lane == 0) {
+      atomicMax(kx + 0, ((unsigned long long)(uint32_t)vw << 12) | (4095u - low));
+      atomicMax(kx + 1, ((unsigned long long)(uint32_t)vw << 12) | high);
+      if (tie1) atomicMax(kx + 2, kT);
+    }
+  }
+  gsync<NT>(bar);  // B3
+  ClearOut c;
+  const unsigned long long kLo = kx[0], kHi = kx[1];
+  c.vstar = (int)(kLo >> 12);
+  c.p_lo = 4095 - (int)(kLo & 4095u);
+  c.p_hi = (int)(kHi & 4095u);
+  c.pstar = tie1 ? 4095 - (int)(kx[2] & 4095u) : c.p_lo;
+  const bool trade = c.vstar > 0;
+  if (t < 4) kx_next[t] = 0ull;  // reset the other parity for the next step
+
+  // Residual book per tick, without atomics (Phase 5): the owners of the
+  // marginal ticks publish R_b = V* - D_cum[p_hi + 1] and R_s = V* - S_cum[p_lo - 1];
+  // a carried book keeps what did not trade, a discarded book is emptied.
+  const int nl = trade ? c.pstar : last;  // last clearing tick after this step (policy depth)
+  if constexpr (LTC > 0) {
+    if (mine) {
+      int D = D0, Sb = Sb0;
+#pragma unroll
+      for (int i = 0; i < LTC; ++i) {
+        const int p = p0 + i;
+        const int b = bv[i], s = sv[i];
+        int nb = b, ns = s;
+        if (trade || !carry) {
+          const int rb = c.vstar - (D - b);
+          const int rs = c.vstar - Sb;
+          if (trade && p == c.p_hi) sm.rem[0] = rb;
+          if (trade && p == c.p_lo) sm.rem[1] = rs;
+          if (carry) {
+            nb = p > c.p_hi ? 0 : (p == c.p_hi ? b - rb : b);
+            ns = p < c.p_lo ? 0 : (p == c.p_lo ? s - rs : s);
+          } else {
+            nb = ns = 0;
+          }
+        }
+        D -= b;
+        Sb += s;
+        if constexpr (FEAT) {
+          if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = ns;
+          if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = nb;
+        }
+        bv[i] = nb;
+        sv[i] = ns;
+      }
+      if (trade || !carry) {
+        st_ticks<LTC>(book + p0, bv);
+        st_ticks<LTC>(book + sb + p0, sv);
+      }
+    }
+  } else {
+    int D = D0, Sb = Sb0;
+    for (int i = 0; i < LT; ++i) {
+      const int p = p0 + i;
+      if (p < L) {
+        const int b = book[p], s = book[sb + p];
+        int nb = b, ns = s;
+        if (trade || !carry) {
+          const int rb = c.vstar - (D - b);
+          const int rs = c.vstar - Sb;
+          if (trade && p == c.p_hi) sm.rem[0] = rb;
+          if (trade && p == c.p_lo) sm.rem[1] = rs;
+          if (carry) {
+            nb = p > c.p_hi ? 0 : (p == c.p_hi ? b - rb : b);
+            ns = p < c.p_lo ? 0 : (p == c.p_lo ? s - rs : s);
+          } else {
+            nb = ns = 0;
+          }
+          book[p] = nb;
+          book[sb + p] = ns;
+        }
+        D -= b;
+        Sb += s;
+        if constexpr (FEAT) {
+          if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = ns;
+          if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = nb;
+        }
+      }
+    }
+  }
+  if constexpr (FEAT) {
+    if (t == 0) {
+#pragma unroll
+      for (int k = 1; k <= 4; ++k) {
+        if (nl + k >= L) sm.feat[k - 1] = 0;
+        if (nl - k < 0) sm.feat[4 + k - 1] = 0;
+      }
+    }
+  }
+  return c;
+}
+
 // Runs steps [s0, s0 + n_steps) of market m.  t: thread index in the group,
 // bar: the group's barrier id, Lcap: the largest L the group's shared memory
 // (sm) was carved for.
@@ -318,6 +546,8 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   }
   const int LT = (L + NT - 1) / NT;
   const int p0 = t * LT;
+  // vector path when every owning thread has exactly LT in-grid ticks
+  const int LTsel = ((LT == 1 || LT == 2 || LT == 4 || LT == 8) && (L % LT == 0)) ? LT : 0;
   const int sb = book_len(Lcap);  // offset of the SELL half of the book
   int32_t* book = sm.book;
 
@@ -428,124 +658,33 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     unsigned long long* kx = sm.kx + 4 * (j & 1);
     gsync<NT>(bar);  // B1: all orders of step s are in the book
 
-    // ---- scans of the book -----------------------------------------------------------
-    int sumB = 0, sumS = 0;
-#pragma unroll 4
-    for (int i = 0; i < LT; ++i) {
-      const int p = p0 + i;
-      if (p < L) {
-        sumB += book[bidx(0, p, sb)];
-        sumS += book[bidx(1, p, sb)];
-      }
+    // ---- clearing and residual book ----------------------------------------------------
+    unsigned long long* kx_next = sm.kx + 4 * ((j + 1) & 1);
+    ClearOut c;
+    switch (LTsel) {
+      case 1: c = clear_step<NT, 1, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 2: c = clear_step<NT, 2, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 4: c = clear_step<NT, 4, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 8: c = clear_step<NT, 8, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      default: c = clear_step<NT, 0, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
     }
-    int sufB = sumB, preS = sumS;  // inclusive warp suffix (BUY) / prefix (SELL) scans
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int vb = __shfl_down_sync(0xffffffffu, sufB, d);
-      const int vs = __shfl_up_sync(0xffffffffu, preS, d);
-      if (lane + d < 32) sufB += vb;
-      if (lane >= d) preS += vs;
-    }
-    if (lane == 0) sm.wD[wid] = sufB;
-    if (lane == 31) sm.wS[wid] = preS;
-    gsync<NT>(bar);  // B2
-    const int offD = (int)__reduce_add_sync(0xffffffffu, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
-    const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
-    const int D0 = offD + sufB;          // D_cum at my first tick
-    const int Sb0 = offS + preS - sumS;  // S_cum just below my first tick
-    {
-      int D = D0, Sb = Sb0;
-      int bestV = -1, lo = 4095, hi = 0;
-      unsigned long long kT = 0ull;
-#pragma unroll 4
-      for (int i = 0; i < LT; ++i) {
-        const int p = p0 + i;
-        if (p < L) {
-          const int b = book[bidx(0, p, sb)];
-          const int S = Sb + book[bidx(1, p, sb)];
-          const int v = min(D, S);
-          if (v > bestV) { bestV = v; lo = p; }
-          if (v >= bestV) hi = p;
-          if (tie1) {
-            const int imb = min(abs(D - S), (1 << 22) - 1);
-            const unsigned long long tk = ((unsigned long long)(uint32_t)v << 34) |
-                                          ((unsigned long long)((1 << 22) - 1 - imb) << 12) | (4095u - p);
-            kT = tk > kT ? tk : kT;
-          }
-          D -= b;
-          Sb = S;
-        }
-      }
-      const int vw = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(bestV, 0));
-      const bool top = bestV == vw;
-      const uint32_t low = __reduce_min_sync(0xffffffffu, top ? (unsigned)lo : 4095u);
-      const uint32_t high = __reduce_max_sync(0xffffffffu, top ? (unsigned)hi : 0u);
-      if (tie1) {
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, kT, d);
-          kT = o > kT ? o : kT;
-        }
-      }
-      if (lane == 0) {
-        atomicMax(kx + 0, ((unsigned long long)(uint32_t)vw << 12) | (4095u - low));
-        atomicMax(kx + 1, ((unsigned long long)(uint32_t)vw << 12) | high);
-        if (tie1) atomicMax(kx + 2, kT);
-      }
-    }
-    gsync<NT>(bar);  // B3
-    const unsigned long long kLo = kx[0], kHi = kx[1];
-    const int vstar = (int)(kLo >> 12);
-    const int p_lo = 4095 - (int)(kLo & 4095u);
-    const int p_hi = (int)(kHi & 4095u);
-    const int pstar = tie1 ? 4095 - (int)(kx[2] & 4095u) : p_lo;
+    const int vstar = c.vstar, p_lo = c.p_lo, p_hi = c.p_hi, pstar = c.pstar;
     const bool trade = vstar > 0;
-    if (t < 4) sm.kx[4 * ((j + 1) & 1) + t] = 0ull;  // reset the other parity for step s+1
-
-    // ---- resting book per tick, marginal remainders -----------------------------------
-    // The owners of the marginal ticks publish R_b = V* - D_cum[p_hi + 1] and
-    // R_s = V* - S_cum[p_lo - 1]; a carried book keeps what did not trade
-    // (Phase 5), a discarded book is emptied.
-    if (trade || !carry) {
-      int D = D0, Sb = Sb0;
-#pragma unroll 4
-      for (int i = 0; i < LT; ++i) {
-        const int p = p0 + i;
-        if (p < L) {
-          const int bi = bidx(0, p, sb), si = bidx(1, p, sb);
-          const int b = book[bi];
-          const int sv = book[si];
-          const int rb = vstar - (D - b);
-          const int rs = vstar - Sb;
-          if (trade && p == p_hi) sm.rem[0] = rb;
-          if (trade && p == p_lo) sm.rem[1] = rs;
-          if (carry) {
-            if (p > p_hi) book[bi] = 0;
-            if (p == p_hi) book[bi] = b - rb;
-            if (p < p_lo) book[si] = 0;
-            if (p == p_lo) book[si] = sv - rs;
-          } else {
-            book[bi] = 0;
-            book[si] = 0;
-          }
-          D -= b;
-          Sb += sv;
-        }
-      }
-    }
-    if constexpr (MLP) publish_depth(sm, book, sb, L, trade ? pstar : last, p0, LT, t);  // own ticks only
 
     // ---- marginal quantities in agent order --------------------------------------------
     uint32_t exB = 0, exS = 0;
     if (trade) {
       uint32_t mB = 0, mS = 0;
+      // an order rests at a marginal tick iff its (side, tick) bits equal that tick's key
+      const uint32_t key_b = (uint32_t)p_hi << W_TICK_SHIFT;
+      const uint32_t key_s = ((uint32_t)p_lo << W_TICK_SHIFT) | W_SIDE;
 #pragma unroll
       for (int k = 0; k < AK; ++k) {
         const uint32_t sl = slot[k];
+        const uint32_t st = sl & (W_SIDE | (W_TICK << W_TICK_SHIFT));
         const uint32_t q = w_qty(sl);
-        const bool marg = q != 0u && fill_dist(sl, p_lo, p_hi) == 0;
-        mB += (marg && !w_sell(sl)) ? q : 0u;
-        mS += (marg && w_sell(sl)) ? q : 0u;
+        mB += st == key_b ? q : 0u;
+        mS += st == key_s ? q : 0u;
       }
       uint32_t iB = mB, iS = mS;
 #pragma unroll
@@ -595,16 +734,20 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       int preB = (int)(exB + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMB[lane] : 0u));
       int preS = (int)(exS + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMS[lane] : 0u));
 #pragma unroll
+      const uint32_t key_b = (uint32_t)p_hi << W_TICK_SHIFT;
+      const uint32_t key_s = ((uint32_t)p_lo << W_TICK_SHIFT) | W_SIDE;
       for (int k = 0; k < AK; ++k) {
         uint32_t sl = slot[k];
         const int q = (int)w_qty(sl);
         const bool sell = w_sell(sl) != 0u;
-        const int d = fill_dist(sl, p_lo, p_hi);
+        const uint32_t st = sl & (W_SIDE | (W_TICK << W_TICK_SHIFT));
+        const int tk = (int)(st >> W_TICK_SHIFT);
+        const bool full = sell ? tk < p_lo : tk > p_hi;  // strictly better than the marginal tick
+        const bool marg = st == (sell ? key_s : key_b);
         const int pre = sell ? preS : preB;
-        const int R = sell ? Rs : Rb;
-        const int fm = min(max(R - pre, 0), q);
-        const int f = q == 0 ? 0 : (d > 0 ? q : (d == 0 ? fm : 0));
-        const int adv = (q != 0 && d == 0) ? q : 0;
+        const int fm = min(max((sell ? Rs : Rb) - pre, 0), q);
+        const int f = full ? q : (marg ? fm : 0);
+        const int adv = marg ? q : 0;
         preS += sell ? adv : 0;
         preB += sell ? 0 : adv;
         if (f) {
