@@ -1,0 +1,56 @@
+"""The multi-GPU launch path on CPU: two gloo ranks shard the global market
+index space with no data-path collective and max-reduce their timings."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    from paper_2606_21784_gb300 import sharding, workloads
+    r, w = sharding.init("gloo")
+    wl = sharding.shard(workloads.workload("plain_mix_8192"), r, w)
+    sharding.barrier()
+    t = sharding.max_over_ranks(1.5 + rank)
+    total = sharding.sum_over_ranks(float(wl["M"]))
+    q.put((rank, wl["market_base"], wl["M"], t, total))
+    sharding.finalize()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_two_gloo_ranks_shard_and_reduce(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    M = out[0][2]
+    bases = [o[1] for o in out]
+    assert bases == [r * M for r in range(world)]          # disjoint global market ranges
+    assert all(o[3] == 1.5 + (world - 1) for o in out)      # time = max over ranks
+    assert all(o[4] == world * M for o in out)              # weak scaling: work grows with ranks
+
+
+def test_single_process_defaults():
+    from paper_2606_21784_gb300 import sharding, workloads
+    r, w, lr = sharding.rank_env()
+    assert (r, w) == (0, 1) or "RANK" in os.environ
+    wl = sharding.shard(workloads.workload("plain_zi_64"), 0, 1)
+    assert wl["market_base"] == 0
+    assert sharding.max_over_ranks(3.0) == 3.0
