@@ -270,6 +270,23 @@ def compare_forms(ks, workloads, stream, plain_rate):
     return out
 
 
+def quick_policy(pairs: int = 2_000_000):
+    """A policy trained by behaviour cloning on `pairs` (state, action) pairs of
+    the rule-based seed-7 run (one epoch); returns (blob, seconds, history)."""
+    import time
+
+    import torch
+
+    from paper_2606_21784_gb300 import bc
+    t0 = time.time()
+    rec, wd = bc.generate(pairs)
+    params, hist, _ = bc.train(rec, wd["A"], epochs=1)
+    blob = bc.export(params)
+    del rec
+    torch.cuda.synchronize()
+    return blob, time.time() - t0, hist
+
+
 def learned_forms(ks, workloads, stream):
     """The learned-agent forms: a policy trained by behaviour cloning on 2M
     (state, action) pairs of the rule-based seed-7 run (a reduced data budget
@@ -282,18 +299,14 @@ def learned_forms(ks, workloads, stream):
     import numpy as np
     import torch
 
-    from paper_2606_21784_gb300 import bc
     out = {}
-    t0 = time.time()
-    rec, wd = bc.generate(2_000_000)
-    params, hist, _ = bc.train(rec, wd["A"], epochs=1)
-    blob = bc.export(params)
-    del rec
-    torch.cuda.synchronize()
-    out["bc"] = {"pairs": 2_000_000, "seconds": time.time() - t0, "val_loss": hist["val_loss"]}
+    blob, secs, hist = quick_policy()
+    out["bc"] = {"pairs": 2_000_000, "seconds": secs, "val_loss": hist["val_loss"]}
     steps = 200
     w = workloads.workload("learned_4096")
     ens = ks.Ensemble(w, mlp_params=blob)
+    from paper_2606_21784_gb300 import autotune
+    autotune.apply(ens, w)
     cap = ens.set_capture(count_policy=True)
     ev = float(w["M"]) * w["A"] * steps
     ens.step(20, stream)
@@ -336,7 +349,9 @@ def run_ours(args):
         w["M"] = args.markets
     w = sharding.shard(w, rank, world)
     S = int(w["S"])
-    ens = ks.Ensemble(w)
+    blob = quick_policy()[0] if int(w["params"].get("mlp_pct", 0)) > 0 else None
+    L_, A_ = workloads.sizes(w)
+    ens = ks.Ensemble(w, L=L_, A=A_, mlp_params=blob)
     if args.launch:
         nt, ak, rc = (int(x) for x in args.launch.split(","))
         ens.set_launch(nt, ak, reg_cap=rc)

@@ -66,8 +66,14 @@ def _pow2(x):
     return 1 << max(0, int(np.ceil(np.log2(max(int(x), 1)))))
 
 
-def plain_candidates(A):
+POLICY_SHAPES = ((128, 16), (256, 8), (256, 16), (512, 8), (512, 16), (1024, 8), (1024, 16))
+
+
+def plain_candidates(A, policy: bool = False):
     out = []
+    if policy:
+        return [dict(threads=nt, agents_per_thread=ak, reg_cap=0) for nt, ak in POLICY_SHAPES
+                if A <= nt * ak <= 4 * max(A, 128)]
     for nt in (128, 256, 512, 1024):
         for ak in (1, 2, 4, 8, 16):
             if nt * ak < A or nt * ak > 4 * max(A, 32):
@@ -77,18 +83,20 @@ def plain_candidates(A):
     return out
 
 
-def tune_plain(w: dict, steps: int = 40, use_cache: bool = True, verbose: bool = False) -> dict:
-    """Best plain-kernel launch for a uniform workload dict; applies nothing."""
+def tune_plain(w: dict, steps: int = 40, use_cache: bool = True, verbose: bool = False, mlp_params=None) -> dict:
+    """Best plain-kernel launch for a uniform workload dict; applies nothing.
+    With mlp_params (policy agents), the policy-capable shapes are timed."""
     M, L, A = int(w["M"]), int(w["L"]), int(w["A"])
-    key = f"plain|{_device_tag()}|L{L}|A{A}|M{M}|carry{w['params']['carry_book']}"
+    policy = mlp_params is not None and int(w["params"].get("mlp_pct", 0)) > 0
+    key = f"plain|{_device_tag()}|L{L}|A{A}|M{M}|carry{w['params']['carry_book']}|policy{int(policy)}"
     if use_cache:
         c = _cache_load().get(key)
         if c:
             return c
-    ens = ks.Ensemble(w)
+    ens = ks.Ensemble(w, mlp_params=mlp_params)
     events = float(M) * A * steps
     best = None
-    for cand in plain_candidates(A):
+    for cand in plain_candidates(A, policy):
         try:
             ens.set_launch(**cand)
         except ks.KsError:
@@ -172,6 +180,6 @@ def apply(ens, w: dict, use_cache: bool = True, verbose: bool = False) -> dict:
         plan = tune_batched(w, ens.L, ens.A, use_cache=use_cache, verbose=verbose)
         ens.set_batch_plan(plan["cta_threads"], plan["buckets"])
         return plan
-    best = tune_plain(w, use_cache=use_cache, verbose=verbose)
+    best = tune_plain(w, use_cache=use_cache, verbose=verbose, mlp_params=getattr(ens, "mlp_params", None))
     ens.set_launch(best["threads"], best["agents_per_thread"], reg_cap=best["reg_cap"])
     return best
