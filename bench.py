@@ -112,6 +112,14 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # nvidia-smi's start-up (NVML init) can stall CUDA calls of this
+        # process for seconds: wait for its first sample so that the stall
+        # falls before the timed region, not inside it
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 20.0:
+            if os.path.getsize(self.path) > 0 or self.proc.poll() is not None:
+                break
+            time.sleep(0.05)
         time.sleep(0.3)
 
     def stop(self):
