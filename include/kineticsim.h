@@ -165,7 +165,8 @@ typedef struct ks_launch {
   int32_t aggregate;          /* 1 = warp-aggregate equal (side,tick) orders with
                                  __match_any_sync before the shared atomic         */
   int32_t reg_cap;            /* register cap class: 0 compiler's choice, 1 about 85,
-                                 2 at most 64 registers per thread (aggregate = 0) */
+                                 2 at most 64 registers per thread (aggregate = 0);
+                                 policy-capable kernels: 0, or 1 = at most 128 */
 } ks_launch;
 
 /*

@@ -66,14 +66,16 @@ def _pow2(x):
     return 1 << max(0, int(np.ceil(np.log2(max(int(x), 1)))))
 
 
-POLICY_SHAPES = ((128, 16), (256, 8), (256, 16), (512, 8), (512, 16), (1024, 8), (1024, 16))
+# compiled policy-capable shapes: (threads, agents per thread, register cap classes)
+POLICY_SHAPES = ((128, 16, (0, 1)), (256, 8, (0, 1)), (256, 16, (0, 1)), (512, 8, (0,)), (512, 16, (0,)),
+                 (1024, 8, (0,)), (1024, 16, (0,)))
 
 
 def plain_candidates(A, policy: bool = False):
     out = []
     if policy:
-        return [dict(threads=nt, agents_per_thread=ak, reg_cap=0) for nt, ak in POLICY_SHAPES
-                if A <= nt * ak <= 4 * max(A, 128)]
+        return [dict(threads=nt, agents_per_thread=ak, reg_cap=rc) for nt, ak, rcs in POLICY_SHAPES
+                for rc in rcs if A <= nt * ak <= 4 * max(A, 128)]
     for nt in (128, 256, 512, 1024):
         for ak in (1, 2, 4, 8, 16):
             if nt * ak < A or nt * ak > 4 * max(A, 32):

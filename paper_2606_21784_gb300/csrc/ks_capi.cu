@@ -44,7 +44,8 @@ const void* batched_mlp_kernel_512();
 const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy, bool mlp) {
   if (mlp) {
     for (int j = 0; j < kPlainMlpCount; ++j)
-      if (kPlainMlp[j].threads == threads && kPlainMlp[j].ak == ak) return &kPlainMlp[j];
+      if (kPlainMlp[j].threads == threads && kPlainMlp[j].ak == ak && kPlainMlp[j].occupancy == occupancy)
+        return &kPlainMlp[j];
     return nullptr;
   }
   const PlainVariant* tabs[4] = {kPlainNT128, kPlainNT256, kPlainNT512, kPlainNT1024};
@@ -276,16 +277,28 @@ static ks_launch default_launch(int Amax, uint32_t M, int num_sms, bool mlp = fa
   ks_launch l;
   memset(&l, 0, sizeof(l));
   if (mlp) {
-    // the smallest compiled policy shape that holds the largest market
+    // the smallest compiled policy shape that holds the largest market;
+    // among equal ones the 128-register cap (two CTAs per SM), then more
+    // threads (measured on 2048-agent markets: 256 x 8 capped 3.4e10
+    // events/s, uncapped 2.3e10, 128 x 16 capped 2.8e10)
     int best = -1;
     for (int j = 0; j < kPlainMlpCount; ++j) {
       const PlainVariant& v = kPlainMlp[j];
       if ((int64_t)v.threads * v.ak < Amax) continue;
-      if (best < 0 || (int64_t)v.threads * v.ak < (int64_t)kPlainMlp[best].threads * kPlainMlp[best].ak) best = j;
+      if (best < 0) {
+        best = j;
+        continue;
+      }
+      const PlainVariant& b = kPlainMlp[best];
+      const int64_t cap = (int64_t)v.threads * v.ak, bcap = (int64_t)b.threads * b.ak;
+      if (cap != bcap ? cap < bcap
+                      : (v.occupancy != b.occupancy ? v.occupancy > b.occupancy : v.threads > b.threads))
+        best = j;
     }
     if (best < 0) best = kPlainMlpCount - 1;
     l.threads = kPlainMlp[best].threads;
     l.agents_per_thread = kPlainMlp[best].ak;
+    l.reg_cap = kPlainMlp[best].occupancy;
     return l;
   }
   const bool few = (int)M < 2 * num_sms;
@@ -304,10 +317,42 @@ static ks_launch default_launch(int Amax, uint32_t M, int num_sms, bool mlp = fa
   return l;
 }
 
+// Resident CTAs per SM of a persistent kernel.  The runtime's occupancy
+// calculator answers one CTA per SM for every kernel that contains tcgen05
+// instructions (CUDA 13.0 on GB300), although the hardware runs several such
+// CTAs on one SM at the same time (measured: up to five 256-thread CTAs,
+// each holding 32 TMEM columns).  For those kernels (tmem_cols > 0) the count
+// is taken here from the same limits -- threads, registers (256-register
+// allocation granules per warp), shared memory with the per-CTA reservation,
+// CTA slots -- and from the 512 TMEM columns of an SM.  An overestimate is
+// harmless: CTAs beyond the resident ones start when others finish.
+static cudaError_t resident_ctas(const void* k, int threads, size_t smem, int tmem_cols, int* occ) {
+  if (tmem_cols <= 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, smem);
+  cudaFuncAttributes a;
+  cudaError_t rc = cudaFuncGetAttributes(&a, k);
+  if (rc != cudaSuccess) return rc;
+  int dev = 0, max_thr = 0, max_regs = 0, max_smem = 0, reserved = 0, max_blocks = 0;
+  if ((rc = cudaGetDevice(&dev)) != cudaSuccess) return rc;
+  cudaDeviceGetAttribute(&max_thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&max_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if ((rc = cudaDeviceGetAttribute(&max_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, dev)) != cudaSuccess) return rc;
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((std::max(a.numRegs, 1) * 32 + 255) / 256) * 256;
+  int n = max_thr / (warps * 32);
+  n = std::min(n, max_regs / (regs_warp * warps));
+  n = std::min(n, (int)((size_t)max_smem / (smem + a.sharedSizeBytes + (size_t)reserved)));
+  n = std::min(n, max_blocks);
+  n = std::min(n, 512 / tmem_cols);
+  *occ = std::max(n, 0);
+  return cudaSuccess;
+}
+
 static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   const PlainVariant* v = find_plain(l->threads, l->agents_per_thread, l->aggregate, l->reg_cap, e->mlp);
   if (!v)
-    return arg_fail(KS_ERR_INVALID_ARG, e->mlp ? "no policy-capable kernel for this (threads, agents_per_thread)"
+    return arg_fail(KS_ERR_INVALID_ARG, e->mlp ? "no policy-capable kernel for this (threads, agents_per_thread, reg_cap)"
                                                : "no kernel for this (threads, agents_per_thread, aggregate, reg_cap)");
   if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
     return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
@@ -317,7 +362,7 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   const void* k = v->kernel;
   KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, l->threads, smem));
+  KS_CUDA(resident_ctas(k, l->threads, smem, e->mlp ? (int)MLP_TMEM_COLS : 0, &occ));
   if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
   // resident CTAs must not ask for more TMEM than an SM has (512 columns)
   if (e->mlp && occ * (int)MLP_TMEM_COLS > 512) return arg_fail(KS_ERR_UNSUPPORTED, "policy launch oversubscribes TMEM");
@@ -462,7 +507,7 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
   }
   KS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem));
+  KS_CUDA(resident_ctas(kern, nt, smem, mlp ? (nt / 128) * (int)MLP_TMEM_COLS : 0, &occ));
   if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "batched plan does not fit on an SM");
   if (mlp && occ * (nt / 128) * (int)MLP_TMEM_COLS > 512)
     return arg_fail(KS_ERR_UNSUPPORTED, "policy batched launch oversubscribes TMEM");

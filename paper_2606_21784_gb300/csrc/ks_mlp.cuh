@@ -272,22 +272,25 @@ __device__ __forceinline__ void mlp_cta_teardown(const MlpCta& c) {
 // inverse-CDF draws of side (w0) and tick offset (w1) from the softmax of
 // their heads, quantity clamp(round(exp(z[36])), 1, qmax).
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ int mlp_sample(const float* z, int n, uint32_t w) {
+template <int N>
+__device__ __forceinline__ int mlp_sample(const float* z, uint32_t w) {
   float mx = z[0];
-  for (int i = 1; i < n; ++i) mx = fmaxf(mx, z[i]);
-  float se = 0.0f;
-  for (int i = 0; i < n; ++i) se += __expf(z[i] - mx);
-  const float u = (float)w * 2.3283064365386963e-10f * se;  // u * sum, compared with the running sum
-  float c = 0.0f;
-  int pick = n - 1;
-  bool found = false;
-  for (int i = 0; i < n; ++i) {
-    c += __expf(z[i] - mx);
-    if (!found && u < c) {
-      pick = i;
-      found = true;
-    }
+#pragma unroll
+  for (int i = 1; i < N; ++i) mx = fmaxf(mx, z[i]);
+  // running sums c_i of exp(z - max); the total is c_{N-1}
+  float c[N];
+  float run = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    run += __expf(z[i] - mx);
+    c[i] = run;
   }
+  const float u = (float)w * 2.3283064365386963e-10f * run;  // u * sum, compared with the running sums
+  // first i with u < c_i (N - 1 if none): c is non-decreasing, so it is the
+  // number of i < N - 1 with c_i <= u
+  int pick = 0;
+#pragma unroll
+  for (int i = 0; i < N - 1; ++i) pick += (c[i] <= u) ? 1 : 0;
   return pick;
 }
 
@@ -361,9 +364,9 @@ __device__ __forceinline__ void mlp_tile_logits(MlpWG& g, const unsigned char* s
 // Order word of a policy decision (qty | side << 8 | tick << 9), or
 // KS_DECISION_PASS.  w: the agent's Philox stream-3 block for the step.
 __device__ __forceinline__ uint32_t mlp_decision(const float* z, uint4 w, int last, int L, int qmax) {
-  const int side = mlp_sample(z, MLP_NSIDE, w.x);
+  const int side = mlp_sample<MLP_NSIDE>(z, w.x);
   if (side == 2) return KS_DECISION_PASS;
-  const int oi = mlp_sample(z + MLP_NSIDE, MLP_NOFF, w.y);
+  const int oi = mlp_sample<MLP_NOFF>(z + MLP_NSIDE, w.y);
   float q = floorf(expf(z[MLP_OUT - 1]) + 0.5f);
   q = (q >= 1.0f) ? q : 1.0f;  // also maps NaN to 1
   q = fminf(q, (float)qmax);

@@ -7,14 +7,16 @@
 namespace ks {
 
 // Register-cap classes of the launch bounds: 0 = compiler's choice, 1 = about
-// 85 registers per thread.
-template <int NT, int OCC>
+// 85 registers per thread (policy kernels: 128, so that two 256-thread CTAs
+// share an SM).
+template <int NT, int OCC, bool MLP = false>
 struct MinBlocks {
-  static constexpr int value = OCC == 0 ? 1 : (65536 / (NT * 85) > 0 ? 65536 / (NT * 85) : 1);
+  static constexpr int cap = MLP ? 128 : 85;
+  static constexpr int value = OCC == 0 ? 1 : (65536 / (NT * cap) > 0 ? 65536 / (NT * cap) : 1);
 };
 
 template <int NT, int AK, bool AGGR, int OCC, bool MLP = false>
-__global__ void __launch_bounds__(NT, MinBlocks<NT, OCC>::value) plain_kernel(DevParams P, uint32_t n_steps) {
+__global__ void __launch_bounds__(NT, (MinBlocks<NT, OCC, MLP>::value)) plain_kernel(DevParams P, uint32_t n_steps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t s0 = (uint32_t)(*P.step);
   if constexpr (MLP) {

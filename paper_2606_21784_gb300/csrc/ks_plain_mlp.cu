@@ -3,10 +3,14 @@
 #include "ks_plain.cuh"
 
 namespace ks {
-#define KS_MLP_VARIANT(NT, AK) \
-  PlainVariant { NT, AK, false, 0, &launch_plain<NT, AK, false, 0, true>, (const void*)&plain_kernel<NT, AK, false, 0, true>, 1 }
-extern const PlainVariant kPlainMlp[] = {KS_MLP_VARIANT(128, 16), KS_MLP_VARIANT(256, 8), KS_MLP_VARIANT(256, 16),
-                                         KS_MLP_VARIANT(512, 8),  KS_MLP_VARIANT(512, 16), KS_MLP_VARIANT(1024, 8),
-                                         KS_MLP_VARIANT(1024, 16)};
+// occupancy 1: 128-register cap (two 256-thread or four 128-thread CTAs per SM by registers)
+#define KS_MLP_VARIANT(NT, AK, OCC)                                                                      \
+  PlainVariant {                                                                                         \
+    NT, AK, false, OCC, &launch_plain<NT, AK, false, OCC, true>, (const void*)&plain_kernel<NT, AK, false, OCC, true>, 1 \
+  }
+extern const PlainVariant kPlainMlp[] = {KS_MLP_VARIANT(128, 16, 0), KS_MLP_VARIANT(128, 16, 1), KS_MLP_VARIANT(256, 8, 0),
+                                         KS_MLP_VARIANT(256, 8, 1),  KS_MLP_VARIANT(256, 16, 0), KS_MLP_VARIANT(256, 16, 1),
+                                         KS_MLP_VARIANT(512, 8, 0),  KS_MLP_VARIANT(512, 16, 0), KS_MLP_VARIANT(1024, 8, 0),
+                                         KS_MLP_VARIANT(1024, 16, 0)};
 extern const int kPlainMlpCount = sizeof(kPlainMlp) / sizeof(kPlainMlp[0]);
 }  // namespace ks

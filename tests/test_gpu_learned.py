@@ -69,8 +69,10 @@ def test_recorded_rule_decisions_match_oracle():
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("mlp_pct,M,L,A", [(100, 6, 512, 2048), (25, 5, 1024, 1500)])
-def test_policy_markets_replay_through_oracle(mlp_pct, M, L, A):
+@pytest.mark.parametrize("mlp_pct,M,L,A,launch", [(100, 6, 512, 2048, None), (25, 5, 1024, 1500, None),
+                                                  (100, 6, 512, 2048, (256, 8, 1)), (25, 5, 1024, 1500, (128, 16, 1))])
+def test_policy_markets_replay_through_oracle(mlp_pct, M, L, A, launch):
+    """launch: (threads, agents per thread, reg_cap); reg_cap 1 is the 128-register policy kernel."""
     import torch
     P = _policy(1)
     blob = ks.pack_mlp_params(*P)
@@ -78,6 +80,8 @@ def test_policy_markets_replay_through_oracle(mlp_pct, M, L, A):
     steps = 40
     ens = ks.Ensemble(w, trace_markets=M, trace_steps=steps, mlp_params=blob)
     ens.set_capture(decisions=True)
+    if launch:
+        ens.set_launch(launch[0], launch[1], reg_cap=launch[2])
     ens.step(steps)
     assert ens.sync(timeout_ms=300_000) == ks.KS_OK
     gs = ens.read_state()
