@@ -66,7 +66,7 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
   X(0, 128, 4) X(1, 128, 8) X(2, 128, 16) X(3, 256, 8) X(4, 256, 16) X(5, 512, 8) X(6, 512, 16) X(7, 512, 32)
 
 template <int NT>
-__device__ void dispatch_item_mlp(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+__device__ __forceinline__ void dispatch_item_mlp(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
                                   unsigned char* raw, const MlpCta& mc);
 
 template <int NT>
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NT, 1) batched_mlp_kernel(DevParams P, uint32_
   X(8, 128, 8) X(9, 256, 8) X(10, 256, 16) X(11, 512, 8) X(12, 512, 16) X(13, 512, 32)
 
 template <int NT>
-__device__ void dispatch_item(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+__device__ __forceinline__ void dispatch_item(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
                               unsigned char* raw);
 
 template <int NT>

@@ -4,7 +4,7 @@
 namespace ks {
 
 template <>
-__device__ void dispatch_item<1024>(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
+__device__ __forceinline__ void dispatch_item<1024>(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
                                    unsigned char* raw) {
   switch (d.z) {
 #define KS_CASE(ID, GT, AK) \

@@ -733,9 +733,9 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       const int Rb = sm.rem[0], Rs = sm.rem[1];
       int preB = (int)(exB + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMB[lane] : 0u));
       int preS = (int)(exS + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMS[lane] : 0u));
-#pragma unroll
       const uint32_t key_b = (uint32_t)p_hi << W_TICK_SHIFT;
       const uint32_t key_s = ((uint32_t)p_lo << W_TICK_SHIFT) | W_SIDE;
+#pragma unroll
       for (int k = 0; k < AK; ++k) {
         uint32_t sl = slot[k];
         const int q = (int)w_qty(sl);
