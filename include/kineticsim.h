@@ -164,9 +164,11 @@ typedef struct ks_launch {
   int32_t ctas_per_sm;        /* 0 = as many as fit                               */
   int32_t aggregate;          /* 1 = warp-aggregate equal (side,tick) orders with
                                  __match_any_sync before the shared atomic         */
-  int32_t reg_cap;            /* register cap class: 0 compiler's choice, 1 about 85,
-                                 2 at most 64 registers per thread (aggregate = 0);
-                                 policy-capable kernels: 0, or 1 = at most 128 */
+  int32_t reg_cap;            /* register cap class: 0 compiler's choice, 1 at most
+                                 128 registers per thread (two 256-thread CTAs per
+                                 SM), 2 at most 85 (three; 128- and 256-thread CTAs
+                                 with 1, 2 or 4 agents per thread, aggregate = 0);
+                                 policy-capable kernels: 0 or 1 */
 } ks_launch;
 
 /*

@@ -27,11 +27,13 @@ __device__ __forceinline__ void run_item(const DevParams& P, const BatchArgs& B,
   constexpr int G = NT / GT;
   const int g = (int)threadIdx.x / GT;
   if (g < G && g < (int)d.y) {
-    size_t o[5];
-    const size_t gsz = plain_smem_layout(GT, AK, (int)d.w, o);
-    const Smem sm = carve<GT, AK>(raw + (size_t)g * gsz, (int)d.w);
+    constexpr int BUDGET = thread_reg_budget(NT, 1);  // the batched kernels' launch bounds
+    constexpr bool REGACC = accounts_in_registers(BUDGET, AK, false);
+    size_t o[8];
+    const size_t gsz = group_smem_layout(BUDGET, GT, AK, (int)d.w, false, o);
+    const Smem sm = carve<GT, AK, false, !REGACC>(raw + (size_t)g * gsz, (int)d.w);
     const int bar = (GT == NT) ? 0 : 1 + g;
-    run_market<GT, AK, false>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w);
+    run_market<GT, AK, false, false, REGACC>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w);
   }
 }
 
@@ -45,10 +47,10 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
   const int g = (int)threadIdx.x / GT;
   if (g < G && g < (int)d.y) {
     size_t o[8];
-    const size_t mbytes = market_smem_layout(GT, AK, (int)d.w, true, o);
+    const size_t mbytes = group_smem_layout(thread_reg_budget(NT, 1), GT, AK, (int)d.w, true, o);
     const size_t gsz = mbytes + MLP_ACT_BYTES;
     unsigned char* graw = raw + (size_t)g * gsz;
-    const Smem sm = carve<GT, AK, true>(graw, (int)d.w);
+    const Smem sm = carve<GT, AK, true, true>(graw, (int)d.w);
     const int bar = (GT == NT) ? 0 : 1 + g;
     MlpWG mw;
     mw.act = graw + mbytes;
@@ -57,7 +59,7 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
     mw.bar_id = (GT == 128) ? bar : 8 + g;
     mw.phase = 0;
     mw.abort = false;
-    run_market<GT, AK, false, true>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w, &mw,
+    run_market<GT, AK, false, true, false>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w, &mw,
                                     mc.sw);
   }
 }

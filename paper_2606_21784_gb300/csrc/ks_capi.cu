@@ -80,11 +80,6 @@ static const int (*batch_table(int nt, int* count, bool mlp = false))[2] {
   return nullptr;
 }
 
-size_t plain_smem_bytes(int threads, int ak, int Lmax) {
-  size_t o[8];
-  return plain_smem_layout(threads, ak, Lmax, o);
-}
-
 // ---------------------------------------------------------------------------
 // Initial state (the paper's Phase 1: empty book, opening price L/2).
 // ---------------------------------------------------------------------------
@@ -271,8 +266,9 @@ static int next_pow2(int x) {
 }
 
 // Default launch shape: with few markets, spread each market over many
-// threads; otherwise 16 agents per thread under the ~85-register cap (the
-// fastest shape measured on GB300 for 4096-agent markets).
+// threads; otherwise 16 agents per thread under the 128-register cap, two
+// 256-thread CTAs per SM (the fastest shape measured on GB300 for
+// 4096-agent markets).
 static ks_launch default_launch(int Amax, uint32_t M, int num_sms, bool mlp = false) {
   ks_launch l;
   memset(&l, 0, sizeof(l));
@@ -357,7 +353,7 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
     return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
   if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
-  const size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, e->Lmax, e->mlp);
+  const size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, e->mlp);
   if (smem > e->max_smem) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more shared memory than a CTA has");
   const void* k = v->kernel;
   KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -389,7 +385,7 @@ static int batch_variant_id(int nt, int gt, int ak, bool mlp) {
 // Groups of one bucket that fit one CTA: thread count, barrier ids, shared memory.
 static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz, bool mlp) {
   size_t o[8];
-  *gsz = market_smem_layout(gt, ak, Lcap, mlp, o) + (mlp ? MLP_ACT_BYTES : 0);
+  *gsz = group_smem_layout(thread_reg_budget(nt, 1), gt, ak, Lcap, mlp, o) + (mlp ? MLP_ACT_BYTES : 0);
   if (mlp) max_smem = max_smem > mlp_cta_bytes() ? max_smem - mlp_cta_bytes() : 0;
   int g = nt / gt;
   if (gt != 32 && gt != nt) g = std::min(g, 15);
@@ -615,6 +611,10 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
   p.A_all = sz.A[0];
   p.key0 = (uint32_t)(cfg->seed & 0xffffffffu);
   p.key1 = (uint32_t)(cfg->seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    p.rk[2 * r] = p.key0 + (uint32_t)r * PH_WA;
+    p.rk[2 * r + 1] = p.key1 + (uint32_t)r * PH_WB;
+  }
   p.carry = cfg->carry_book ? 1 : 0;
   p.cancel_thr = cfg->cancel_thresh_q32;
   p.mix0 = cfg->mix_pct[0];

@@ -23,11 +23,16 @@ __device__ __forceinline__ uint32_t w_qty(uint32_t w) { return w & W_QTY; }
 __device__ __forceinline__ uint32_t w_sell(uint32_t w) { return (w >> 8) & 1u; }
 __device__ __forceinline__ uint32_t w_tick(uint32_t w) { return (w >> W_TICK_SHIFT) & W_TICK; }
 __device__ __forceinline__ uint32_t w_class(uint32_t w) { return (w >> W_CLASS_SHIFT) & 3u; }
+constexpr uint32_t W_ST = W_SIDE | (W_TICK << W_TICK_SHIFT);  // side and tick bits
 
-// Length of one half (BUY or SELL) of a market's book in shared memory:
-// rounded to 16 ticks so that both halves start 64-byte aligned and a thread
-// can load its contiguous ticks with vector accesses (contiguous vector
-// accesses across a warp are free of bank conflicts).
+// The book interleaves the two sides per tick: BUY[p] at word 2p, SELL[p]
+// at 2p + 1.  The index of an order word is then its bits 8-20 as they stand.
+__device__ __forceinline__ int bidx(uint32_t sell, uint32_t tick) { return (int)(2u * tick + sell); }
+__device__ __forceinline__ uint32_t w_bidx(uint32_t w) { return (w >> 8) & 0x1FFFu; }
+
+// Ticks of a market's book in shared memory, rounded to 16 so that a thread
+// can load the (BUY, SELL) pairs of its contiguous ticks with vector accesses
+// (contiguous vector accesses across a warp are free of bank conflicts).
 __host__ __device__ __forceinline__ int book_len(int L) { return (L + 15) & ~15; }
 
 // ---------------------------------------------------------------------------
@@ -74,45 +79,43 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 // market only the agent word varies, so the parts of rounds 1-3 that do not
 // depend on it are computed once (StepKey) and each agent finishes the block
 // with 16 instead of 20 wide multiplies.  The result equals philox() exactly.
+// Round keys come from rk (the kernel parameters: constant-bank operands).
 struct StepKey {
   uint32_t c0;    // round-1 word 0 without the agent term
   uint32_t x3k;   // round-1 word 3 xor round-2 key 1
   uint32_t y1k;   // round-2 word 1 xor round-3 key 0
   uint32_t hAk;   // round-3 hi(A) xor round-3 key 1
   uint32_t z3;    // round-3 word 3
-  uint32_t k0, k1;
 };
 
-__device__ __forceinline__ StepKey step_key(uint32_t step, uint32_t market, uint32_t stream, uint32_t k0,
-                                            uint32_t k1) {
+__device__ __forceinline__ StepKey step_key(uint32_t step, uint32_t market, uint32_t stream, const uint32_t* rk) {
   StepKey s;
   // round 1 (key k): A = MA*step, B = MB*market
   uint32_t hA, lA, hB, lB;
   mulhilo(PH_MA, step, hA, lA);
   mulhilo(PH_MB, market, hB, lB);
   uint32_t x1 = lB;
-  uint32_t x2 = hA ^ stream ^ k1;
+  uint32_t x2 = hA ^ stream ^ rk[1];
   uint32_t x3 = lA;
-  s.c0 = hB ^ k0;  // x0 = c0 ^ agent
+  s.c0 = hB ^ rk[0];  // x0 = c0 ^ agent
   // round 2 (key k + W): B = MB*x2 is agent independent
   uint32_t hB2, lB2;
   mulhilo(PH_MB, x2, hB2, lB2);
-  uint32_t y0 = hB2 ^ x1 ^ (k0 + PH_WA);
+  uint32_t y0 = hB2 ^ x1 ^ rk[2];
   uint32_t y1 = lB2;
-  s.x3k = x3 ^ (k1 + PH_WB);
+  s.x3k = x3 ^ rk[3];
   // round 3 (key k + 2W): A = MA*y0 is agent independent
   uint32_t hA3, lA3;
   mulhilo(PH_MA, y0, hA3, lA3);
-  s.y1k = y1 ^ (k0 + 2u * PH_WA);
-  s.hAk = hA3 ^ (k1 + 2u * PH_WB);
+  s.y1k = y1 ^ rk[4];
+  s.hAk = hA3 ^ rk[5];
   s.z3 = lA3;
-  s.k0 = k0;
-  s.k1 = k1;
   return s;
 }
 
-__device__ __forceinline__ uint4 step_draw(const StepKey& s, uint32_t agent) {
-  uint32_t x0 = s.c0 ^ agent;
+// x0 = s.c0 ^ agent (an agent index a0 + k with a0 a multiple of a power of
+// two above k is s.c0 ^ a0 ^ k: one xor per agent).
+__device__ __forceinline__ uint4 step_draw_x0(const StepKey& s, uint32_t x0, const uint32_t* rk) {
   // round 2, agent-dependent half: A = MA*x0
   uint32_t hA2, lA2;
   mulhilo(PH_MA, x0, hA2, lA2);
@@ -126,20 +129,14 @@ __device__ __forceinline__ uint4 step_draw(const StepKey& s, uint32_t agent) {
   uint32_t z2 = s.hAk ^ y3;
   uint32_t z3 = s.z3;
 #pragma unroll
-  for (int r = 3; r < 10; ++r) {
-    philox_round(z0, z1, z2, z3, s.k0 + (uint32_t)r * PH_WA, s.k1 + (uint32_t)r * PH_WB);
-  }
+  for (int r = 3; r < 10; ++r) philox_round(z0, z1, z2, z3, rk[2 * r], rk[2 * r + 1]);
   return make_uint4(z0, z1, z2, z3);
 }
 
 // floor(w * n / 2^32)
 __device__ __forceinline__ uint32_t range_u32(uint32_t w, uint32_t n) { return __umulhi(w, n); }
 
-// ---------------------------------------------------------------------------
-// Rule-based decision of an agent without a working order.
-// side_mom / side_mr: 0 buy, 1 sell, -1 undecided (use the draw's side bit).
-// Returns the new order word (static bits of `slot` kept).
-// ---------------------------------------------------------------------------
+// Rule parameters of the ensemble (derived from ks_config once per market).
 struct RuleConsts {
   int32_t zi_off;
   uint32_t zi_n;     // 2*zi_off + 1
@@ -149,20 +146,81 @@ struct RuleConsts {
   uint32_t rb_qmax;
 };
 
-__device__ __forceinline__ uint32_t decide_rule(uint32_t slot, uint4 w, int last, int side_mom, int side_mr,
-                                                int L, const RuleConsts& rc) {
-  uint32_t cls = w_class(slot);
-  uint32_t coin = w.y >> 31;  // 0 buy (w1 < 2^31), 1 sell
-  bool zi = cls == KS_CLASS_ZI;
-  int sd_rule = cls == KS_CLASS_MOM ? side_mom : side_mr;
-  uint32_t sell = zi ? coin : (sd_rule < 0 ? coin : (uint32_t)sd_rule);
-  uint32_t n = zi ? rc.zi_n : (cls == KS_CLASS_MOM ? rc.mom_n : rc.mr_n);
-  int o = (int)range_u32(w.z, n);
-  int off = zi ? o - rc.zi_off : (sell ? -o : o);
-  int tick = min(max(last + off, 0), L - 1);
-  uint32_t qmax = zi ? rc.zi_qmax : rc.rb_qmax;
-  uint32_t qty = 1u + range_u32(w.w, qmax);
-  return (slot & W_STATIC) | qty | (sell << 8) | ((uint32_t)tick << W_TICK_SHIFT);
+// book[i] += v where pred holds, as one predicated shared-memory reduction
+// (no branch around it).
+__device__ __forceinline__ void red_add_if(uint32_t saddr, int v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(saddr),
+      "r"(v), "r"((int)pred));
+}
+
+// ---------------------------------------------------------------------------
+// Rule-based decision of an agent without a working order, from the draw
+// words w = (w0 cancel, w1 side, w2 offset, w3 quantity) of its Philox block:
+//   zero intelligence: sell iff w1 >= 2^31; tick = last - zi_off +
+//     floor(w2 (2 zi_off + 1) / 2^32); qty = 1 + floor(w3 zi_qmax / 2^32);
+//   momentum: side = sign of the lookback return of the last clearing tick
+//     (buy if up, sell if down, the w1 coin if flat); mean reversion: side
+//     toward the market's fundamental tick (the coin at the fundamental);
+//     both order o = floor(w2 (omax + 1) / 2^32) ticks through the last tick
+//     (a buy at last + o, a sell at last - o), qty 1 + floor(w3 rb_qmax / 2^32);
+// ticks clamped to [0, L).  Within a step everything but the draw words is
+// the same for all agents of a class, so the step's constants sit in a
+// 4-row table in shared memory indexed by the class bits of the order word
+// (class 3, never assigned, behaves as mean reversion).  Row fields: sell
+// iff bit 31 of (w1 & coin_mask) | forced_sell; o = floor(w2 n / 2^32);
+// tick = clamp(base + sgn o) with sgn = -1 if w1 & sgn_mask, else sgn_fix;
+// qty = 1 + floor(w3 qmax / 2^32).
+// ---------------------------------------------------------------------------
+struct ClassRule {
+  uint32_t n, qmax, coin_mask, forced_sell;
+  uint32_t sgn_mask;
+  int32_t sgn_fix, base, pad;
+};
+
+// Row c of the table for a step whose last clearing tick is `last`;
+// side_mom / side_mr: 0 buy, 1 sell, -1 undecided.
+__device__ __forceinline__ ClassRule class_rule(int c, int last, int side_mom, int side_mr, const RuleConsts& rc) {
+  ClassRule r;
+  r.pad = 0;
+  if (c == KS_CLASS_ZI) {
+    r.n = rc.zi_n;
+    r.qmax = rc.zi_qmax;
+    r.coin_mask = 0x80000000u;
+    r.forced_sell = 0u;
+    r.sgn_mask = 0u;
+    r.sgn_fix = 1;
+    r.base = last - rc.zi_off;
+  } else {
+    const int side = c == KS_CLASS_MOM ? side_mom : side_mr;
+    r.n = c == KS_CLASS_MOM ? rc.mom_n : rc.mr_n;
+    r.qmax = rc.rb_qmax;
+    r.base = last;
+    if (side < 0) {
+      r.coin_mask = 0x80000000u;
+      r.forced_sell = 0u;
+      r.sgn_mask = 0x80000000u;
+      r.sgn_fix = 1;
+    } else {
+      r.coin_mask = 0u;
+      r.forced_sell = (uint32_t)side << 31;
+      r.sgn_mask = 0u;
+      r.sgn_fix = side ? -1 : 1;
+    }
+  }
+  return r;
+}
+
+// New order word of an agent (static bits of `slot` kept) from its table row.
+__device__ __forceinline__ uint32_t decide_tab(uint32_t slot, uint4 w, const ClassRule* tab, int L) {
+  const uint4 a = *reinterpret_cast<const uint4*>(tab + w_class(slot));
+  const uint4 b = *(reinterpret_cast<const uint4*>(tab + w_class(slot)) + 1);
+  const uint32_t sell31 = (w.y & a.z) | a.w;
+  const int o = (int)__umulhi(w.z, a.x);
+  const int sgn = (w.y & b.x) ? -1 : (int)b.y;
+  const int tick = min(max((int)b.z + sgn * o, 0), L - 1);
+  const uint32_t qty = 1u + __umulhi(w.w, a.y);
+  return (slot & W_STATIC) | qty | (sell31 >> 23) | ((uint32_t)tick << W_TICK_SHIFT);
 }
 
 // SplitMix64 finaliser (Sec. III-F) folding the per-step clearing trace.

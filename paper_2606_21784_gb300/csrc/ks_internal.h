@@ -32,6 +32,7 @@ struct DevParams {
   uint32_t market_base;  // global index of market 0 (Philox counter word)
   int32_t L_all, A_all;
   uint32_t key0, key1;
+  uint32_t rk[20];       // Philox round keys: rk[2r] = key0 + r * 0x9E3779B9, rk[2r+1] = key1 + r * 0xBB67AE85
   int32_t carry;
   uint32_t cancel_thr;
   uint32_t mix0, mix01;  // class percentile thresholds: ZI < mix0 <= MOM < mix01 <= MR
@@ -70,16 +71,14 @@ struct PlainVariant {
   int threads;
   int ak;
   int aggregate;  // warp-aggregated book atomics
-  int occupancy;  // register-cap class (0 none, 1 ~85, 2 64 registers)
+  int occupancy;  // register-cap class (0 none, 1 128, 2 85 registers per thread)
   PlainLaunchFn launch;
   const void* kernel;  // for attribute and occupancy queries
   int mlp = 0;         // policy path compiled in
 };
 
 // Registry filled by the instantiation translation units.
-const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy);
-
-// Shared memory bytes of the plain kernel for a launch shape and max L.
-size_t plain_smem_bytes(int threads, int ak, int Lmax);
+const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy, bool mlp);
 
 }  // namespace ks
+

@@ -1,11 +1,15 @@
 // ks_market.cuh -- one market's persistent call-auction loop (sm_103a).
 //
 // A group of GT threads (a whole CTA, or a slice of one when several small
-// markets share a CTA) owns one market at a time and keeps it on chip for all n steps of a
-// call (the paper's Algorithm 1 and Sec. III-B residency, re-shaped for
-// GB300): thread t owns agents [t*AK, t*AK+AK) -- order words in registers,
-// inventory and cash in thread-private shared-memory columns -- and ticks
-// [t*LT, t*LT+LT) of the aggregated book in shared memory.
+// markets share a CTA) owns one market at a time and keeps it on chip for all
+// n steps of a call (the paper's Algorithm 1 and Sec. III-B residency,
+// re-shaped for GB300): thread t owns agents [t*AK, t*AK+AK) and ticks
+// [t*LT, t*LT+LT) of the aggregated book in shared memory.  An agent's order
+// word lives in a register of its thread; its inventory and cash either in
+// registers too (inventory, and the cash of the current 1024-step window
+// over a 64-bit total in a thread-private shared-memory column) or, where
+// the CTA's register budget is smaller, in thread-private shared-memory
+// columns (accounts_in_registers).
 //
 // Step s, between four group barriers:
 //   B1  all orders of step s are in the book (shared atomics)      (Alg. 1, Phase 3)
@@ -32,11 +36,30 @@
 
 namespace ks {
 
+// Cash moves into 32-bit per-agent registers between flushes into the 64-bit
+// total: one step changes an agent's cash by at most 4095 * 255 < 2^20 tick
+// units, so 1024 steps stay below 2^31.
+constexpr uint32_t CASH_FLUSH_STEPS = 1024;
+
+// Registers a thread may use when min_ctas CTAs of cta_threads threads share
+// an SM's 65536 (the launch bounds), at most 255.
+__host__ __device__ constexpr int thread_reg_budget(int cta_threads, int min_ctas) {
+  return 65536 / (cta_threads * min_ctas) < 255 ? 65536 / (cta_threads * min_ctas) : 255;
+}
+
+// Where the agents' inventory and cash live: registers when order word,
+// inventory and pending cash (3 per agent) and about 56 more fit the budget,
+// shared memory otherwise.  Policy kernels keep them in shared memory, where
+// the policy rows read the inventory.
+__host__ __device__ constexpr bool accounts_in_registers(int reg_budget, int ak, bool mlp) {
+  return !mlp && 3 * ak + 56 <= reg_budget;
+}
+
 struct Smem {
-  int64_t* cash;          // [AK][NT] thread-private columns
+  int64_t* cash;          // [AK][NT] thread-private columns: cash (registers accounts: up to the last flush)
   unsigned long long* kx; // [2 parities][4]: lowest / highest maximiser keys, tie key
-  int32_t* inv;           // [AK][NT]
-  int32_t* book;          // buy at [0, BL), sell at [BL, 2 BL), BL = book_len(Lmax)
+  int32_t* inv;           // [AK][NT] thread-private columns of inventory (shared-memory accounts)
+  int32_t* book;          // BUY[p] at 2p, SELL[p] at 2p + 1, p < book_len(Lmax)
   int32_t* wD;            // [32] warp totals of BUY
   int32_t* wS;            // [32] warp totals of SELL
   uint32_t* wMB;          // [32] warp totals of marginal buy quantity
@@ -44,32 +67,35 @@ struct Smem {
   int32_t* rem;           // [2]: R_b, R_s (units filled at the marginal buy / sell tick)
   int32_t* feat;          // [8]: resting sell qty at last+1..+4, buy qty at last-1..-4 (policy inputs)
   int32_t* wR;            // [32] warp totals of policy rows
+  ClassRule* ctab;        // [4] rule constants per agent class for the next orders
   float* cvec;            // [64] layer-1 pre-activation shared by the market's agents (policy kernels)
   uint32_t* rowbuf;       // [NT * AK] policy rows: agent index, then the decision (policy kernels)
 };
 
-// Shared memory of one market group; `mlp` adds the policy rows.
-__host__ __device__ inline size_t market_smem_layout(int nt, int ak, int Lmax, bool mlp, size_t* o) {
+// Shared memory of one market group; `mlp` adds the policy buffers,
+// `inv_col` the inventory columns (shared-memory accounts).
+__host__ __device__ inline size_t market_smem_layout(int nt, int ak, int Lmax, bool mlp, bool inv_col, size_t* o) {
   size_t off = 0;
   o[0] = off; off += (size_t)8 * ak * nt;                // cash
   o[1] = off; off += (size_t)8 * 8;                      // kx
-  o[2] = off; off += (size_t)4 * ak * nt;                // inv
+  o[2] = off; off += inv_col ? (size_t)4 * ak * nt : 0;  // inv
   o[3] = off; off += (size_t)4 * 2 * book_len(Lmax);     // book
   o[4] = off; off += (size_t)4 * 32 * 4 + 4 * 4;         // wD, wS, wMB, wMS, rem
-  o[5] = off; off += (size_t)4 * 8 + 4 * 32;             // feat, wR
+  o[5] = off; off += (size_t)4 * 8 + 4 * 32 + 4 * sizeof(ClassRule);  // feat, wR, ctab
   o[6] = off; off += mlp ? (size_t)4 * 64 : 0;           // cvec
   o[7] = off; off += mlp ? (size_t)4 * ak * nt : 0;      // rowbuf
   return (off + 15) & ~(size_t)15;
 }
 
-__host__ __device__ inline size_t plain_smem_layout(int nt, int ak, int Lmax, size_t* o) {
-  return market_smem_layout(nt, ak, Lmax, false, o);
+// Shared memory of one market group of gt threads under a register budget.
+__host__ __device__ inline size_t group_smem_layout(int reg_budget, int gt, int ak, int Lmax, bool mlp, size_t* o) {
+  return market_smem_layout(gt, ak, Lmax, mlp, !accounts_in_registers(reg_budget, ak, mlp), o);
 }
 
-template <int NT, int AK, bool MLP = false>
+template <int NT, int AK, bool MLP, bool INV_COL>
 __device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
   size_t o[8];
-  market_smem_layout(NT, AK, Lmax, MLP, o);
+  market_smem_layout(NT, AK, Lmax, MLP, INV_COL, o);
   Smem s;
   s.cash = reinterpret_cast<int64_t*>(raw + o[0]);
   s.kx = reinterpret_cast<unsigned long long*>(raw + o[1]);
@@ -82,6 +108,7 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
   s.rem = s.wD + 128;
   s.feat = reinterpret_cast<int32_t*>(raw + o[5]);
   s.wR = s.feat + 8;
+  s.ctab = reinterpret_cast<ClassRule*>(s.wR + 32);
   s.cvec = reinterpret_cast<float*>(raw + o[6]);
   s.rowbuf = reinterpret_cast<uint32_t*>(raw + o[7]);
   return s;
@@ -99,23 +126,21 @@ __device__ __forceinline__ void gsync(int bar) {
   }
 }
 
-__device__ __forceinline__ int bidx(uint32_t sell, uint32_t tick, int sb) { return (int)tick + (sell ? sb : 0); }
-
 // Add the order word's quantity at its (side, tick).  With AGGR, lanes of the
 // warp holding the same (side, tick) first combine their quantities
 // (__match_any_sync + __reduce_add_sync) and one lane issues the atomic.
 template <bool AGGR>
-__device__ __forceinline__ void book_add(int32_t* book, int sb, bool valid, uint32_t w) {
-  const uint32_t sell = w_sell(w), tick = w_tick(w);
+__device__ __forceinline__ void book_add(uint32_t book_s, bool valid, uint32_t w) {
+  const uint32_t i = w_bidx(w);
   const int q = (int)w_qty(w);
   if constexpr (AGGR) {
-    const uint32_t key = valid ? ((sell << 12) | tick) : 0xFFFFFFFFu;
+    const uint32_t key = valid ? i : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int tot = (int)__reduce_add_sync(peers, (unsigned)q);
     const int leader = __ffs(peers) - 1;
-    if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(book + bidx(sell, tick, sb), tot);
+    red_add_if(book_s + 4u * i, tot, valid && (int)(threadIdx.x & 31) == leader);
   } else {
-    if (valid) atomicAdd(book + bidx(sell, tick, sb), q);
+    red_add_if(book_s + 4u * i, q, valid);
   }
 }
 
@@ -154,22 +179,24 @@ __device__ __forceinline__ void record_decision(const DevParams& P, const StepFe
 }
 
 // Step-s order of one agent: cancellation of its working order (carried
-// books), then a new order if it has none.  Returns the new order word.
-// With MLP, a policy-driven agent without an order sets `policy` instead of
-// deciding, and rule decisions of recorded agents are appended.
+// books; cthr = 0 never cancels), then a new order if it has none.  x0 is the
+// agent's first Philox word (StepKey::c0 ^ agent).  Returns the new order
+// word.  With MLP, a policy-driven agent without an order sets `policy`
+// instead of deciding, and rule decisions of recorded agents are appended.
 template <bool AGGR, bool MLP = false>
-__device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, bool valid, const StepRules& sr, bool carry,
-                                                uint32_t cthr, int L, const RuleConsts& rc, int32_t* book, int sb,
-                                                bool* policy = nullptr, const DevParams* P = nullptr,
-                                                const StepFeat* f = nullptr, int inv = 0) {
-  const uint4 w = step_draw(sr.sk, (uint32_t)a);
+__device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, uint32_t x0, bool valid, const StepRules& sr,
+                                                uint32_t cthr, int L, const ClassRule* tab, uint32_t book_s,
+                                                const uint32_t* rk, bool* policy = nullptr,
+                                                const DevParams* P = nullptr, const StepFeat* f = nullptr,
+                                                int inv = 0) {
+  const uint4 w = step_draw_x0(sr.sk, x0, rk);
   const uint32_t q = w_qty(sl);
-  const bool cancel = valid && carry && q != 0u && w.x < cthr;
-  if (cancel) atomicSub(book + bidx(w_sell(sl), w_tick(sl), sb), (int)q);
+  const bool cancel = q != 0u && w.x < cthr;
+  red_add_if(book_s + 4u * w_bidx(sl), -(int)q, cancel);
   const bool empty = valid && (q == 0u || cancel);
   const bool dec = empty && !(sl & W_MLP);
-  const uint32_t ns = decide_rule(sl, w, sr.last, sr.side_mom, sr.side_mr, L, rc);
-  book_add<AGGR>(book, sb, dec, ns);
+  const uint32_t ns = decide_tab(sl, w, tab, L);
+  book_add<AGGR>(book_s, dec, ns);
   if constexpr (MLP) {
     *policy = empty && (sl & W_MLP);
     if (dec && (uint32_t)a < P->rec_agents) record_decision(*P, *f, inv, ns, sr.last);
@@ -180,7 +207,7 @@ __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, bool valid, 
 __device__ __forceinline__ StepRules step_rules(const DevParams& P, uint32_t s, uint32_t gm, int h0, int hlb, int last,
                                                 int fund) {
   StepRules r;
-  r.sk = step_key(s, gm, 0u, P.key0, P.key1);
+  r.sk = step_key(s, gm, 0u, P.rk);
   const int ret = h0 - hlb;
   r.side_mom = ret > 0 ? 0 : (ret < 0 ? 1 : -1);
   r.side_mr = last < fund ? 0 : (last > fund ? 1 : -1);
@@ -202,11 +229,12 @@ __device__ __forceinline__ int hist_at(const int (&hist)[KS_HISTORY], int lb) {
 // agent a0 + k): rows are compacted in agent order, the group's first
 // warpgroup evaluates them 128 at a time on the tensor cores and samples the
 // actions (Philox stream 3 of step sdec), then the owners place the orders.
+// The inventories of the flagged agents are in sm.inv.
 template <int NT, int AK>
 __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm, MlpWG& mw, const unsigned char* sw,
                                              uint32_t (&slot)[AK], uint32_t pflags, int t, int bar, int a0, int A,
                                              int L, uint32_t sdec, uint32_t gm, const StepFeat& f, int last,
-                                             int64_t aoff, bool traced, int32_t* book, int sb) {
+                                             int64_t aoff, bool traced, int32_t* book) {
   constexpr int NW = NT / 32;
   const int lane = t & 31;
   const int wid = t >> 5;
@@ -263,7 +291,7 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
       const uint32_t d = sm.rowbuf[r++];
       if (!(d & KS_DECISION_PASS)) {
         slot[k] = (slot[k] & W_STATIC) | d;
-        atomicAdd(book + bidx(w_sell(d), w_tick(d), sb), (int)w_qty(d));
+        atomicAdd(book + w_bidx(d), (int)w_qty(d));
       }
       if (traced && P.dec_trace && sdec < P.trace_steps)
         P.dec_trace[(size_t)sdec * P.dec_trace_agents + (size_t)(aoff + a0 + k)] = d;
@@ -273,13 +301,13 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
 
 // Resting depth around tick nl from the book (the policy inputs): each entry
 // has exactly one writer, the owner of its tick or thread 0 off the grid.
-__device__ __forceinline__ void publish_depth(const Smem& sm, const int32_t* book, int sb, int L, int nl, int p0,
-                                              int LT, int t) {
+__device__ __forceinline__ void publish_depth(const Smem& sm, const int32_t* book, int L, int nl, int p0, int LT,
+                                              int t) {
   for (int i = 0; i < LT; ++i) {
     const int p = p0 + i;
     if (p < L) {
-      if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = book[bidx(1, p, sb)];
-      if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = book[bidx(0, p, sb)];
+      if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = book[bidx(1, p)];
+      if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = book[bidx(0, p)];
     }
   }
   if (t == 0) {
@@ -294,45 +322,42 @@ __device__ __forceinline__ void publish_depth(const Smem& sm, const int32_t* boo
 // ---------------------------------------------------------------------------
 // One clearing of the book (Eq. 1-2, Phase 4) and the residual update
 // (Phase 5).  The thread owns ticks [p0, p0 + LT).  LTC > 0: LT == LTC and
-// the ticks are loaded once with vector accesses and kept in registers;
-// LTC == 0: any LT, scalar accesses.
+// the (BUY, SELL) pairs are loaded once with vector accesses and kept in
+// registers; LTC == 0: any LT, scalar accesses.
 // ---------------------------------------------------------------------------
 struct ClearOut {
   int vstar, p_lo, p_hi, pstar;
 };
 
+// (BUY, SELL) pairs of N consecutive ticks starting at word src (8N bytes, aligned to min(16, 8N)).
 template <int N>
-__device__ __forceinline__ void ld_ticks(const int32_t* src, int* v) {
+__device__ __forceinline__ void ld_pairs(const int32_t* src, int* b, int* s) {
   if constexpr (N == 1) {
-    v[0] = src[0];
-  } else if constexpr (N == 2) {
     const int2 a = *reinterpret_cast<const int2*>(src);
-    v[0] = a.x; v[1] = a.y;
+    b[0] = a.x; s[0] = a.y;
   } else {
 #pragma unroll
-    for (int i = 0; i < N; i += 4) {
-      const int4 a = *reinterpret_cast<const int4*>(src + i);
-      v[i] = a.x; v[i + 1] = a.y; v[i + 2] = a.z; v[i + 3] = a.w;
+    for (int i = 0; i < N; i += 2) {
+      const int4 a = *reinterpret_cast<const int4*>(src + 2 * i);
+      b[i] = a.x; s[i] = a.y; b[i + 1] = a.z; s[i + 1] = a.w;
     }
   }
 }
 
 template <int N>
-__device__ __forceinline__ void st_ticks(int32_t* dst, const int* v) {
+__device__ __forceinline__ void st_pairs(int32_t* dst, const int* b, const int* s) {
   if constexpr (N == 1) {
-    dst[0] = v[0];
-  } else if constexpr (N == 2) {
-    *reinterpret_cast<int2*>(dst) = make_int2(v[0], v[1]);
+    *reinterpret_cast<int2*>(dst) = make_int2(b[0], s[0]);
   } else {
 #pragma unroll
-    for (int i = 0; i < N; i += 4) *reinterpret_cast<int4*>(dst + i) = make_int4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    for (int i = 0; i < N; i += 2) *reinterpret_cast<int4*>(dst + 2 * i) = make_int4(b[i], s[i], b[i + 1], s[i + 1]);
   }
 }
 
 template <int NT, int LTC, bool FEAT>
-__device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, int sb, int L, int LT, int p0, int t,
-                                               int bar, unsigned long long* kx, unsigned long long* kx_next,
-                                               bool tie1, bool carry, int last) {
+__device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, int L, int LT, int p0, int t, int bar,
+                                               unsigned long long* kx, unsigned long long* kx_next, bool tie1,
+                                               bool carry, int last) {
   const int lane = t & 31;
   const int wid = t >> 5;
   constexpr int R = LTC > 0 ? LTC : 1;
@@ -341,8 +366,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   int sumB = 0, sumS = 0;
   if constexpr (LTC > 0) {
     if (mine) {
-      ld_ticks<LTC>(book + p0, bv);
-      ld_ticks<LTC>(book + sb + p0, sv);
+      ld_pairs<LTC>(book + 2 * p0, bv, sv);
     } else {
 #pragma unroll
       for (int i = 0; i < LTC; ++i) bv[i] = sv[i] = 0;
@@ -356,8 +380,8 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
     for (int i = 0; i < LT; ++i) {
       const int p = p0 + i;
       if (p < L) {
-        sumB += book[p];
-        sumS += book[sb + p];
+        sumB += book[2 * p];
+        sumS += book[2 * p + 1];
       }
     }
   }
@@ -404,8 +428,8 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
       for (int i = 0; i < LT; ++i) {
         const int p = p0 + i;
         if (p < L) {
-          const int b = book[p];
-          const int S = Sb + book[sb + p];
+          const int b = book[2 * p];
+          const int S = Sb + book[2 * p + 1];
           const int v = min(D, S);
           if (v > bestV) { bestV = v; lo = p; }
           if (v >= bestV) hi = p;
@@ -480,17 +504,14 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
         bv[i] = nb;
         sv[i] = ns;
       }
-      if (trade || !carry) {
-        st_ticks<LTC>(book + p0, bv);
-        st_ticks<LTC>(book + sb + p0, sv);
-      }
+      if (trade || !carry) st_pairs<LTC>(book + 2 * p0, bv, sv);
     }
   } else {
     int D = D0, Sb = Sb0;
     for (int i = 0; i < LT; ++i) {
       const int p = p0 + i;
       if (p < L) {
-        const int b = book[p], s = book[sb + p];
+        const int b = book[2 * p], s = book[2 * p + 1];
         int nb = b, ns = s;
         if (trade || !carry) {
           const int rb = c.vstar - (D - b);
@@ -503,8 +524,8 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
           } else {
             nb = ns = 0;
           }
-          book[p] = nb;
-          book[sb + p] = ns;
+          book[2 * p] = nb;
+          book[2 * p + 1] = ns;
         }
         D -= b;
         Sb += s;
@@ -529,12 +550,15 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
 
 // Runs steps [s0, s0 + n_steps) of market m.  t: thread index in the group,
 // bar: the group's barrier id, Lcap: the largest L the group's shared memory
-// (sm) was carved for.
-template <int NT, int AK, bool AGGR, bool MLP = false>
+// (sm) was carved for, REGACC: inventory and cash in registers (else in the
+// shared-memory columns sm.inv / sm.cash).
+template <int NT, int AK, bool AGGR, bool MLP, bool REGACC>
 __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t n_steps, const Smem& sm, int t,
                            int bar, int Lcap, MlpWG* mw = nullptr, const unsigned char* sw = nullptr) {
   static_assert(!(MLP && AGGR), "policy kernels use plain shared atomics");
+  static_assert(!(MLP && REGACC), "policy rows read the inventory from shared memory");
   static_assert(!MLP || (NT >= 128 && NT % 128 == 0), "policy groups are whole warpgroups");
+  static_assert((AK & (AK - 1)) == 0 && AK <= 32, "agents per thread: a power of two (agent = a0 ^ k)");
   const int lane = t & 31;
   const int wid = t >> 5;
   const int L = P.Ls ? P.Ls[m] : P.L_all;
@@ -548,11 +572,13 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   const int p0 = t * LT;
   // vector path when every owning thread has exactly LT in-grid ticks
   const int LTsel = ((LT == 1 || LT == 2 || LT == 4 || LT == 8) && (L % LT == 0)) ? LT : 0;
-  const int sb = book_len(Lcap);  // offset of the SELL half of the book
   int32_t* book = sm.book;
+  const uint32_t book_s = (uint32_t)__cvta_generic_to_shared(book);
 
   // ---- load the market's state (128-bit accesses where aligned) -----------------
   uint32_t slot[AK];
+  int inv[REGACC ? AK : 1];
+  int cpend[REGACC ? AK : 1];  // cash since the last flush into sm.cash
   const int a0 = t * AK;
   const bool vec = (AK % 4 == 0) && ((aoff + a0) % 4 == 0) && (a0 + AK <= A);
   if (vec) {
@@ -563,8 +589,12 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       const longlong2 c0 = *reinterpret_cast<const longlong2*>(P.cash + aoff + a0 + k);
       const longlong2 c1 = *reinterpret_cast<const longlong2*>(P.cash + aoff + a0 + k + 2);
       slot[k] = sv.x; slot[k + 1] = sv.y; slot[k + 2] = sv.z; slot[k + 3] = sv.w;
-      sm.inv[(k + 0) * NT + t] = iv.x; sm.inv[(k + 1) * NT + t] = iv.y;
-      sm.inv[(k + 2) * NT + t] = iv.z; sm.inv[(k + 3) * NT + t] = iv.w;
+      if constexpr (REGACC) {
+        inv[k] = iv.x; inv[k + 1] = iv.y; inv[k + 2] = iv.z; inv[k + 3] = iv.w;
+      } else {
+        sm.inv[(k + 0) * NT + t] = iv.x; sm.inv[(k + 1) * NT + t] = iv.y;
+        sm.inv[(k + 2) * NT + t] = iv.z; sm.inv[(k + 3) * NT + t] = iv.w;
+      }
       sm.cash[(k + 0) * NT + t] = c0.x; sm.cash[(k + 1) * NT + t] = c0.y;
       sm.cash[(k + 2) * NT + t] = c1.x; sm.cash[(k + 3) * NT + t] = c1.y;
     }
@@ -574,9 +604,16 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       const int a = a0 + k;
       const bool v = a < A;
       slot[k] = v ? P.slot[aoff + a] : 0u;
-      sm.inv[k * NT + t] = v ? P.inv[aoff + a] : 0;
+      if constexpr (REGACC)
+        inv[k] = v ? P.inv[aoff + a] : 0;
+      else
+        sm.inv[k * NT + t] = v ? P.inv[aoff + a] : 0;
       sm.cash[k * NT + t] = v ? P.cash[aoff + a] : 0ll;
     }
+  }
+  if constexpr (REGACC) {
+#pragma unroll
+    for (int k = 0; k < AK; ++k) cpend[k] = 0;
   }
   const int32_t* mi = P.mi32 + (size_t)m * MI32_STRIDE;
   int hist[KS_HISTORY];
@@ -591,8 +628,20 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   int64_t sumv = mi64[MI_SUMV];
   uint64_t hash = (uint64_t)mi64[MI_HASH];
 
+  RuleConsts rc;
+  rc.zi_off = P.zi_off;
+  rc.zi_n = 2u * (uint32_t)P.zi_off + 1u;
+  rc.zi_qmax = (uint32_t)P.zi_qmax;
+  rc.mom_n = (uint32_t)P.mom_omax + 1u;
+  rc.mr_n = (uint32_t)P.mr_omax + 1u;
+  rc.rb_qmax = (uint32_t)P.rb_qmax;
+  const uint32_t gm = P.market_base + m;
+  // rule constants of the first step's orders
+  StepRules sr0 = step_rules(P, s0, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+  if (t < 4) sm.ctab[t] = class_rule(t, last, sr0.side_mom, sr0.side_mr, rc);
+
   // rebuild the aggregated resting book from the working orders
-  for (int i = t; i < 2 * sb; i += NT) book[i] = 0;
+  for (int i = t; i < 2 * book_len(Lcap); i += NT) book[i] = 0;
   if (t < 8) sm.kx[t] = 0ull;
   gsync<NT>(bar);
 #pragma unroll
@@ -602,20 +651,13 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       atomicOr(P.err, ERR_TICK);
       slot[k] &= W_STATIC;
     }
-    book_add<AGGR>(book, sb, w_qty(slot[k]) != 0u, slot[k]);
+    book_add<AGGR>(book_s, w_qty(slot[k]) != 0u, slot[k]);
   }
 
-  RuleConsts rc;
-  rc.zi_off = P.zi_off;
-  rc.zi_n = 2u * (uint32_t)P.zi_off + 1u;
-  rc.zi_qmax = (uint32_t)P.zi_qmax;
-  rc.mom_n = (uint32_t)P.mom_omax + 1u;
-  rc.mr_n = (uint32_t)P.mr_omax + 1u;
-  rc.rb_qmax = (uint32_t)P.rb_qmax;
   const bool carry = P.carry != 0;
-  const uint32_t cthr = P.cancel_thr;
+  const uint32_t cthr = carry ? P.cancel_thr : 0u;     // a discarded book has nothing to cancel
+  const uint32_t keep = carry ? 0xFFFFFFFFu : W_STATIC;  // what of an order word survives the step
   const bool traced = m < P.trace_markets;
-  const uint32_t gm = P.market_base + m;
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
 
   const bool policy_on = MLP && P.mlp != nullptr && P.mlp_pct > 0;
@@ -623,7 +665,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   if constexpr (MLP) {
     // the policy inputs of the first step read the rebuilt book
     gsync<NT>(bar);
-    publish_depth(sm, book, sb, L, last, p0, LT, t);
+    publish_depth(sm, book, L, last, p0, LT, t);
     gsync<NT>(bar);
 #pragma unroll
     for (int j = 0; j < 8; ++j) sf.h[j] = hist[j] - hist[j + 1];
@@ -633,23 +675,23 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 
   // orders of the first step
   if (n_steps > 0) {
-    const StepRules sr = step_rules(P, s0, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+    const StepRules& sr = sr0;
+    const uint32_t x0a = sr.sk.c0 ^ (uint32_t)a0;
     uint32_t pflags = 0;
 #pragma unroll
     for (int k = 0; k < AK; ++k) {
       if constexpr (MLP) {
         bool pol = false;
-        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb, &pol, &P,
-                                          &sf, sm.inv[k * NT + t]);
+        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s,
+                                          P.rk, &pol, &P, &sf, sm.inv[k * NT + t]);
         pflags |= pol ? (1u << k) : 0u;
       } else {
-        slot[k] = order_agent<AGGR>(slot[k], a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
+        slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
       }
     }
     if constexpr (MLP) {
       if (policy_on)
-        policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s0, gm, sf, last, aoff, traced, book,
-                             sb);
+        policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s0, gm, sf, last, aoff, traced, book);
     }
   }
 
@@ -662,27 +704,29 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     unsigned long long* kx_next = sm.kx + 4 * ((j + 1) & 1);
     ClearOut c;
     switch (LTsel) {
-      case 1: c = clear_step<NT, 1, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      case 2: c = clear_step<NT, 2, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      case 4: c = clear_step<NT, 4, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      case 8: c = clear_step<NT, 8, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      default: c = clear_step<NT, 0, MLP>(sm, book, sb, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 1: c = clear_step<NT, 1, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 2: c = clear_step<NT, 2, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 4: c = clear_step<NT, 4, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      case 8: c = clear_step<NT, 8, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+      default: c = clear_step<NT, 0, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
     }
-    const int vstar = c.vstar, p_lo = c.p_lo, p_hi = c.p_hi, pstar = c.pstar;
+    const int vstar = c.vstar, pstar = c.pstar;
     const bool trade = vstar > 0;
+    // An order of side/tick bits st fills fully when it is strictly better
+    // than its side's marginal tick (rank > 0) and is rationed at it (rank
+    // 0): rank = st - key_b for buys, key_s - st for sells.  Without a trade
+    // the keys put every order below its margin.
+    const uint32_t key_b = trade ? (uint32_t)c.p_hi << W_TICK_SHIFT : 0x1FFFFFFFu;
+    const uint32_t key_s = trade ? (((uint32_t)c.p_lo << W_TICK_SHIFT) | W_SIDE) : 0u;
 
     // ---- marginal quantities in agent order --------------------------------------------
     uint32_t exB = 0, exS = 0;
     if (trade) {
       uint32_t mB = 0, mS = 0;
-      // an order rests at a marginal tick iff its (side, tick) bits equal that tick's key
-      const uint32_t key_b = (uint32_t)p_hi << W_TICK_SHIFT;
-      const uint32_t key_s = ((uint32_t)p_lo << W_TICK_SHIFT) | W_SIDE;
 #pragma unroll
       for (int k = 0; k < AK; ++k) {
-        const uint32_t sl = slot[k];
-        const uint32_t st = sl & (W_SIDE | (W_TICK << W_TICK_SHIFT));
-        const uint32_t q = w_qty(sl);
+        const uint32_t st = slot[k] & W_ST;
+        const uint32_t q = w_qty(slot[k]);
         mB += st == key_b ? q : 0u;
         mS += st == key_s ? q : 0u;
       }
@@ -697,7 +741,6 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       exB = iB - mB;
       exS = iS - mS;
     }
-    gsync<NT>(bar);  // B5: book residual, remainders and marginal totals visible
 
     // ---- market scalars of step s ---------------------------------------------------------
     if (trade) last = pstar;
@@ -719,77 +762,72 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
         tr[1] = vstar;
       }
     }
-
-    // ---- fills of step s, fused with the orders of step s+1 ------------------------------
     const bool more = j + 1 < n_steps;
     const StepRules sr = step_rules(P, s + 1, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
+    if (t < 4) sm.ctab[t] = class_rule(t, last, sr.side_mom, sr.side_mr, rc);
+    gsync<NT>(bar);  // B5: book residual, remainders, marginal totals and rule constants visible
+
+    // ---- fills of step s, fused with the orders of step s+1 ------------------------------
+    const uint32_t x0a = sr.sk.c0 ^ (uint32_t)a0;
     if constexpr (MLP) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) sf.h[q] = hist[q] - hist[q + 1];
       sf.lastv = vstar;
     }
-    uint32_t pflags = 0;
+    // units still to fill at the marginal buy / sell tick before my first agent
+    int remB = 0, remS = 0;
     if (trade) {
-      const int Rb = sm.rem[0], Rs = sm.rem[1];
-      int preB = (int)(exB + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMB[lane] : 0u));
-      int preS = (int)(exS + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMS[lane] : 0u));
-      const uint32_t key_b = (uint32_t)p_hi << W_TICK_SHIFT;
-      const uint32_t key_s = ((uint32_t)p_lo << W_TICK_SHIFT) | W_SIDE;
+      remB = sm.rem[0] - (int)(exB + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMB[lane] : 0u));
+      remS = sm.rem[1] - (int)(exS + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMS[lane] : 0u));
+    }
+    uint32_t pflags = 0;
 #pragma unroll
-      for (int k = 0; k < AK; ++k) {
-        uint32_t sl = slot[k];
-        const int q = (int)w_qty(sl);
-        const bool sell = w_sell(sl) != 0u;
-        const uint32_t st = sl & (W_SIDE | (W_TICK << W_TICK_SHIFT));
-        const int tk = (int)(st >> W_TICK_SHIFT);
-        const bool full = sell ? tk < p_lo : tk > p_hi;  // strictly better than the marginal tick
-        const bool marg = st == (sell ? key_s : key_b);
-        const int pre = sell ? preS : preB;
-        const int fm = min(max((sell ? Rs : Rb) - pre, 0), q);
-        const int f = full ? q : (marg ? fm : 0);
-        const int adv = marg ? q : 0;
-        preS += sell ? adv : 0;
-        preB += sell ? 0 : adv;
-        if (f) {
-          sm.inv[k * NT + t] += sell ? -f : f;
-          sm.cash[k * NT + t] += (int64_t)(sell ? pstar : -pstar) * f;
-        }
-        sl -= (uint32_t)f;
-        if (!carry) sl &= W_STATIC;
-        if (more) {
-          if constexpr (MLP) {
-            bool pol = false;
-            sl = order_agent<AGGR, true>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb, &pol, &P, &sf,
-                                         sm.inv[k * NT + t]);
-            pflags |= pol ? (1u << k) : 0u;
-          } else {
-            sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
-          }
-        }
-        slot[k] = sl;
+    for (int k = 0; k < AK; ++k) {
+      const uint32_t sl0 = slot[k];
+      const int q = (int)w_qty(sl0);
+      const uint32_t st = sl0 & W_ST;
+      const bool sell = (sl0 & W_SIDE) != 0u;
+      const int rank = sell ? (int)(key_s - st) : (int)(st - key_b);
+      const bool marg = rank == 0;
+      const int fm = min(max(sell ? remS : remB, 0), q);
+      const int f = rank > 0 ? q : (marg ? fm : 0);
+      const int adv = marg ? q : 0;
+      remS -= sell ? adv : 0;
+      remB -= sell ? 0 : adv;
+      const int sfill = sell ? -f : f;
+      if constexpr (REGACC) {
+        inv[k] += sfill;
+        cpend[k] -= pstar * sfill;
+      } else if (f) {
+        sm.inv[k * NT + t] += sfill;
+        sm.cash[k * NT + t] -= (int64_t)pstar * sfill;
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < AK; ++k) {
-        uint32_t sl = slot[k];
-        if (!carry) sl &= W_STATIC;
-        if (more) {
-          if constexpr (MLP) {
-            bool pol = false;
-            sl = order_agent<AGGR, true>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb, &pol, &P, &sf,
-                                         sm.inv[k * NT + t]);
-            pflags |= pol ? (1u << k) : 0u;
-          } else {
-            sl = order_agent<AGGR>(sl, a0 + k, a0 + k < A, sr, carry, cthr, L, rc, book, sb);
-          }
+      uint32_t sl = (sl0 - (uint32_t)f) & keep;
+      if (more) {
+        if constexpr (MLP) {
+          bool pol = false;
+          sl = order_agent<AGGR, true>(sl, a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk,
+                                       &pol, &P, &sf, sm.inv[k * NT + t]);
+          pflags |= pol ? (1u << k) : 0u;
+        } else {
+          sl = order_agent<AGGR>(sl, a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
         }
-        slot[k] = sl;
+      }
+      slot[k] = sl;
+    }
+    if constexpr (REGACC) {
+      if ((j + 1) % CASH_FLUSH_STEPS == 0) {
+#pragma unroll
+        for (int k = 0; k < AK; ++k) {
+          sm.cash[k * NT + t] += cpend[k];
+          cpend[k] = 0;
+        }
       }
     }
     if constexpr (MLP) {
       if (policy_on && more)
         policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s + 1, gm, sf, last, aoff, traced,
-                             book, sb);
+                             book);
     }
   }
 
@@ -798,14 +836,22 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 #pragma unroll
     for (int k = 0; k < AK; k += 4) {
       *reinterpret_cast<uint4*>(P.slot + aoff + a0 + k) = make_uint4(slot[k], slot[k + 1], slot[k + 2], slot[k + 3]);
-      *reinterpret_cast<int4*>(P.inv + aoff + a0 + k) =
-          make_int4(sm.inv[(k + 0) * NT + t], sm.inv[(k + 1) * NT + t], sm.inv[(k + 2) * NT + t],
-                    sm.inv[(k + 3) * NT + t]);
       longlong2 c0, c1;
       c0.x = sm.cash[(k + 0) * NT + t];
       c0.y = sm.cash[(k + 1) * NT + t];
       c1.x = sm.cash[(k + 2) * NT + t];
       c1.y = sm.cash[(k + 3) * NT + t];
+      if constexpr (REGACC) {
+        *reinterpret_cast<int4*>(P.inv + aoff + a0 + k) = make_int4(inv[k], inv[k + 1], inv[k + 2], inv[k + 3]);
+        c0.x += cpend[k];
+        c0.y += cpend[k + 1];
+        c1.x += cpend[k + 2];
+        c1.y += cpend[k + 3];
+      } else {
+        *reinterpret_cast<int4*>(P.inv + aoff + a0 + k) =
+            make_int4(sm.inv[(k + 0) * NT + t], sm.inv[(k + 1) * NT + t], sm.inv[(k + 2) * NT + t],
+                      sm.inv[(k + 3) * NT + t]);
+      }
       *reinterpret_cast<longlong2*>(P.cash + aoff + a0 + k) = c0;
       *reinterpret_cast<longlong2*>(P.cash + aoff + a0 + k + 2) = c1;
     }
@@ -815,8 +861,13 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       const int a = a0 + k;
       if (a < A) {
         P.slot[aoff + a] = slot[k];
-        P.inv[aoff + a] = sm.inv[k * NT + t];
-        P.cash[aoff + a] = sm.cash[k * NT + t];
+        if constexpr (REGACC) {
+          P.inv[aoff + a] = inv[k];
+          P.cash[aoff + a] = sm.cash[k * NT + t] + cpend[k];
+        } else {
+          P.inv[aoff + a] = sm.inv[k * NT + t];
+          P.cash[aoff + a] = sm.cash[k * NT + t];
+        }
       }
     }
   }

@@ -6,17 +6,16 @@
 
 namespace ks {
 
-// Register-cap classes of the launch bounds: 0 = compiler's choice, 1 = about
-// 85 registers per thread (policy kernels: 128, so that two 256-thread CTAs
-// share an SM).
-template <int NT, int OCC, bool MLP = false>
-struct MinBlocks {
-  static constexpr int cap = MLP ? 128 : 85;
-  static constexpr int value = OCC == 0 ? 1 : (65536 / (NT * cap) > 0 ? 65536 / (NT * cap) : 1);
-};
+// Register-cap classes of the launch bounds: 0 = compiler's choice, 1 = 128
+// registers per thread (two 256-thread CTAs per SM), 2 = 85 (three).
+// Returns the launch bounds' minimum of resident CTAs.
+__host__ __device__ constexpr int plain_min_ctas(int nt, int occ) {
+  return occ == 0 ? 1 : (65536 / (nt * (occ == 2 ? 85 : 128)) > 0 ? 65536 / (nt * (occ == 2 ? 85 : 128)) : 1);
+}
 
 template <int NT, int AK, bool AGGR, int OCC, bool MLP = false>
-__global__ void __launch_bounds__(NT, (MinBlocks<NT, OCC, MLP>::value)) plain_kernel(DevParams P, uint32_t n_steps) {
+__global__ void __launch_bounds__(NT, plain_min_ctas(NT, OCC)) plain_kernel(DevParams P, uint32_t n_steps) {
+  constexpr int BUDGET = thread_reg_budget(NT, plain_min_ctas(NT, OCC));
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t s0 = (uint32_t)(*P.step);
   if constexpr (MLP) {
@@ -25,8 +24,8 @@ __global__ void __launch_bounds__(NT, (MinBlocks<NT, OCC, MLP>::value)) plain_ke
     mlp_cta_setup(mc, P.mlp);
     unsigned char* graw = smem_raw + mlp_cta_bytes();
     size_t o[8];
-    const size_t mbytes = market_smem_layout(NT, AK, P.Lmax, true, o);
-    const Smem sm = carve<NT, AK, true>(graw, P.Lmax);
+    const size_t mbytes = group_smem_layout(BUDGET, NT, AK, P.Lmax, true, o);
+    const Smem sm = carve<NT, AK, true, true>(graw, P.Lmax);
     MlpWG mw;
     mw.act = graw + mbytes;
     mw.bar = &mc.bars[0];
@@ -35,12 +34,13 @@ __global__ void __launch_bounds__(NT, (MinBlocks<NT, OCC, MLP>::value)) plain_ke
     mw.phase = 0;
     mw.abort = false;
     for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x)
-      run_market<NT, AK, false, true>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax, &mw, mc.sw);
+      run_market<NT, AK, false, true, false>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax, &mw, mc.sw);
     mlp_cta_teardown(mc);
   } else {
-    const Smem sm = carve<NT, AK>(smem_raw, P.Lmax);
+    constexpr bool REGACC = accounts_in_registers(BUDGET, AK, false);
+    const Smem sm = carve<NT, AK, false, !REGACC>(smem_raw, P.Lmax);
     for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x)
-      run_market<NT, AK, AGGR>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax);
+      run_market<NT, AK, AGGR, false, REGACC>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax);
   }
 }
 
@@ -50,10 +50,10 @@ cudaError_t launch_plain(const DevParams& p, uint32_t n_steps, int grid, size_t 
   return cudaGetLastError();
 }
 
-// Dynamic shared memory of a plain launch.
-__host__ __device__ inline size_t plain_launch_smem(int nt, int ak, int Lmax, bool mlp) {
+// Dynamic shared memory of a plain launch (occ: register-cap class).
+__host__ __device__ inline size_t plain_launch_smem(int nt, int ak, int occ, int Lmax, bool mlp) {
   size_t o[8];
-  const size_t m = market_smem_layout(nt, ak, Lmax, mlp, o);
+  const size_t m = group_smem_layout(thread_reg_budget(nt, plain_min_ctas(nt, occ)), nt, ak, Lmax, mlp, o);
   return mlp ? mlp_cta_bytes() + m + MLP_ACT_BYTES : m;
 }
 

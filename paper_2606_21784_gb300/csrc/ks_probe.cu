@@ -42,13 +42,19 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_mul_wide(uint32_t iters, 
   sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = x;
 }
 
-// The persistent kernel's per-agent draw (StepKey + step_draw), one block per iteration.
+// The persistent kernel's per-agent draw (StepKey + step_draw_x0), one block per iteration.
 __global__ void __launch_bounds__(PROBE_THREADS) probe_philox(uint32_t iters, uint64_t* sink) {
-  const StepKey sk = step_key(7u, blockIdx.x, 0u, 0x1234567u, 0x89abcdefu);
+  uint32_t rk[20];
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = 0x1234567u + (uint32_t)r * PH_WA;
+    rk[2 * r + 1] = 0x89abcdefu + (uint32_t)r * PH_WB;
+  }
+  const StepKey sk = step_key(7u, blockIdx.x, 0u, rk);
   uint32_t x = 0;
   const uint32_t base = threadIdx.x;
   for (uint32_t it = 0; it < iters; ++it) {
-    const uint4 w = step_draw(sk, base + it * PROBE_THREADS);
+    const uint4 w = step_draw_x0(sk, sk.c0 ^ (base + it * PROBE_THREADS), rk);
     x ^= w.x ^ w.y ^ w.z ^ w.w;
   }
   sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = x;
