@@ -781,39 +781,53 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       remS = sm.rem[1] - (int)(exS + __reduce_add_sync(0xffffffffu, lane < wid ? sm.wMS[lane] : 0u));
     }
     uint32_t pflags = 0;
+    // The orders of two agents share one block (their Philox chains
+    // interleave); larger groups gained nothing and cost registers, which
+    // the policy kernels cannot spare.
+    constexpr int IL = (AK < 2 || MLP) ? 1 : 2;
 #pragma unroll
-    for (int k = 0; k < AK; ++k) {
-      const uint32_t sl0 = slot[k];
-      const int q = (int)w_qty(sl0);
-      const uint32_t st = sl0 & W_ST;
-      const bool sell = (sl0 & W_SIDE) != 0u;
-      const int rank = sell ? (int)(key_s - st) : (int)(st - key_b);
-      const bool marg = rank == 0;
-      const int fm = min(max(sell ? remS : remB, 0), q);
-      const int f = rank > 0 ? q : (marg ? fm : 0);
-      const int adv = marg ? q : 0;
-      remS -= sell ? adv : 0;
-      remB -= sell ? 0 : adv;
-      const int sfill = sell ? -f : f;
-      if constexpr (REGACC) {
-        inv[k] += sfill;
-        cpend[k] -= pstar * sfill;
-      } else if (f) {
-        sm.inv[k * NT + t] += sfill;
-        sm.cash[k * NT + t] -= (int64_t)pstar * sfill;
+    for (int kb = 0; kb < AK; kb += IL) {
+      uint32_t sl[IL];
+#pragma unroll
+      for (int i = 0; i < IL; ++i) {
+        const int k = kb + i;
+        const uint32_t sl0 = slot[k];
+        const int q = (int)w_qty(sl0);
+        const uint32_t st = sl0 & W_ST;
+        const bool sell = (sl0 & W_SIDE) != 0u;
+        const int rank = sell ? (int)(key_s - st) : (int)(st - key_b);
+        const bool marg = rank == 0;
+        const int fm = min(max(sell ? remS : remB, 0), q);
+        const int f = rank > 0 ? q : (marg ? fm : 0);
+        const int adv = marg ? q : 0;
+        remS -= sell ? adv : 0;
+        remB -= sell ? 0 : adv;
+        const int sfill = sell ? -f : f;
+        if constexpr (REGACC) {
+          inv[k] += sfill;
+          cpend[k] -= pstar * sfill;
+        } else if (f) {
+          sm.inv[k * NT + t] += sfill;
+          sm.cash[k * NT + t] -= (int64_t)pstar * sfill;
+        }
+        sl[i] = (sl0 - (uint32_t)f) & keep;
       }
-      uint32_t sl = (sl0 - (uint32_t)f) & keep;
       if (more) {
-        if constexpr (MLP) {
-          bool pol = false;
-          sl = order_agent<AGGR, true>(sl, a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk,
-                                       &pol, &P, &sf, sm.inv[k * NT + t]);
-          pflags |= pol ? (1u << k) : 0u;
-        } else {
-          sl = order_agent<AGGR>(sl, a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
+#pragma unroll
+        for (int i = 0; i < IL; ++i) {
+          const int k = kb + i;
+          if constexpr (MLP) {
+            bool pol = false;
+            sl[i] = order_agent<AGGR, true>(sl[i], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s,
+                                            P.rk, &pol, &P, &sf, sm.inv[k * NT + t]);
+            pflags |= pol ? (1u << k) : 0u;
+          } else {
+            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
+          }
         }
       }
-      slot[k] = sl;
+#pragma unroll
+      for (int i = 0; i < IL; ++i) slot[kb + i] = sl[i];
     }
     if constexpr (REGACC) {
       if ((j + 1) % CASH_FLUSH_STEPS == 0) {
