@@ -240,7 +240,7 @@ ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l);
 /* Switches the ensemble to the batched kernel with the given plan; uploads the
  * work list on `stream` and synchronises it.  cta_threads: 512 or 1024.
  * Uneven ensembles start with a default plan (one bucket per power-of-two
- * (L, A) class, about 8 agents per thread, 1024-thread CTAs). */
+ * (L, A) class, about 8 agents per thread, 512-thread CTAs). */
 ks_status ks_set_batch_plan(ks_ensemble* e, int32_t cta_threads, const ks_bucket* buckets, int32_t n_buckets,
                             void* stream);
 

@@ -67,7 +67,7 @@ def _pow2(x):
 
 
 # compiled policy-capable shapes: (threads, agents per thread, register cap classes)
-POLICY_SHAPES = ((128, 16, (0, 1)), (256, 8, (0, 1)), (256, 16, (0, 1)), (512, 8, (0,)), (512, 16, (0,)),
+POLICY_SHAPES = ((128, 16, (0, 1)), (256, 8, (0, 1)), (256, 16, (0, 1)), (512, 4, (0,)), (512, 8, (0,)), (512, 16, (0,)),
                  (1024, 8, (0,)), (1024, 16, (0,)))
 
 

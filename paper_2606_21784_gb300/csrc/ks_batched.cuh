@@ -37,8 +37,9 @@ __device__ __forceinline__ void run_item(const DevParams& P, const BatchArgs& B,
   }
 }
 
-// Policy-capable variant: each group also owns an activation buffer after
-// its market shared memory, an mbarrier and 64 TMEM columns of the CTA.
+// Policy-capable variant: each warpgroup of a group also owns an activation
+// buffer (after the group's market shared memory), an mbarrier, 64 TMEM
+// columns of the CTA and a named barrier.
 template <int NT, int GT, int AK>
 __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
                                              unsigned char* raw, const MlpCta& mc) {
@@ -48,15 +49,20 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
   if (g < G && g < (int)d.y) {
     size_t o[8];
     const size_t mbytes = group_smem_layout(thread_reg_budget(NT, 1), GT, AK, (int)d.w, true, o);
-    const size_t gsz = mbytes + MLP_ACT_BYTES;
+    const int ntw = max(1, (int)(d.z >> 16));  // warpgroups of a group evaluating policy tiles (host-chosen)
+    const size_t gsz = mbytes + (size_t)ntw * MLP_ACT_BYTES;
     unsigned char* graw = raw + (size_t)g * gsz;
     const Smem sm = carve<GT, AK, true, true>(graw, (int)d.w);
     const int bar = (GT == NT) ? 0 : 1 + g;
+    const int wl = ((int)threadIdx.x % GT) / 128;  // warpgroup in the group
+    const int wc = (int)threadIdx.x / 128;         // warpgroup in the CTA
     MlpWG mw;
-    mw.act = graw + mbytes;
-    mw.bar = &mc.bars[g];
-    mw.tmem = *mc.tslot + (uint32_t)(g * MLP_TMEM_COLS);
-    mw.bar_id = (GT == 128) ? bar : 8 + g;
+    mw.wg = wl;
+    mw.nwg = ntw;
+    mw.act = graw + mbytes + (size_t)min(wl, ntw - 1) * MLP_ACT_BYTES;
+    mw.bar = &mc.bars[wc];
+    mw.tmem = *mc.tslot + (uint32_t)(wc * MLP_TMEM_COLS);
+    mw.bar_id = (GT == 128) ? bar : 8 + wc;
     mw.phase = 0;
     mw.abort = false;
     run_market<GT, AK, false, true, false>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w, &mw,

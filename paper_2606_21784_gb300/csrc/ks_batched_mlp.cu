@@ -7,7 +7,7 @@ namespace ks {
   template <>                                                                                                  \
   __device__ __forceinline__ void dispatch_item_mlp<NT>(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n, \
                                         unsigned char* raw, const MlpCta& mc) {                                \
-    switch (d.z) {                                                                                             \
+    switch (d.z & 0xFFFFu) {                                                                                             \
       KS_BATCH_MLP_VARIANTS_##NT(KS_MLP_CASE##NT) default : if (threadIdx.x == 0) atomicOr(P.err, ERR_SHAPE);  \
     }                                                                                                          \
   }                                                                                                            \

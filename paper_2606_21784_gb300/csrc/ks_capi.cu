@@ -353,18 +353,38 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
     return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
   if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
-  const size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, e->mlp);
+  size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, e->mlp);
   if (smem > e->max_smem) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more shared memory than a CTA has");
   const void* k = v->kernel;
   KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KS_CUDA(resident_ctas(k, l->threads, smem, e->mlp ? (int)MLP_TMEM_COLS : 0, &occ));
+  const int tmem_cols = e->mlp ? (l->threads / 128) * (int)MLP_TMEM_COLS : 0;  // 64 per warpgroup
+  KS_CUDA(resident_ctas(k, l->threads, smem, tmem_cols, &occ));
   if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+  int tile_wgs = 1;
+  if (e->mlp) {
+    // as many warpgroups evaluate policy tiles (one activation buffer each)
+    // as fit without lowering the resident CTAs per SM
+    for (int w = l->threads / 128; w > 1; --w) {
+      const size_t s = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, true, w);
+      if (s > e->max_smem) continue;
+      int o = 0;
+      KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s));
+      KS_CUDA(resident_ctas(k, l->threads, s, tmem_cols, &o));
+      if (o >= occ) {
+        tile_wgs = w;
+        smem = s;
+        break;
+      }
+    }
+    KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
   // resident CTAs must not ask for more TMEM than an SM has (512 columns)
-  if (e->mlp && occ * (int)MLP_TMEM_COLS > 512) return arg_fail(KS_ERR_UNSUPPORTED, "policy launch oversubscribes TMEM");
+  if (e->mlp && occ * tmem_cols > 512) return arg_fail(KS_ERR_UNSUPPORTED, "policy launch oversubscribes TMEM");
   const int per_sm = l->ctas_per_sm > 0 ? std::min(occ, l->ctas_per_sm) : occ;
   e->grid = (int)std::min<int64_t>((int64_t)e->M, (int64_t)per_sm * e->num_sms);
   e->smem = smem;
+  e->dp.mlp_tile_wgs = tile_wgs;
   e->var = v;
   e->launch = *l;
   e->mode = 0;
@@ -382,10 +402,13 @@ static int batch_variant_id(int nt, int gt, int ak, bool mlp) {
   return -1;
 }
 
-// Groups of one bucket that fit one CTA: thread count, barrier ids, shared memory.
-static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz, bool mlp) {
+// Groups of one bucket that fit one CTA: thread count, barrier ids, shared
+// memory (policy kernels: tile_wgs activation buffers per group).
+static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz, bool mlp,
+                          int tile_wgs = 1) {
   size_t o[8];
-  *gsz = group_smem_layout(thread_reg_budget(nt, 1), gt, ak, Lcap, mlp, o) + (mlp ? MLP_ACT_BYTES : 0);
+  *gsz = group_smem_layout(thread_reg_budget(nt, 1), gt, ak, Lcap, mlp, o) +
+         (mlp ? (size_t)tile_wgs * MLP_ACT_BYTES : 0);
   if (mlp) max_smem = max_smem > mlp_cta_bytes() ? max_smem - mlp_cta_bytes() : 0;
   int g = nt / gt;
   if (gt != 32 && gt != nt) g = std::min(g, 15);
@@ -414,6 +437,9 @@ static bool default_shape(int nt, int Ac, int* gt, int* ak, bool mlp) {
   *ak = tab[best][1];
   return true;
 }
+
+// CTA size of the default batched plan (the policy-capable batched kernel exists for 512 only).
+constexpr int kDefaultBatchThreads = 512;
 
 static std::vector<ks_bucket> default_plan(const std::vector<int32_t>& L, const std::vector<int32_t>& A, int nt,
                                            bool mlp) {
@@ -465,6 +491,28 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
     if (b == nb) return arg_fail(KS_ERR_INVALID_ARG, "a market matches no bucket of the plan");
     members[b].push_back(m);
   }
+  // policy kernel: as many warpgroups of a group evaluate policy tiles (one
+  // activation buffer each) as fit in the shared memory the plan needs with one
+  std::vector<int> tile_wgs(nb, 1);
+  if (mlp) {
+    size_t cap = 0;
+    for (int b = 0; b < nb; ++b)
+      if (!members[b].empty()) cap = std::max(cap, (size_t)std::min<size_t>(G[b], members[b].size()) * gsz[b]);
+    for (int b = 0; b < nb; ++b) {
+      if (members[b].empty()) continue;
+      const size_t used = std::min<size_t>(G[b], members[b].size());
+      for (int w = buckets[b].group_threads / 128; w > 1; --w) {
+        size_t gw = 0;
+        const int Gw = groups_per_cta(nt, buckets[b].group_threads, buckets[b].agents_per_thread, buckets[b].L_max,
+                                      max_dyn, &gw, true, w);
+        if (Gw >= G[b] && used * gw <= cap) {
+          tile_wgs[b] = w;
+          gsz[b] = gw;
+          break;
+        }
+      }
+    }
+  }
   struct Item {
     double cost;
     int bucket;
@@ -496,7 +544,8 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
     uint4 d;
     d.x = (uint32_t)order.size();
     d.y = (uint32_t)it.mk.size();
-    d.z = (uint32_t)var[it.bucket];
+    // variant id; the policy kernel also reads its tile warpgroups from bits 16+
+    d.z = (uint32_t)var[it.bucket] | (mlp ? (uint32_t)tile_wgs[it.bucket] << 16 : 0u);
     d.w = (uint32_t)buckets[it.bucket].L_max;
     order.insert(order.end(), it.mk.begin(), it.mk.end());
     ditems.push_back(d);
@@ -676,8 +725,10 @@ ks_status ks_create_ensemble(const ks_config* cfg, void* workspace, size_t ws_by
   KS_CUDA_E(cudaStreamSynchronize(st));
 #undef KS_CUDA_E
   if (!sz.uniform) {
-    // uneven ensembles default to the batched kernel with one bucket per (L, A) power-of-two class
-    const int nt = e->mlp ? 512 : 1024;
+    // uneven ensembles default to the batched kernel with one bucket per (L, A) power-of-two class,
+    // in 512-thread CTAs (measured 5-7% faster than 1024-thread CTAs on the 20000- and 32768-market
+    // ensembles: a 1024-thread CTA leaves 64 registers per thread)
+    const int nt = kDefaultBatchThreads;
     std::vector<ks_bucket> plan = default_plan(e->L, e->A, nt, e->mlp);
     s = build_batch(e, nt, plan.data(), (int)plan.size(), st);
     if (s != KS_OK) {
@@ -847,9 +898,8 @@ ks_status ks_set_capture(ks_ensemble* e, const ks_capture* c) {
   // switch between the rule-only and the policy-capable kernels, keeping the mode
   e->mlp = want;
   if (e->mode == 1) {
-    const int nt = e->mlp ? 512 : 1024;
-    std::vector<ks_bucket> plan = default_plan(e->L, e->A, nt, e->mlp);
-    return build_batch(e, nt, plan.data(), (int)plan.size(), nullptr);
+    std::vector<ks_bucket> plan = default_plan(e->L, e->A, kDefaultBatchThreads, e->mlp);
+    return build_batch(e, kDefaultBatchThreads, plan.data(), (int)plan.size(), nullptr);
   }
   ks_launch l = default_launch(e->Amax, e->M, e->num_sms, e->mlp);
   return apply_launch(e, &l);

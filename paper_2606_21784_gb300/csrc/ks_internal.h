@@ -38,6 +38,7 @@ struct DevParams {
   uint32_t mix0, mix01;  // class percentile thresholds: ZI < mix0 <= MOM < mix01 <= MR
   int32_t zi_off, zi_qmax, mom_lb, mom_omax, mr_omax, rb_qmax;
   uint32_t mlp_pct;
+  int32_t mlp_tile_wgs;  // plain policy kernels: warpgroups of a CTA that evaluate policy tiles
   int32_t tie_rule;
   uint32_t trace_markets, trace_steps;
   int32_t Lmax;  // largest L in the ensemble (shared-memory sizing)

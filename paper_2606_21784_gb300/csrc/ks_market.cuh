@@ -226,9 +226,11 @@ __device__ __forceinline__ int hist_at(const int (&hist)[KS_HISTORY], int lb) {
 
 
 // Policy decisions of one step for the agents flagged in `pflags` (bit k =
-// agent a0 + k): rows are compacted in agent order, the group's first
-// warpgroup evaluates them 128 at a time on the tensor cores and samples the
-// actions (Philox stream 3 of step sdec), then the owners place the orders.
+// agent a0 + k): rows are compacted in agent order, the group's warpgroups
+// evaluate them in tiles of 128 (tile i on warpgroup i mod mw.nwg, each
+// with its own activation buffer, accumulator columns and mbarrier in `mw`)
+// on the tensor cores and sample the actions (Philox stream 3 of step
+// sdec), then the owners place the orders.
 // The inventories of the flagged agents are in sm.inv.
 template <int NT, int AK>
 __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm, MlpWG& mw, const unsigned char* sw,
@@ -269,9 +271,9 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
     if ((pflags >> k) & 1u) sm.rowbuf[r++] = (uint32_t)(a0 + k);
   gsync<NT>(bar);
   if (t == 0 && total > 0 && P.pol_count) atomicAdd(P.pol_count, (unsigned long long)total);
-  if (total > 0 && t < 128) {
-    for (int tile = 0; tile * 128 < total; ++tile) {
-      const int row = tile * 128 + t;
+  if (total > 0 && mw.wg < mw.nwg) {
+    for (int tile = mw.wg; tile * 128 < total; tile += mw.nwg) {
+      const int row = tile * 128 + (t & 127);
       const bool valid = row < total;
       const int a = valid ? (int)sm.rowbuf[row] : 0;
       const int inv = valid ? sm.inv[(a % AK) * NT + a / AK] : 0;

@@ -44,6 +44,8 @@ __global__ void __launch_bounds__(128 * FWD_NWG, 1)
   g.bar_id = 1 + wg;
   g.phase = 0;
   g.abort = false;
+  g.wg = wg;
+  g.nwg = FWD_NWG;
   const int64_t ntiles = (n + 127) / 128;
   for (int64_t tile = (int64_t)blockIdx.x * FWD_NWG + wg; tile < ntiles; tile += (int64_t)gridDim.x * FWD_NWG) {
     const int64_t row = tile * 128 + r;

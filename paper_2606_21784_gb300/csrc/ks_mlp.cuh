@@ -115,6 +115,8 @@ struct MlpWG {
   int bar_id;          // named barrier of the 128 threads
   uint32_t phase;      // parity of the next mbarrier completion
   bool abort;          // a bounded wait gave up: no further MMAs
+  int wg;              // this warpgroup's index in its market group
+  int nwg;             // warpgroups of the group that evaluate policy tiles (those with wg < nwg)
 };
 
 // Issues one layer: for each 16-wide K chunk, acc += hi * W and acc += lo * W;

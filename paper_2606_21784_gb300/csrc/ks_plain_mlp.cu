@@ -10,7 +10,7 @@ namespace ks {
   }
 extern const PlainVariant kPlainMlp[] = {KS_MLP_VARIANT(128, 16, 0), KS_MLP_VARIANT(128, 16, 1), KS_MLP_VARIANT(256, 8, 0),
                                          KS_MLP_VARIANT(256, 8, 1),  KS_MLP_VARIANT(256, 16, 0), KS_MLP_VARIANT(256, 16, 1),
-                                         KS_MLP_VARIANT(512, 8, 0),  KS_MLP_VARIANT(512, 16, 0), KS_MLP_VARIANT(1024, 8, 0),
-                                         KS_MLP_VARIANT(1024, 16, 0)};
+                                         KS_MLP_VARIANT(512, 4, 0),  KS_MLP_VARIANT(512, 8, 0),  KS_MLP_VARIANT(512, 16, 0),
+                                         KS_MLP_VARIANT(1024, 8, 0), KS_MLP_VARIANT(1024, 16, 0)};
 extern const int kPlainMlpCount = sizeof(kPlainMlp) / sizeof(kPlainMlp[0]);
 }  // namespace ks
