@@ -75,6 +75,13 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return make_uint4(c0, c1, c2, c3);
 }
 
+// The same block with precomputed round keys (rk as in DevParams::rk).
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, rk[2 * r], rk[2 * r + 1]);
+  return make_uint4(c0, c1, c2, c3);
+}
+
 // Per-step draws use counter (step, agent, market, 0).  Within one step and
 // market only the agent word varies, so the parts of rounds 1-3 that do not
 // depend on it are computed once (StepKey) and each agent finishes the block

@@ -280,7 +280,7 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
       float z[MLP_OUT];
       mlp_tile_logits(mw, sw, sm.cvec, (float)inv * (1.0f / 256.0f), z, P.err);
       if (valid) {
-        const uint4 w = philox(sdec, (uint32_t)a, gm, 3u, P.key0, P.key1);
+        const uint4 w = philox_rk(sdec, (uint32_t)a, gm, 3u, P.rk);
         sm.rowbuf[row] = mlp_decision(z, w, last, L, P.rb_qmax);
       }
     }

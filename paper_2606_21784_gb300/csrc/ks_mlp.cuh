@@ -48,7 +48,9 @@ constexpr uint32_t MLP_SM_W1 = 0;                               // f32 [64][32]
 constexpr uint32_t MLP_SM_W2 = MLP_SM_W1 + 4 * MLP_H * MLP_IN;    // bf16 [64 x 64] operand layout
 constexpr uint32_t MLP_SM_W3 = MLP_SM_W2 + 2 * MLP_H * MLP_H;     // bf16 [48 x 64], rows 37..47 zero
 constexpr uint32_t MLP_SM_B = MLP_SM_W3 + 2 * MLP_OUT_PAD * MLP_H;  // f32 b1[64] b2[64] b3[48]
-constexpr uint32_t MLP_SM_BYTES = MLP_SM_B + 4 * (MLP_H + MLP_H + MLP_OUT_PAD);
+// f32 [64]: column 8 of W1 (the inventory input) stored contiguously for the step loop's layer 1
+constexpr uint32_t MLP_SM_W1INV = MLP_SM_B + 4 * (MLP_H + MLP_H + MLP_OUT_PAD);
+constexpr uint32_t MLP_SM_BYTES = MLP_SM_W1INV + 4 * MLP_H;
 // Per warpgroup: the hidden activations as two [128 x 64] BF16 operands (high, low part).
 constexpr uint32_t MLP_ACT_HALF = 2 * 128 * MLP_H;
 constexpr uint32_t MLP_ACT_BYTES = 2 * MLP_ACT_HALF;
@@ -82,6 +84,8 @@ __device__ __forceinline__ void mlp_load_weights(const unsigned char* blob, unsi
     else v = (i - 2 * MLP_H) < MLP_OUT ? b3[i - 2 * MLP_H] : 0.0f;
     sb[i] = v;
   }
+  float* w1i = reinterpret_cast<float*>(sw + MLP_SM_W1INV);
+  for (int i = tid; i < MLP_H; i += nthr) w1i[i] = __bfloat162float(W1[i * MLP_IN + 8]);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -133,10 +137,12 @@ __device__ __forceinline__ void mlp_issue(const MlpWG& g, uint32_t act_addr, uin
   mma_commit(g.bar);
 }
 
-// Waits for the layer's MMAs; the warpgroup agrees on a timeout.
+// Waits for the layer's MMAs: the issuing thread polls the mbarrier, the
+// others wait at the warpgroup's named barrier, which also spreads a timeout.
 __device__ __forceinline__ void mlp_wait(MlpWG& g, uint32_t* err) {
-  bool ok = g.abort ? false : mbar_wait_bounded(g.bar, g.phase, MLP_WAIT_LIMIT);
-  const bool any_fail = named_sync_or(g.bar_id, 128, !ok);
+  bool ok = true;
+  if ((threadIdx.x & 127) == 0) ok = g.abort ? false : mbar_wait_bounded(g.bar, g.phase, MLP_WAIT_LIMIT);
+  const bool any_fail = named_sync_or(g.bar_id, 128, !ok) || g.abort;
   if (any_fail && !g.abort) {
     g.abort = true;
     if ((threadIdx.x & 127) == 0) atomicOr(err, ERR_MLP_WAIT);
@@ -319,16 +325,19 @@ __device__ __forceinline__ void mlp_store_split8(unsigned char* act, int r, int 
 __device__ __forceinline__ void mlp_tile_logits(MlpWG& g, const unsigned char* sw, const float* cvec, float x_inv,
                                                 float* z, uint32_t* err) {
   const int r = (int)(threadIdx.x & 127);
-  const float* w1 = reinterpret_cast<const float*>(sw + MLP_SM_W1);
+  const float4* w1i = reinterpret_cast<const float4*>(sw + MLP_SM_W1INV);
+  const float4* cv = reinterpret_cast<const float4*>(cvec);
   const float* sb = reinterpret_cast<const float*>(sw + MLP_SM_B);
   const uint32_t act_addr = smem_u32(g.act);
   const uint32_t w_addr = smem_u32(sw);
   const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) & 3) * 32u;
 #pragma unroll 1
   for (int kc = 0; kc < MLP_H / 8; ++kc) {
-    float h[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) h[j] = fmaxf(fmaf(w1[(8 * kc + j) * MLP_IN + 8], x_inv, cvec[8 * kc + j]), 0.0f);
+    const float4 wa = w1i[2 * kc], wb = w1i[2 * kc + 1], ca = cv[2 * kc], cb = cv[2 * kc + 1];
+    const float h[8] = {fmaxf(fmaf(wa.x, x_inv, ca.x), 0.0f), fmaxf(fmaf(wa.y, x_inv, ca.y), 0.0f),
+                        fmaxf(fmaf(wa.z, x_inv, ca.z), 0.0f), fmaxf(fmaf(wa.w, x_inv, ca.w), 0.0f),
+                        fmaxf(fmaf(wb.x, x_inv, cb.x), 0.0f), fmaxf(fmaf(wb.y, x_inv, cb.y), 0.0f),
+                        fmaxf(fmaf(wb.z, x_inv, cb.z), 0.0f), fmaxf(fmaf(wb.w, x_inv, cb.w), 0.0f)};
     mlp_store_split8(g.act, r, kc, h);
   }
   fence_async_smem();
