@@ -701,3 +701,191 @@ done:
   free(buy); free(sell); free(dcum); free(scum); free(vol); free(fill);
   return rc;
 }
+
+/* ======================================================================== */
+/* The paper's own agents (Sec. III-C, "Agent Decision and Order            */
+/* Aggregation") on a tick-aggregated book with SplitMix64 draws (Sec.      */
+/* III-F).  Readings where the paper is silent (each marked READING):        */
+/*  - draws: u(gid, s, c) = mix64(seed + 0x9E3779B97F4A7C15 * (gid * 2^35 +   */
+/*    8 s + c)) mod 2^64, i.e. output number gid*2^35 + 8s + c of the         */
+/*    SplitMix64 generator with state `seed` (Steele, Lea, Flood, OOPSLA      */
+/*    2014); gid = market * A + a is the paper's global agent id.  Channel 0: */
+/*    high word = marketable draw, low word = side coin (bit 31); channel 1:  */
+/*    high word = price draw, low word = quantity draw; channel 2 at step 0:  */
+/*    high word = agent class draw.                                          */
+/*  - class: percentile floor(100 w / 2^32) of the class draw; MAKER below    */
+/*    maker_pct, MOMENTUM below maker_pct + mom_pct, NOISE otherwise.         */
+/*  - the clearing takes the step's own orders (Algorithm 1 scans s_BUY and   */
+/*    s_SELL); their unfilled part (the worked example's new_bid = BUY -      */
+/*    traded_buy) replaces the resting book, which feeds the next step's mid. */
+/*  - round(x) = the nearest integer, ties to even (IEEE-754 round to        */
+/*    nearest); a round-half-up rule shifts both maker quotes up by half a    */
+/*    tick whenever the spread is odd, a ratchet that walks the price to the  */
+/*    top of the grid.  Ticks are clamped to [0, L).                           */
+/*  - the first step's previous mid is the opening mid L/2 (integer part).   */
+/* ======================================================================== */
+#define KO_PAPER_NOISE 0
+#define KO_PAPER_MOMENTUM 1
+#define KO_PAPER_MAKER 2
+
+typedef struct {
+  uint64_t seed;
+  int32_t noise_halfwidth;   /* Delta_noise, ticks                            */
+  uint32_t p_mkt_q32;        /* P_mkt * 2^32                                  */
+  int32_t qmax;              /* q_max                                         */
+  int32_t maker_half_spread; /* Delta_maker_half_spread, ticks                */
+  int32_t mom_pct;           /* alpha_mom in percent                          */
+  int32_t maker_pct;         /* alpha_maker in percent                        */
+  int32_t tie_rule;
+  int32_t pad_;
+} ko_paper_params;
+
+typedef struct {
+  int32_t last;    /* last clearing tick                                      */
+  int32_t mid2;    /* twice the mid of the latest step (the next step's mid_{t-1}) */
+  int32_t trades;
+  int32_t last_v;
+  int64_t sum_p;
+  int64_t sum_v;
+  uint64_t hash;
+} ko_paper_market;
+
+/* floor(num / den) for den > 0 */
+static int64_t ko_floor_div(int64_t num, int64_t den) {
+  int64_t q = num / den;
+  if ((num % den) != 0 && num < 0) q -= 1;
+  return q;
+}
+
+/* num / den rounded to the nearest integer, ties to even (den > 0, even) */
+static int64_t ko_round_even(int64_t num, int64_t den) {
+  int64_t q = ko_floor_div(num, den);
+  int64_t r = num - q * den;      /* 0 <= r < den */
+  if (2 * r > den) return q + 1;
+  if (2 * r < den) return q;
+  return (q % 2 != 0) ? q + 1 : q;
+}
+
+uint64_t ko_splitmix64_draw(uint64_t seed, uint64_t gid, uint32_t step, uint32_t channel) {
+  uint64_t counter = gid * (1ull << 35) + (uint64_t)step * 8ull + (uint64_t)channel;
+  return ko_mix64(seed + 0x9E3779B97F4A7C15ull * counter);
+}
+
+int32_t ko_paper_class(const ko_paper_params* P, uint64_t gid) {
+  uint32_t w = (uint32_t)(ko_splitmix64_draw(P->seed, gid, 0, 2) >> 32);
+  int64_t pct = ko_range(w, 100);
+  if (pct < P->maker_pct) return KO_PAPER_MAKER;
+  if (pct < P->maker_pct + P->mom_pct) return KO_PAPER_MOMENTUM;
+  return KO_PAPER_NOISE;
+}
+
+/* Order of agent a (class cls) at step s given the step's mid (mid2 = 2 mid)
+ * and the sign of the mid change ret: side 0 buy / 1 sell, tick, qty. */
+void ko_paper_order(const ko_paper_params* P, int32_t L, uint64_t gid, int32_t a, uint32_t s, int32_t cls,
+                    int32_t mid2, int32_t ret, int32_t* side, int32_t* tick, int32_t* qty) {
+  uint64_t u0 = ko_splitmix64_draw(P->seed, gid, s, 0);
+  uint64_t u1 = ko_splitmix64_draw(P->seed, gid, s, 1);
+  uint32_t w_mkt = (uint32_t)(u0 >> 32), w_coin = (uint32_t)u0;
+  uint32_t w_price = (uint32_t)(u1 >> 32), w_qty = (uint32_t)u1;
+  int32_t sd;
+  int64_t p;
+  if (cls == KO_PAPER_MAKER) {
+    /* buys iff (a + s) mod 2 = 0; bid at round(mid - D), ask at round(mid + D) */
+    sd = (int32_t)(((int64_t)a + (int64_t)s) % 2);
+    int64_t D = P->maker_half_spread;
+    p = ko_round_even((int64_t)mid2 + (sd ? 2 * D : -2 * D), 2);
+  } else {
+    if (cls == KO_PAPER_MOMENTUM && ret != 0)
+      sd = ret > 0 ? 0 : 1;                 /* side = sign of the mid change */
+    else
+      sd = (w_coin >= 0x80000000u) ? 1 : 0; /* buy or sell with equal probability */
+    if (w_mkt < P->p_mkt_q32) {
+      p = sd ? 0 : L - 1;                   /* marketable: the grid boundary */
+    } else if (cls == KO_PAPER_MOMENTUM) {
+      p = ko_round_even((int64_t)mid2 + (sd ? -2 : 2), 2);   /* round(mid + side) */
+    } else {
+      /* round(mid + eta), eta = -D + 2 D w / 2^32: numerator over 2^33 */
+      int64_t D = P->noise_halfwidth;
+      int64_t num = ((int64_t)mid2 - 2 * D) * (1ll << 32) + 4 * D * (int64_t)w_price;
+      p = ko_round_even(num, 1ll << 33);
+    }
+  }
+  *side = sd;
+  *tick = ko_clamp(p, 0, L - 1);
+  *qty = (int32_t)(1 + ko_range(w_qty, P->qmax));
+}
+
+int ko_paper_init(int32_t L, int32_t* bid, int32_t* ask, ko_paper_market* ms) {
+  if (L < 2) return -1;
+  for (int32_t p = 0; p < L; ++p) bid[p] = ask[p] = 0;
+  memset(ms, 0, sizeof(*ms));
+  ms->last = L / 2;
+  ms->mid2 = 2 * (L / 2);
+  return 0;
+}
+
+/* Steps [s0, s0 + n) of global market `market`; trace: 2 int32 per step or NULL. */
+int ko_paper_run(const ko_paper_params* P, uint32_t market, int32_t L, int32_t A, int32_t* bid, int32_t* ask,
+                 ko_paper_market* ms, uint32_t s0, uint32_t n, int32_t* trace) {
+  if (L < 2 || A < 0) return -1;
+  int64_t* buy = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int64_t* sell = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int64_t* dcum = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int64_t* scum = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int64_t* vol = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+  int32_t* cls = (int32_t*)calloc((size_t)(A > 0 ? A : 1), sizeof(int32_t));
+  if (!buy || !sell || !dcum || !scum || !vol || !cls) return -2;
+  for (int32_t a = 0; a < A; ++a) cls[a] = ko_paper_class(P, (uint64_t)market * (uint64_t)A + (uint64_t)a);
+  for (uint32_t j = 0; j < n; ++j) {
+    uint32_t s = s0 + j;
+    /* state retrieval: best bid / ask of the resting book, mid price */
+    int32_t bb = -1, ba = L;
+    for (int32_t p = 0; p < L; ++p)
+      if (bid[p] > 0) bb = p;
+    for (int32_t p = L - 1; p >= 0; --p)
+      if (ask[p] > 0) ba = p;
+    int32_t mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * ms->last;
+    int32_t ret = (mid2 > ms->mid2) - (mid2 < ms->mid2);
+    /* the step's orders */
+    for (int32_t p = 0; p < L; ++p) buy[p] = sell[p] = 0;
+    for (int32_t a = 0; a < A; ++a) {
+      int32_t sd, tk, q;
+      ko_paper_order(P, L, (uint64_t)market * (uint64_t)A + (uint64_t)a, a, s, cls[a], mid2, ret, &sd, &tk, &q);
+      if (sd) sell[tk] += q; else buy[tk] += q;
+    }
+    /* clearing */
+    ko_clear_result cr;
+    ko_clear_book(L, buy, sell, P->tie_rule, dcum, scum, vol, &cr);
+    /* the unfilled part of the step's orders becomes the resting book */
+    for (int32_t p = 0; p < L; ++p) {
+      int64_t nb = buy[p], na = sell[p];
+      if (cr.vstar > 0) {
+        int64_t above_b = p + 1 < L ? dcum[p + 1] : 0;  /* demand strictly above p */
+        int64_t below_s = p > 0 ? scum[p - 1] : 0;      /* supply strictly below p */
+        if (p > cr.p_buy) nb = 0;
+        else if (p == cr.p_buy) nb = buy[p] - (cr.vstar - above_b);
+        if (p < cr.p_sell) na = 0;
+        else if (p == cr.p_sell) na = sell[p] - (cr.vstar - below_s);
+      }
+      if (nb > 0x7FFFFFFF || na > 0x7FFFFFFF) return -3;
+      bid[p] = (int32_t)nb;
+      ask[p] = (int32_t)na;
+    }
+    if (cr.vstar > 0) {
+      ms->last = cr.pstar;
+      ms->trades += 1;
+      ms->sum_p += cr.pstar;
+    }
+    if (cr.vstar > 0x7FFFFFFF) return -3;
+    ms->sum_v += cr.vstar;
+    ms->last_v = (int32_t)cr.vstar;
+    ms->mid2 = mid2;
+    ms->hash = ko_trace_hash_update(ms->hash, s, cr.pstar, (int32_t)cr.vstar);
+    if (trace) {
+      trace[2 * j] = cr.pstar;
+      trace[2 * j + 1] = (int32_t)cr.vstar;
+    }
+  }
+  free(buy); free(sell); free(dcum); free(scum); free(vol); free(cls);
+  return 0;
+}

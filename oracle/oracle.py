@@ -91,6 +91,21 @@ class _Options(ctypes.Structure):
 MLP_IN, MLP_H, MLP_OUT, N_RAW, REC_WORDS = 32, 64, 37, 18, 22
 
 
+class PaperParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("noise_halfwidth", ctypes.c_int32), ("p_mkt_q32", ctypes.c_uint32),
+                ("qmax", ctypes.c_int32), ("maker_half_spread", ctypes.c_int32), ("mom_pct", ctypes.c_int32),
+                ("maker_pct", ctypes.c_int32), ("tie_rule", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class PaperMarket(ctypes.Structure):
+    _fields_ = [("last", ctypes.c_int32), ("mid2", ctypes.c_int32), ("trades", ctypes.c_int32),
+                ("last_v", ctypes.c_int32), ("sum_p", ctypes.c_int64), ("sum_v", ctypes.c_int64),
+                ("hash", ctypes.c_uint64)]
+
+
+PAPER_NOISE, PAPER_MOMENTUM, PAPER_MAKER = 0, 1, 2
+
+
 class _ClearResult(ctypes.Structure):
     _fields_ = [
         ("vstar", ctypes.c_int64),
@@ -141,6 +156,20 @@ def _load():
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double]
             lib.ko_adam_step.restype = None
+            lib.ko_splitmix64_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+            lib.ko_splitmix64_draw.restype = ctypes.c_uint64
+            lib.ko_paper_class.argtypes = [P(PaperParams), ctypes.c_uint64]
+            lib.ko_paper_class.restype = ctypes.c_int32
+            lib.ko_paper_order.argtypes = [P(PaperParams), ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
+                                           ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]
+            lib.ko_paper_order.restype = None
+            lib.ko_paper_init.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, P(PaperMarket)]
+            lib.ko_paper_init.restype = ctypes.c_int
+            lib.ko_paper_run.argtypes = [P(PaperParams), ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p, P(PaperMarket), ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_void_p]
+            lib.ko_paper_run.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -397,3 +426,68 @@ def simulate(params: dict, m: int, L: int, A: int, steps: int, replay=None, mlp_
     mk = init_market(params, m, L, A)
     tp, tv = run_market(params, mk, 0, steps, replay=replay, mlp_w=mlp_w)
     return mk, tp, tv
+
+
+# ---------------------------------------------------------------------------
+# The paper's own agents on a tick-aggregated book (Sec. III-C, III-F)
+# ---------------------------------------------------------------------------
+def make_paper_params(p: dict) -> PaperParams:
+    return PaperParams(int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(p["noise_halfwidth"]), int(p["p_mkt_q32"]),
+                       int(p["qmax"]), int(p["maker_half_spread"]), int(p["mom_pct"]), int(p["maker_pct"]),
+                       int(p.get("tie_rule", 0)), 0)
+
+
+def splitmix64_draw(seed: int, gid: int, step: int, channel: int) -> int:
+    """Output number gid*2^35 + 8*step + channel of SplitMix64 with state ``seed``."""
+    return int(_load().ko_splitmix64_draw(seed & 0xFFFFFFFFFFFFFFFF, gid & 0xFFFFFFFFFFFFFFFF, step, channel))
+
+
+def paper_class(params: dict, gid: int) -> int:
+    P = make_paper_params(params)
+    return int(_load().ko_paper_class(ctypes.byref(P), gid))
+
+
+def paper_order(params: dict, L: int, gid: int, a: int, s: int, cls: int, mid2: int, ret: int):
+    """(side, tick, qty) of one agent's order at step s (side 0 buy, 1 sell)."""
+    P = make_paper_params(params)
+    sd, tk, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _load().ko_paper_order(ctypes.byref(P), L, gid, a, s, cls, mid2, ret, ctypes.byref(sd), ctypes.byref(tk),
+                           ctypes.byref(q))
+    return int(sd.value), int(tk.value), int(q.value)
+
+
+@dataclass
+class PaperBook:
+    market: int
+    L: int
+    A: int
+    bid: np.ndarray
+    ask: np.ndarray
+    sc: PaperMarket = field(default_factory=PaperMarket)
+
+    def scalars(self) -> dict:
+        return {k: int(getattr(self.sc, k)) for k in ("last", "mid2", "trades", "last_v", "sum_p", "sum_v", "hash")}
+
+
+def paper_init(market: int, L: int, A: int) -> PaperBook:
+    bk = PaperBook(market, L, A, np.zeros(L, np.int32), np.zeros(L, np.int32))
+    if _load().ko_paper_init(L, _ptr(bk.bid), _ptr(bk.ask), ctypes.byref(bk.sc)) != 0:
+        raise ValueError("ko_paper_init failed")
+    return bk
+
+
+def paper_run(params: dict, bk: PaperBook, s0: int, n: int, want_trace: bool = True):
+    """Advance ``bk`` in place over steps [s0, s0+n); returns (trace_p, trace_v) or None."""
+    P = make_paper_params(params)
+    tr = np.zeros((max(n, 1), 2), np.int32)
+    rc = _load().ko_paper_run(ctypes.byref(P), bk.market, bk.L, bk.A, _ptr(bk.bid), _ptr(bk.ask),
+                              ctypes.byref(bk.sc), s0, n, _ptr(tr) if want_trace else None)
+    if rc != 0:
+        raise ValueError(f"ko_paper_run failed: {rc}")
+    return (tr[:n, 0].copy(), tr[:n, 1].copy()) if want_trace else None
+
+
+def paper_simulate(params: dict, market: int, L: int, A: int, steps: int):
+    bk = paper_init(market, L, A)
+    tp, tv = paper_run(params, bk, 0, steps)
+    return bk, tp, tv

@@ -35,6 +35,21 @@ MUTANTS = {
     "mlp_mse_factor": ("dz[KO_OUT - 1] = 2.0 * e;", "dz[KO_OUT - 1] = e;"),
     "mlp_sample_le": ("if (u < c) return i;", "if (u <= c) return i;"),
     "mlp_qty_rounding": ("double q = floor(exp(z[KO_OUT - 1]) + 0.5);", "double q = floor(exp(z[KO_OUT - 1]));"),
+    # the paper-agent mode
+    "paper_maker_parity": ("sd = (int32_t)(((int64_t)a + (int64_t)s) % 2);",
+                           "sd = (int32_t)(((int64_t)a + (int64_t)s + 1) % 2);"),
+    "paper_round_half_up": ("return (q % 2 != 0) ? q + 1 : q;", "return q + 1;"),
+    "paper_marketable_sides": ("p = sd ? 0 : L - 1;", "p = sd ? L - 1 : 0;"),
+    "paper_momentum_reversed": ("sd = ret > 0 ? 0 : 1;", "sd = ret > 0 ? 1 : 0;"),
+    "paper_mid_fallback": ("int32_t mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * ms->last;",
+                           "int32_t mid2 = (bb >= 0 && ba < L) ? bb + ba : ms->mid2;"),
+    "paper_marginal_residual": ("else if (p == cr.p_buy) nb = buy[p] - (cr.vstar - above_b);",
+                                "else if (p == cr.p_buy) nb = buy[p] - cr.vstar;"),
+    "paper_counter_layout": ("(uint64_t)step * 8ull", "(uint64_t)step * 4ull"),
+    "paper_class_threshold": ("if (pct < P->maker_pct) return KO_PAPER_MAKER;",
+                              "if (pct <= P->maker_pct) return KO_PAPER_MAKER;"),
+    "paper_noise_width": ("int64_t num = ((int64_t)mid2 - 2 * D) * (1ll << 32) + 4 * D * (int64_t)w_price;",
+                          "int64_t num = ((int64_t)mid2 - 2 * D) * (1ll << 32) + 2 * D * (int64_t)w_price;"),
 }
 
 
@@ -51,6 +66,7 @@ def test_pins_catch_mutant(name):
         env = dict(os.environ, KS_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_mlp_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_mlp_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_paper_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
