@@ -255,6 +255,87 @@ ks_status ks_batch_variants(int32_t cta_threads, int32_t* pairs, int32_t capacit
 /* Frees the host handle.  The workspace stays the caller's. */
 ks_status ks_destroy(ks_ensemble* e);
 
+/*
+ * The paper's own agent model on a tick-aggregated book (Sec. III-C, "Agent
+ * Decision and Order Aggregation"; Algorithm 1).  A second ensemble type: no
+ * agent accounts and no cancellation.  Every step, every agent submits one
+ * order; the step's orders clear (Eq. 1-2, ties as tie_rule, allocation in
+ * price priority as above); their unfilled part is the resting book, whose
+ * best bid bb and best ask ba give the next step's mid price (state
+ * retrieval, Sec. III-C: mid = (bb + ba) / 2 when both exist, else the last
+ * clearing tick).  The opening book is empty and the opening price L/2.
+ * Agents (class from the channel-2 draw of step 0: MAKER if its percentile
+ * floor(100 w / 2^32) < maker_pct, MOMENTUM if < maker_pct + mom_pct, else
+ * NOISE):
+ *  - NOISE: buys or sells with probability 1/2; with probability P_mkt a
+ *    marketable order at tick L-1 (buy) or 0 (sell), else at round(mid + eta),
+ *    eta uniform on [-noise_halfwidth, noise_halfwidth];
+ *  - MOMENTUM: side = sign of the mid change since the previous step (the
+ *    coin when zero; the first step's previous mid is L/2); marketable with
+ *    probability P_mkt, else at round(mid + 1) (buy) / round(mid - 1) (sell);
+ *  - MAKER: buys iff (a + s) mod 2 = 0, at round(mid - maker_half_spread),
+ *    sells at round(mid + maker_half_spread); never marketable.
+ * Quantity 1 + floor(qmax u).  round() is to the nearest integer with ties to
+ * even; ticks are clamped to [0, L).
+ * Draws (SplitMix64, Sec. III-F): u(gid, s, c) = mix64(seed +
+ * 0x9E3779B97F4A7C15 * (gid * 2^35 + 8 s + c)), the output number
+ * gid * 2^35 + 8 s + c of the generator with state `seed`, gid = (market_base
+ * + m) * A + a.  Channel 0: high word = marketable draw (marketable iff below
+ * p_mkt_q32), low word = side coin (sell iff >= 2^31); channel 1: high word =
+ * price draw w (eta = -D + 2 D w / 2^32), low word = quantity draw (u =
+ * w / 2^32); channel 2 at step 0: high word = class draw.
+ */
+typedef struct ks_paper_config {
+  uint32_t n_markets;          /* M >= 1                                          */
+  uint32_t market_base;        /* global index of market 0 (draws use it)         */
+  int32_t L;                   /* ticks, 2..KS_MAX_TICKS                          */
+  int32_t A;                   /* agents per market, 0..KS_MAX_AGENTS             */
+  uint64_t seed;               /* SplitMix64 generator state                     */
+  int32_t noise_halfwidth;     /* Delta_noise in ticks, 0..L                      */
+  uint32_t p_mkt_q32;          /* P_mkt * 2^32                                    */
+  int32_t qmax;                /* q_max, 1..KS_MAX_QTY                            */
+  int32_t maker_half_spread;   /* Delta_maker_half_spread in ticks, 0..L          */
+  uint32_t mom_pct;            /* alpha_mom in percent                            */
+  uint32_t maker_pct;          /* alpha_maker in percent, mom_pct + maker_pct <= 100 */
+  int32_t tie_rule;            /* ks_tie_rule                                     */
+  uint32_t trace_markets;      /* markets 0..trace_markets-1 record (p*, V*) per step */
+  uint32_t trace_steps;        /* trace capacity in steps                         */
+  int32_t pad_;
+} ks_paper_config;
+
+typedef struct ks_paper_ensemble ks_paper_ensemble;
+
+/* State of a paper-agent ensemble (caller-owned buffers, host or device; NULL
+ * fields are skipped). */
+typedef struct ks_paper_state_view {
+  int32_t* bid;          /* [M*L] resting buy quantity per tick: bid[m*L + p]  */
+  int32_t* ask;          /* [M*L] resting sell quantity per tick               */
+  int32_t* last_tick;    /* [M] last clearing tick                             */
+  int32_t* mid2;         /* [M] twice the mid price of the latest step         */
+  int32_t* trades;       /* [M] steps with V* > 0                              */
+  int32_t* last_volume;  /* [M] V* of the latest step                          */
+  int64_t* sum_price;    /* [M] sum of p* over trading steps                   */
+  int64_t* sum_volume;   /* [M] sum of V* over steps                           */
+  uint64_t* trace_hash;  /* [M] as ks_state_view::trace_hash                   */
+  uint64_t* step;        /* [1] absolute step counter                          */
+  int32_t* trace;        /* [trace_markets*trace_steps*2] (p*, V*) per market and step */
+} ks_paper_state_view;
+
+/* Workspace bytes, creation (init kernel queued on `stream`), steps [s, s+n)
+ * in one persistent launch (asynchronous, capturable), state copies (then
+ * `stream` is synchronised), launch shape (threads 128..1024, agents per
+ * thread 1..16, threads * agents_per_thread >= A), deadline wait and error
+ * word check, handle release: as the functions above of the same name. */
+ks_status ks_paper_workspace_size(const ks_paper_config* cfg, size_t* bytes);
+ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws_bytes, void* stream,
+                          ks_paper_ensemble** out);
+ks_status ks_paper_step_n(ks_paper_ensemble* e, uint32_t n_steps, void* stream);
+ks_status ks_paper_read_state(ks_paper_ensemble* e, const ks_paper_state_view* dst, void* stream);
+ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread);
+ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread);
+ks_status ks_paper_sync(ks_paper_ensemble* e, void* stream, uint32_t timeout_ms);
+ks_status ks_paper_destroy(ks_paper_ensemble* e);
+
 const char* ks_status_string(ks_status s);
 const char* ks_last_error(void);
 

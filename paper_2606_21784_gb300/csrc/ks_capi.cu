@@ -128,6 +128,11 @@ using namespace ks;
 // ---------------------------------------------------------------------------
 static thread_local char g_last_error[512] = "";
 
+namespace ks {
+// Error text for ks_last_error from the other translation units of the library.
+void internal_set_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace ks
+
 static ks_status cuda_fail(cudaError_t e, const char* what) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
   return KS_ERR_CUDA;

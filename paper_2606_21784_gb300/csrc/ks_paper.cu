@@ -1,0 +1,714 @@
+// ks_paper.cu -- the paper's own agent model (Sec. III-C NOISE / MOMENTUM /
+// MAKER agents around the mid price, SplitMix64 draws of Sec. III-F) on a
+// tick-aggregated book, as a persistent kernel and its C ABI (ks_paper_*).
+//
+// One CTA runs one market at a time for all n steps of a call, markets dealt
+// round-robin.  Thread t owns agents [t*AK, t*AK+AK) (their classes packed
+// in one register) and ticks [t*LT, t*LT+LT) of the book in shared memory
+// (BUY[p] at word 2p, SELL[p] at 2p+1).  Step s, between four barriers:
+//   orders    every agent draws two SplitMix64 words and adds its order to the
+//             book with a shared reduction                   (Alg. 1, Phase 3)
+//   B1..B3    suffix / prefix scans by warp shuffles, lowest / highest
+//             maximiser of min(D, S) by redux.sync and shared atomicMax
+//                                                            (Eq. 1-2, Phase 4)
+//   residual  tick owners compute the unfilled part of the step's orders (the
+//             resting book), fold its best bid / best ask into shared keys for
+//             the next step's mid price, and clear their ticks; at the last
+//             step of the call they write the resting book out  (Phase 5)
+//   B5        next step's mid visible, book empty
+// Global memory is read once and written once per market and call.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <thread>
+
+#include "kineticsim.h"
+#include "ks_market.cuh"
+
+namespace ks {
+
+void internal_set_error(const char* msg);
+
+constexpr int PAPER_NOISE = 0;
+constexpr int PAPER_MOMENTUM = 1;
+constexpr int PAPER_MAKER = 2;
+constexpr int PMI32 = 8;  // last, mid2, trades, last_v
+constexpr int PMI64 = 4;  // sum_p, sum_v, hash
+
+struct PaperParams {
+  uint32_t M, market_base;
+  int32_t L, A;
+  uint64_t seed;
+  int32_t noise2;     // 2 * noise_halfwidth
+  uint32_t eta4;      // 4 * noise_halfwidth
+  uint32_t p_mkt;
+  uint32_t qmax;
+  int32_t maker2;     // 2 * maker_half_spread
+  uint32_t mom_pct, maker_pct;
+  int32_t tie_rule;
+  uint32_t trace_markets, trace_steps;
+  int32_t* bid;       // [M][L]
+  int32_t* ask;       // [M][L]
+  int32_t* mi32;      // [M][PMI32]
+  int64_t* mi64;      // [M][PMI64]
+  int32_t* trace;     // [trace_markets][trace_steps][2]
+  uint32_t* err;
+  uint64_t* step;
+};
+
+// ---- SplitMix64 (Steele, Lea, Flood, OOPSLA 2014; mixer as printed in Sec. III-F) ----
+constexpr uint64_t SM64_GAMMA = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t SM64_GID = SM64_GAMMA << 35;  // counter step of one agent id (gid * 2^35)
+
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// round(x / 2^33) of x = hi * 2^32 + lo (hi signed) to the nearest integer,
+// ties to even: the quotient is hi >> 1 (floor) and the remainder
+// (hi & 1) * 2^32 + lo is compared with half the divisor, 2^32.
+__device__ __forceinline__ int round_even_2p33(int32_t hi, uint32_t lo) {
+  const int q = hi >> 1;
+  const bool up = (hi & 1) && (lo != 0u || (q & 1));
+  return q + (up ? 1 : 0);
+}
+
+// Shared memory of one market.
+struct PaperSmem {
+  int32_t* book;                 // 2 * book_len(L) words
+  unsigned long long* kx;        // [2][4] argmax keys per parity
+  int32_t* bbk;                  // [2][2] best bid (max) / best ask (min) of the resting book per parity
+  int32_t* wD;                   // [32]
+  int32_t* wS;                   // [32]
+  int32_t* rem;                  // [2]
+};
+
+__host__ __device__ inline size_t paper_smem_bytes(int L) {
+  return (size_t)4 * 2 * book_len(L) + 8 * 8 + 4 * 4 + 4 * 64 + 16;
+}
+
+__device__ __forceinline__ PaperSmem paper_carve(unsigned char* raw, int L) {
+  PaperSmem s;
+  s.book = reinterpret_cast<int32_t*>(raw);
+  s.kx = reinterpret_cast<unsigned long long*>(raw + (size_t)4 * 2 * book_len(L));
+  s.bbk = reinterpret_cast<int32_t*>(s.kx + 8);
+  s.wD = s.bbk + 4;
+  s.wS = s.wD + 32;
+  s.rem = s.wS + 32;
+  return s;
+}
+
+// Local best bid (highest tick with resting buy quantity) and best ask
+// (lowest tick with resting sell quantity) folded into the shared keys.
+__device__ __forceinline__ void fold_best(int32_t* keys, int bb, int ba) {
+  const int wbb = (int)__reduce_max_sync(0xffffffffu, (unsigned)(bb + 1)) - 1;
+  const int wba = (int)__reduce_min_sync(0xffffffffu, (unsigned)ba);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(keys + 0, wbb);
+    atomicMin(keys + 1, wba);
+  }
+}
+
+template <int NT, int AK, int LTC>
+__device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, uint32_t s0, uint32_t n_steps,
+                                             const PaperSmem& sm) {
+  const int t = (int)threadIdx.x;
+  const int lane = t & 31;
+  const int wid = t >> 5;
+  const int L = P.L, A = P.A;
+  const int LT = (L + NT - 1) / NT;
+  const int p0 = t * LT;
+  const bool mine = p0 < L;
+  int32_t* book = sm.book;
+  const uint32_t book_s = (uint32_t)__cvta_generic_to_shared(book);
+  const size_t moff = (size_t)m * (size_t)L;
+
+  // ---- the resting book's best bid / ask give the first step's mid --------------------
+  if (t < 4) sm.bbk[t] = (t & 1) ? L : -1;  // both parities: best bid -1, best ask L
+  for (int i = t; i < 2 * book_len(L); i += NT) book[i] = 0;
+  if (t < 8) sm.kx[t] = 0ull;
+  __syncthreads();
+  {
+    int bb = -1, ba = L;
+    for (int i = 0; i < LT; ++i) {
+      const int p = p0 + i;
+      if (p < L) {
+        if (P.bid[moff + p] > 0) bb = p;
+        if (P.ask[moff + p] > 0 && ba == L) ba = p;
+      }
+    }
+    fold_best(sm.bbk, bb, ba);
+  }
+  const int32_t* mi = P.mi32 + (size_t)m * PMI32;
+  int last = mi[0];
+  int pmid2 = mi[1];
+  int trades = mi[2];
+  int lastv = mi[3];
+  const int64_t* m64 = P.mi64 + (size_t)m * PMI64;
+  int64_t sump = m64[0], sumv = m64[1];
+  uint64_t hash = (uint64_t)m64[2];
+
+  // ---- agent classes (channel 2 of step 0), two bits per agent ----------------------------
+  const uint64_t gid0 = (uint64_t)(P.market_base + m) * (uint64_t)A + (uint64_t)(t * AK);
+  const uint64_t abase = P.seed + SM64_GID * gid0;  // + gamma * (8 s + c) + SM64_GID * k
+  uint32_t cls = 0;
+#pragma unroll
+  for (int k = 0; k < AK; ++k) {
+    const uint32_t w = (uint32_t)(sm64_mix(abase + SM64_GID * (uint64_t)k + 2ull * SM64_GAMMA) >> 32);
+    const uint32_t pct = __umulhi(w, 100u);
+    const uint32_t c = pct < P.maker_pct ? PAPER_MAKER : (pct < P.maker_pct + P.mom_pct ? PAPER_MOMENTUM : PAPER_NOISE);
+    cls |= c << (2 * k);
+  }
+  const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
+  const bool traced = m < P.trace_markets;
+  __syncthreads();
+
+  for (uint32_t j = 0; j < n_steps; ++j) {
+    const uint32_t s = s0 + j;
+    const int32_t* keys = sm.bbk + 2 * (j & 1);
+    const int bb = keys[0], ba = keys[1];
+    const int mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * last;
+    const int ret = (mid2 > pmid2) - (mid2 < pmid2);
+
+    // ---- orders of step s ---------------------------------------------------------------
+    const uint64_t sbase = abase + SM64_GAMMA * (8ull * (uint64_t)s);
+#pragma unroll
+    for (int k = 0; k < AK; ++k) {
+      const int a = t * AK + k;
+      const uint64_t c0 = sbase + SM64_GID * (uint64_t)k;
+      const uint64_t u0 = sm64_mix(c0);
+      const uint64_t u1 = sm64_mix(c0 + SM64_GAMMA);
+      const uint32_t w_mkt = (uint32_t)(u0 >> 32), w_coin = (uint32_t)u0;
+      const uint32_t w_price = (uint32_t)(u1 >> 32), w_qty = (uint32_t)u1;
+      const uint32_t c = (cls >> (2 * k)) & 3u;
+      const bool maker = c == PAPER_MAKER;
+      const bool mom = c == PAPER_MOMENTUM;
+      const uint32_t coin = w_coin >> 31;
+      const uint32_t sell = maker ? ((uint32_t)a + s) & 1u : ((mom && ret != 0) ? (uint32_t)(ret < 0) : coin);
+      const bool mkt = !maker && w_mkt < P.p_mkt;
+      // round(mid + eta) (noise), round(mid +/- 1) (momentum), round(mid -/+ D) (maker):
+      // the value times 2^33 is base2 * 2^32 + scale * w
+      const int base2 = maker ? mid2 + (sell ? P.maker2 : -P.maker2)
+                              : (mom ? mid2 + (sell ? -2 : 2) : mid2 - P.noise2);
+      const uint32_t scale = (maker || mom) ? 0u : P.eta4;
+      const uint64_t prod = (uint64_t)scale * (uint64_t)w_price;
+      const int rounded = round_even_2p33(base2 + (int32_t)(prod >> 32), (uint32_t)prod);
+      const int tick = mkt ? (sell ? 0 : L - 1) : min(max(rounded, 0), L - 1);
+      const int q = 1 + (int)__umulhi(w_qty, P.qmax);
+      red_add_if(book_s + 4u * (uint32_t)(2 * tick + (int)sell), q, a < A);
+    }
+    __syncthreads();  // B1: the step's orders are in the book
+
+    // ---- clearing (Eq. 1-2) ---------------------------------------------------------------
+    constexpr int R = LTC > 0 ? LTC : 1;
+    int bv[R], sv[R];
+    int sumB = 0, sumS = 0;
+    if constexpr (LTC > 0) {
+      if (mine) {
+        ld_pairs<LTC>(book + 2 * p0, bv, sv);
+      } else {
+#pragma unroll
+        for (int i = 0; i < LTC; ++i) bv[i] = sv[i] = 0;
+      }
+#pragma unroll
+      for (int i = 0; i < LTC; ++i) {
+        sumB += bv[i];
+        sumS += sv[i];
+      }
+    } else {
+      for (int i = 0; i < LT; ++i)
+        if (p0 + i < L) {
+          sumB += book[2 * (p0 + i)];
+          sumS += book[2 * (p0 + i) + 1];
+        }
+    }
+    int sufB = sumB, preS = sumS;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int vb = __shfl_down_sync(0xffffffffu, sufB, d);
+      const int vs = __shfl_up_sync(0xffffffffu, preS, d);
+      if (lane + d < 32) sufB += vb;
+      if (lane >= d) preS += vs;
+    }
+    if (lane == 0) sm.wD[wid] = sufB;
+    if (lane == 31) sm.wS[wid] = preS;
+    unsigned long long* kx = sm.kx + 4 * (j & 1);
+    __syncthreads();  // B2
+    const int offD = (int)__reduce_add_sync(0xffffffffu, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
+    const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
+    const int D0 = offD + sufB;
+    const int Sb0 = offS + preS - sumS;
+    {
+      int D = D0, Sb = Sb0;
+      int bestV = -1, lo = 4095, hi = 0;
+      unsigned long long kT = 0ull;
+      auto visit = [&](int p, int b, int sq) {
+        const int S = Sb + sq;
+        const int v = min(D, S);
+        if (v > bestV) { bestV = v; lo = p; }
+        if (v >= bestV) hi = p;
+        if (tie1) {
+          const int imb = min(abs(D - S), (1 << 22) - 1);
+          const unsigned long long tk = ((unsigned long long)(uint32_t)v << 34) |
+                                        ((unsigned long long)((1 << 22) - 1 - imb) << 12) | (4095u - p);
+          kT = tk > kT ? tk : kT;
+        }
+        D -= b;
+        Sb = S;
+      };
+      if constexpr (LTC > 0) {
+        if (mine) {
+#pragma unroll
+          for (int i = 0; i < LTC; ++i) visit(p0 + i, bv[i], sv[i]);
+        }
+      } else {
+        for (int i = 0; i < LT; ++i)
+          if (p0 + i < L) visit(p0 + i, book[2 * (p0 + i)], book[2 * (p0 + i) + 1]);
+      }
+      const int vw = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(bestV, 0));
+      const bool top = bestV == vw;
+      const uint32_t low = __reduce_min_sync(0xffffffffu, top ? (unsigned)lo : 4095u);
+      const uint32_t high = __reduce_max_sync(0xffffffffu, top ? (unsigned)hi : 0u);
+      if (tie1) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, kT, d);
+          kT = o > kT ? o : kT;
+        }
+      }
+      if (lane == 0) {
+        atomicMax(kx + 0, ((unsigned long long)(uint32_t)vw << 12) | (4095u - low));
+        atomicMax(kx + 1, ((unsigned long long)(uint32_t)vw << 12) | high);
+        if (tie1) atomicMax(kx + 2, kT);
+      }
+    }
+    __syncthreads();  // B3
+    const unsigned long long kLo = kx[0], kHi = kx[1];
+    const int vstar = (int)(kLo >> 12);
+    const int p_lo = 4095 - (int)(kLo & 4095u);
+    const int p_hi = (int)(kHi & 4095u);
+    const int pstar = tie1 ? 4095 - (int)(kx[2] & 4095u) : p_lo;
+    const bool trade = vstar > 0;
+    if (t < 4) sm.kx[4 * ((j + 1) & 1) + t] = 0ull;  // the other parity's keys for the next step
+    int32_t* nkeys = sm.bbk + 2 * ((j + 1) & 1);       // (reset by the previous step, see below)
+    const bool final_step = j + 1 == n_steps;
+
+    // ---- resting book: the unfilled part of the step's orders (Phase 5) --------------------
+    {
+      int D = D0, Sb = Sb0;
+      int nbb = -1, nba = L;
+      auto rest = [&](int p, int b, int sq) {
+        int nb = b, ns = sq;
+        if (trade) {
+          const int rb = vstar - (D - b);  // units filled at the marginal buy tick
+          const int rs = vstar - Sb;       // units filled at the marginal sell tick
+          nb = p > p_hi ? 0 : (p == p_hi ? b - rb : b);
+          ns = p < p_lo ? 0 : (p == p_lo ? sq - rs : sq);
+        }
+        D -= b;
+        Sb += sq;
+        if (nb > 0) nbb = p;
+        if (ns > 0 && nba == L) nba = p;
+        if (final_step) {
+          P.bid[moff + p] = nb;
+          P.ask[moff + p] = ns;
+        }
+      };
+      if constexpr (LTC > 0) {
+        if (mine) {
+          int z[R];
+#pragma unroll
+          for (int i = 0; i < LTC; ++i) {
+            rest(p0 + i, bv[i], sv[i]);
+            z[i] = 0;
+          }
+          st_pairs<LTC>(book + 2 * p0, z, z);
+        }
+      } else {
+        for (int i = 0; i < LT; ++i) {
+          const int p = p0 + i;
+          if (p < L) {
+            rest(p, book[2 * p], book[2 * p + 1]);
+            book[2 * p] = 0;
+            book[2 * p + 1] = 0;
+          }
+        }
+      }
+      fold_best(nkeys, nbb, nba);
+    }
+    if (t == 0) {
+      // keys of the step after next start empty (this step read them already)
+      sm.bbk[2 * (j & 1)] = -1;
+      sm.bbk[2 * (j & 1) + 1] = L;
+    }
+    // ---- market scalars ---------------------------------------------------------------------
+    if (trade) last = pstar;
+    pmid2 = mid2;
+    if (t == 0) {
+      const int pt = trade ? pstar : -1;
+      if (trade) {
+        sump += pstar;
+        trades += 1;
+      }
+      sumv += vstar;
+      lastv = vstar;
+      hash = trace_mix(hash, s, pt, vstar);
+      if (traced && s < P.trace_steps) {
+        int32_t* tr = P.trace + ((size_t)m * P.trace_steps + s) * 2;
+        tr[0] = pt;
+        tr[1] = vstar;
+      }
+    }
+    __syncthreads();  // B5: next mid keys complete, book empty
+  }
+  if (t == 0) {
+    int32_t* mo = P.mi32 + (size_t)m * PMI32;
+    mo[0] = last;
+    mo[1] = pmid2;
+    mo[2] = trades;
+    mo[3] = lastv;
+    int64_t* mo64 = P.mi64 + (size_t)m * PMI64;
+    mo64[0] = sump;
+    mo64[1] = sumv;
+    mo64[2] = (int64_t)hash;
+  }
+  __syncthreads();  // shared memory is reused by the CTA's next market
+}
+
+template <int NT, int AK>
+__global__ void __launch_bounds__(NT) paper_kernel(PaperParams P, uint32_t n_steps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const uint32_t s0 = (uint32_t)(*P.step);
+  const PaperSmem sm = paper_carve(smem_raw, P.L);
+  const int LT = (P.L + NT - 1) / NT;
+  const int LTsel = ((LT == 1 || LT == 2 || LT == 4 || LT == 8) && (P.L % LT == 0)) ? LT : 0;
+  if (P.A > NT * AK) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(P.err, ERR_SHAPE);
+    return;
+  }
+  for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
+    switch (LTsel) {
+      case 1: paper_market<NT, AK, 1>(P, m, s0, n_steps, sm); break;
+      case 2: paper_market<NT, AK, 2>(P, m, s0, n_steps, sm); break;
+      case 4: paper_market<NT, AK, 4>(P, m, s0, n_steps, sm); break;
+      case 8: paper_market<NT, AK, 8>(P, m, s0, n_steps, sm); break;
+      default: paper_market<NT, AK, 0>(P, m, s0, n_steps, sm); break;
+    }
+  }
+}
+
+__global__ void paper_init_kernel(PaperParams P) {
+  for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
+    for (int p = threadIdx.x; p < P.L; p += blockDim.x) {
+      P.bid[(size_t)m * P.L + p] = 0;
+      P.ask[(size_t)m * P.L + p] = 0;
+    }
+    if (threadIdx.x == 0) {
+      int32_t* mi = P.mi32 + (size_t)m * PMI32;
+      mi[0] = P.L / 2;
+      mi[1] = 2 * (P.L / 2);
+      for (int i = 2; i < PMI32; ++i) mi[i] = 0;
+      int64_t* m64 = P.mi64 + (size_t)m * PMI64;
+      for (int i = 0; i < PMI64; ++i) m64[i] = 0;
+    }
+  }
+}
+
+__global__ void paper_step_bump(uint64_t* step, uint32_t n) { *step += n; }
+
+using PaperLaunchFn = void (*)(const PaperParams&, uint32_t, int, size_t, cudaStream_t);
+template <int NT, int AK>
+void paper_launch(const PaperParams& p, uint32_t n, int grid, size_t smem, cudaStream_t st) {
+  paper_kernel<NT, AK><<<grid, NT, smem, st>>>(p, n);
+}
+
+struct PaperVariant {
+  int threads, ak;
+  PaperLaunchFn launch;
+  const void* kernel;
+};
+#define KS_PV(NT, AK) PaperVariant{NT, AK, &paper_launch<NT, AK>, (const void*)&paper_kernel<NT, AK>}
+static const PaperVariant kPaperVariants[] = {KS_PV(128, 1),  KS_PV(128, 2),  KS_PV(128, 4),  KS_PV(128, 8),
+                                              KS_PV(128, 16), KS_PV(256, 1),  KS_PV(256, 2),  KS_PV(256, 4),
+                                              KS_PV(256, 8),  KS_PV(256, 16), KS_PV(512, 16), KS_PV(1024, 16)};
+#undef KS_PV
+
+}  // namespace ks
+
+using namespace ks;
+
+struct ks_paper_ensemble {
+  PaperParams p;
+  uint32_t M;
+  int L, A;
+  const PaperVariant* var;
+  int grid;
+  size_t smem;
+  int num_sms;
+  int device;
+};
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct PaperLayout {
+  size_t bid, ask, mi32, mi64, trace, ctrl, total;
+};
+
+PaperLayout paper_layout(const ks_paper_config* c) {
+  PaperLayout l;
+  size_t o = 0;
+  const size_t ML = (size_t)c->n_markets * (size_t)c->L;
+  l.bid = o; o = al256(o + ML * 4);
+  l.ask = o; o = al256(o + ML * 4);
+  l.mi32 = o; o = al256(o + (size_t)c->n_markets * PMI32 * 4);
+  l.mi64 = o; o = al256(o + (size_t)c->n_markets * PMI64 * 8);
+  l.trace = o; o = al256(o + (size_t)c->trace_markets * c->trace_steps * 2 * 4);
+  l.ctrl = o; o = al256(o + 64);  // err (u32) at +0, step (u64) at +8
+  l.total = o;
+  return l;
+}
+
+ks_status fail(ks_status s, const char* msg) {
+  internal_set_error(msg);
+  return s;
+}
+
+ks_status cuda_status(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  internal_set_error(buf);
+  return KS_ERR_CUDA;
+}
+
+#define KSP_CUDA(call)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_status(e_, #call);  \
+  } while (0)
+
+ks_status validate(const ks_paper_config* c) {
+  if (!c) return fail(KS_ERR_INVALID_ARG, "config is NULL");
+  if (c->n_markets == 0) return fail(KS_ERR_INVALID_ARG, "n_markets must be >= 1");
+  if (c->n_markets > (1u << 26)) return fail(KS_ERR_UNSUPPORTED, "n_markets above 2^26");
+  if ((uint64_t)c->market_base + c->n_markets > 0xFFFFFFFFull)
+    return fail(KS_ERR_INVALID_ARG, "market_base + n_markets above 2^32");
+  if (c->L < 2 || c->L > KS_MAX_TICKS) return fail(KS_ERR_UNSUPPORTED, "L outside [2, KS_MAX_TICKS]");
+  if (c->A < 0 || c->A > KS_MAX_AGENTS) return fail(KS_ERR_UNSUPPORTED, "A outside [0, KS_MAX_AGENTS]");
+  if (c->qmax < 1 || c->qmax > KS_MAX_QTY) return fail(KS_ERR_INVALID_ARG, "qmax outside [1, KS_MAX_QTY]");
+  if (c->noise_halfwidth < 0 || c->noise_halfwidth > c->L)
+    return fail(KS_ERR_INVALID_ARG, "noise_halfwidth outside [0, L]");
+  if (c->maker_half_spread < 0 || c->maker_half_spread > c->L)
+    return fail(KS_ERR_INVALID_ARG, "maker_half_spread outside [0, L]");
+  if (c->mom_pct + c->maker_pct > 100u) return fail(KS_ERR_INVALID_ARG, "mom_pct + maker_pct above 100");
+  if (c->tie_rule != KS_TIE_LOWEST_TICK && c->tie_rule != KS_TIE_MIN_IMBALANCE)
+    return fail(KS_ERR_INVALID_ARG, "unknown tie_rule");
+  // per-step volume: A orders of at most KS_MAX_QTY must fit int32 (and the 22-bit imbalance key)
+  if ((int64_t)c->A * c->qmax >= (1ll << 31)) return fail(KS_ERR_UNSUPPORTED, "A * qmax above 2^31");
+  return KS_OK;
+}
+
+ks_status apply_launch(ks_paper_ensemble* e, int threads, int ak) {
+  const PaperVariant* v = nullptr;
+  for (const auto& x : kPaperVariants)
+    if (x.threads == threads && x.ak == ak) v = &x;
+  if (!v) return fail(KS_ERR_INVALID_ARG, "no paper-agent kernel for this (threads, agents_per_thread)");
+  if ((int64_t)threads * ak < e->A) return fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below A");
+  const size_t smem = paper_smem_bytes(e->L);
+  KSP_CUDA(cudaFuncSetAttribute(v->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  KSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v->kernel, threads, smem));
+  if (occ < 1) return fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+  e->var = v;
+  e->smem = smem;
+  e->grid = (int)std::min<int64_t>((int64_t)e->M, (int64_t)occ * e->num_sms);
+  return KS_OK;
+}
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+ks_status ks_paper_workspace_size(const ks_paper_config* cfg, size_t* bytes) {
+  if (!bytes) return fail(KS_ERR_INVALID_ARG, "bytes is NULL");
+  ks_status s = validate(cfg);
+  if (s != KS_OK) return s;
+  *bytes = paper_layout(cfg).total;
+  return KS_OK;
+}
+
+ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws_bytes, void* stream,
+                          ks_paper_ensemble** out) {
+  if (!out) return fail(KS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  ks_status s = validate(cfg);
+  if (s != KS_OK) return s;
+  if (!workspace) return fail(KS_ERR_INVALID_ARG, "workspace is NULL");
+  if (((uintptr_t)workspace & 255u) != 0) return fail(KS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  const PaperLayout lay = paper_layout(cfg);
+  if (ws_bytes < lay.total) return fail(KS_ERR_WORKSPACE_TOO_SMALL, "workspace below ks_paper_workspace_size");
+  ks_paper_ensemble* e = new ks_paper_ensemble();
+  unsigned char* ws = (unsigned char*)workspace;
+  PaperParams& p = e->p;
+  memset(&p, 0, sizeof(p));
+  p.M = cfg->n_markets;
+  p.market_base = cfg->market_base;
+  p.L = cfg->L;
+  p.A = cfg->A;
+  p.seed = cfg->seed;
+  p.noise2 = 2 * cfg->noise_halfwidth;
+  p.eta4 = 4u * (uint32_t)cfg->noise_halfwidth;
+  p.p_mkt = cfg->p_mkt_q32;
+  p.qmax = (uint32_t)cfg->qmax;
+  p.maker2 = 2 * cfg->maker_half_spread;
+  p.mom_pct = cfg->mom_pct;
+  p.maker_pct = cfg->maker_pct;
+  p.tie_rule = cfg->tie_rule;
+  p.trace_markets = std::min(cfg->trace_markets, cfg->n_markets);
+  p.trace_steps = cfg->trace_markets ? cfg->trace_steps : 0;
+  p.bid = (int32_t*)(ws + lay.bid);
+  p.ask = (int32_t*)(ws + lay.ask);
+  p.mi32 = (int32_t*)(ws + lay.mi32);
+  p.mi64 = (int64_t*)(ws + lay.mi64);
+  p.trace = (int32_t*)(ws + lay.trace);
+  p.err = (uint32_t*)(ws + lay.ctrl);
+  p.step = (uint64_t*)(ws + lay.ctrl + 8);
+  e->M = cfg->n_markets;
+  e->L = cfg->L;
+  e->A = cfg->A;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t ce;
+  if ((ce = cudaGetDevice(&e->device)) != cudaSuccess ||
+      (ce = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ws + lay.ctrl, 0, 64, st)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ws + lay.trace, 0xFF, lay.ctrl - lay.trace, st)) != cudaSuccess) {
+    delete e;
+    return cuda_status(ce, "ks_paper_create");
+  }
+  paper_init_kernel<<<std::min<uint32_t>(e->M, 4096u), 128, 0, st>>>(p);
+  if ((ce = cudaGetLastError()) != cudaSuccess) {
+    delete e;
+    return cuda_status(ce, "paper_init_kernel");
+  }
+  // default shape: 128 threads (one tick each at L = 128), up to 16 agents per thread
+  int nt = 128;
+  while (nt < 1024 && (int64_t)nt * 16 < cfg->A) nt *= 2;
+  int ak = next_pow2(std::max(1, (cfg->A + nt - 1) / nt));
+  s = apply_launch(e, nt, std::min(ak, 16));
+  if (s != KS_OK) {
+    delete e;
+    return s;
+  }
+  *out = e;
+  return KS_OK;
+}
+
+ks_status ks_paper_step_n(ks_paper_ensemble* e, uint32_t n_steps, void* stream) {
+  if (!e) return fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
+  if (n_steps == 0) return KS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  e->var->launch(e->p, n_steps, e->grid, e->smem, st);
+  KSP_CUDA(cudaGetLastError());
+  paper_step_bump<<<1, 1, 0, st>>>(e->p.step, n_steps);
+  KSP_CUDA(cudaGetLastError());
+  return KS_OK;
+}
+
+ks_status ks_paper_read_state(ks_paper_ensemble* e, const ks_paper_state_view* v, void* stream) {
+  if (!e || !v) return fail(KS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const PaperParams& p = e->p;
+  const size_t ML = (size_t)e->M * (size_t)e->L;
+  if (v->bid) KSP_CUDA(cudaMemcpyAsync(v->bid, p.bid, ML * 4, cudaMemcpyDefault, st));
+  if (v->ask) KSP_CUDA(cudaMemcpyAsync(v->ask, p.ask, ML * 4, cudaMemcpyDefault, st));
+  struct F {
+    void* view;
+    const void* dev;
+    size_t pitch, width;
+  } fs[] = {
+      {v->last_tick, p.mi32 + 0, PMI32 * 4, 4}, {v->mid2, p.mi32 + 1, PMI32 * 4, 4},
+      {v->trades, p.mi32 + 2, PMI32 * 4, 4},    {v->last_volume, p.mi32 + 3, PMI32 * 4, 4},
+      {v->sum_price, p.mi64 + 0, PMI64 * 8, 8}, {v->sum_volume, p.mi64 + 1, PMI64 * 8, 8},
+      {v->trace_hash, p.mi64 + 2, PMI64 * 8, 8},
+  };
+  for (auto& f : fs)
+    if (f.view) KSP_CUDA(cudaMemcpy2DAsync(f.view, f.width, f.dev, f.pitch, f.width, e->M, cudaMemcpyDefault, st));
+  if (v->step) KSP_CUDA(cudaMemcpyAsync(v->step, p.step, 8, cudaMemcpyDefault, st));
+  if (v->trace)
+    KSP_CUDA(cudaMemcpyAsync(v->trace, p.trace, (size_t)p.trace_markets * p.trace_steps * 2 * 4, cudaMemcpyDefault,
+                             st));
+  KSP_CUDA(cudaStreamSynchronize(st));
+  return KS_OK;
+}
+
+ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread) {
+  if (!e) return fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
+  return apply_launch(e, threads, agents_per_thread);
+}
+
+ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread) {
+  if (!e || !threads || !agents_per_thread) return fail(KS_ERR_INVALID_ARG, "NULL argument");
+  *threads = e->var->threads;
+  *agents_per_thread = e->var->ak;
+  return KS_OK;
+}
+
+ks_status ks_paper_sync(ks_paper_ensemble* e, void* stream, uint32_t timeout_ms) {
+  if (!e) return fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  KSP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t ce = cudaEventRecord(ev, st);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_status(ce, "cudaEventRecord");
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    ce = cudaEventQuery(ev);
+    if (ce == cudaSuccess) break;
+    if (ce != cudaErrorNotReady) {
+      cudaEventDestroy(ev);
+      return cuda_status(ce, "cudaEventQuery");
+    }
+    if (timeout_ms) {
+      const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+      if (ms.count() >= (long long)timeout_ms) {
+        cudaEventDestroy(ev);
+        return fail(KS_ERR_TIMEOUT, "ks_paper_sync deadline passed before the stream finished");
+      }
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  uint32_t word = 0;
+  KSP_CUDA(cudaMemcpyAsync(&word, e->p.err, 4, cudaMemcpyDeviceToHost, st));
+  KSP_CUDA(cudaStreamSynchronize(st));
+  if (word) {
+    char buf[64];
+    snprintf(buf, sizeof(buf), "device error word 0x%x", word);
+    internal_set_error(buf);
+    return KS_ERR_DEVICE_FAULT;
+  }
+  return KS_OK;
+}
+
+ks_status ks_paper_destroy(ks_paper_ensemble* e) {
+  delete e;
+  return KS_OK;
+}
+
+}  // extern "C"

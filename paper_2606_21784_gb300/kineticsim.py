@@ -30,7 +30,9 @@ EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_stat
            "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
            "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
            "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward", "ks_set_capture", "ks_bc_grad",
-           "ks_adam_step", "ks_mlp_export")
+           "ks_adam_step", "ks_mlp_export", "ks_paper_workspace_size", "ks_paper_create", "ks_paper_step_n",
+           "ks_paper_read_state", "ks_paper_set_launch", "ks_paper_get_launch", "ks_paper_sync",
+           "ks_paper_destroy")
 KS_MLP_NPARAM = 8677
 
 KS_RECORD_WORDS = 22
@@ -102,6 +104,20 @@ class ks_batch_info(ctypes.Structure):
                 ("smem_bytes", ctypes.c_int64)]
 
 
+class ks_paper_config(ctypes.Structure):
+    _fields_ = [("n_markets", ctypes.c_uint32), ("market_base", ctypes.c_uint32), ("L", ctypes.c_int32),
+                ("A", ctypes.c_int32), ("seed", ctypes.c_uint64), ("noise_halfwidth", ctypes.c_int32),
+                ("p_mkt_q32", ctypes.c_uint32), ("qmax", ctypes.c_int32), ("maker_half_spread", ctypes.c_int32),
+                ("mom_pct", ctypes.c_uint32), ("maker_pct", ctypes.c_uint32), ("tie_rule", ctypes.c_int32),
+                ("trace_markets", ctypes.c_uint32), ("trace_steps", ctypes.c_uint32), ("pad_", ctypes.c_int32)]
+
+
+class ks_paper_state_view(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "bid", "ask", "last_tick", "mid2", "trades", "last_volume", "sum_price", "sum_volume", "trace_hash",
+        "step", "trace")]
+
+
 _lib = None
 
 
@@ -147,6 +163,14 @@ def load(build_if_missing: bool = True):
         "ks_adam_step": ([vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, vp], ctypes.c_int),
         "ks_mlp_export": ([vp, vp, vp], ctypes.c_int),
+        "ks_paper_workspace_size": ([P(ks_paper_config), P(ctypes.c_size_t)], ctypes.c_int),
+        "ks_paper_create": ([P(ks_paper_config), vp, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+        "ks_paper_step_n": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
+        "ks_paper_read_state": ([vp, P(ks_paper_state_view), vp], ctypes.c_int),
+        "ks_paper_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "ks_paper_get_launch": ([vp, P(ctypes.c_int32), P(ctypes.c_int32)], ctypes.c_int),
+        "ks_paper_sync": ([vp, vp, ctypes.c_uint32], ctypes.c_int),
+        "ks_paper_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -521,3 +545,86 @@ def unpack_orders(words: np.ndarray) -> dict:
     return dict(qty=(w & 0xFF).astype(np.int32), side=((w >> 8) & 1).astype(np.int32),
                 tick=((w >> 9) & 0xFFF).astype(np.int32), atype=((w >> 21) & 3).astype(np.int32),
                 mlp=((w >> 23) & 1).astype(np.int32))
+
+
+
+# ---------------------------------------------------------------------------
+# The paper's own agents on a tick-aggregated book (ks_paper_*)
+# ---------------------------------------------------------------------------
+PAPER_STATE_FIELDS = {
+    "bid": (np.int32, "book"), "ask": (np.int32, "book"), "last_tick": (np.int32, "market"),
+    "mid2": (np.int32, "market"), "trades": (np.int32, "market"), "last_volume": (np.int32, "market"),
+    "sum_price": (np.int64, "market"), "sum_volume": (np.int64, "market"), "trace_hash": (np.uint64, "market"),
+    "step": (np.uint64, "one"), "trace": (np.int32, "trace"),
+}
+
+
+def make_paper_config(w: dict, trace_markets: int = 0, trace_steps: int = 0) -> ks_paper_config:
+    """ks_paper_config from a paper-agent workload dict (see ``workloads``)."""
+    p = w["params"]
+    return ks_paper_config(int(w["M"]), int(w.get("market_base", 0)), int(w["L"]), int(w["A"]),
+                           int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(p["noise_halfwidth"]), int(p["p_mkt_q32"]),
+                           int(p["qmax"]), int(p["maker_half_spread"]), int(p["mom_pct"]), int(p["maker_pct"]),
+                           int(p.get("tie_rule", 0)), int(trace_markets), int(trace_steps), 0)
+
+
+class PaperEnsemble:
+    """Markets of the paper's own agent model on the current CUDA device; the
+    workspace is a torch uint8 tensor held by this object."""
+
+    def __init__(self, workload: dict, trace_markets: int = 0, trace_steps: int = 0, stream=None):
+        import torch
+        self.workload = workload
+        self.cfg = make_paper_config(workload, trace_markets, trace_steps)
+        self.M, self.L, self.A = int(workload["M"]), int(workload["L"]), int(workload["A"])
+        self.trace_markets = min(int(trace_markets), self.M)
+        self.trace_steps = int(trace_steps) if trace_markets else 0
+        n = ctypes.c_size_t()
+        _check(load().ks_paper_workspace_size(ctypes.byref(self.cfg), ctypes.byref(n)), "ks_paper_workspace_size")
+        self.ws_bytes = n.value
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        _check(load().ks_paper_create(ctypes.byref(self.cfg), self.workspace.data_ptr(), self.ws_bytes,
+                                      _stream_ptr(stream), ctypes.byref(h)), "ks_paper_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ks_paper_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int, stream=None):
+        _check(load().ks_paper_step_n(self.handle, int(n), _stream_ptr(stream)), "ks_paper_step_n")
+
+    def set_launch(self, threads: int, agents_per_thread: int):
+        _check(load().ks_paper_set_launch(self.handle, int(threads), int(agents_per_thread)), "ks_paper_set_launch")
+
+    def get_launch(self) -> dict:
+        t, k = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ks_paper_get_launch(self.handle, ctypes.byref(t), ctypes.byref(k)), "ks_paper_get_launch")
+        return {"threads": t.value, "agents_per_thread": k.value}
+
+    def sync(self, timeout_ms: int = 0, stream=None) -> int:
+        return int(load().ks_paper_sync(self.handle, _stream_ptr(stream), int(timeout_ms)))
+
+    def read_state(self, fields=None, stream=None) -> dict:
+        """Copy the state to host numpy arrays (bid / ask as [M, L])."""
+        import torch
+        fields = list(PAPER_STATE_FIELDS) if fields is None else list(fields)
+        shapes = {"book": (self.M, self.L), "market": (self.M,), "one": (1,),
+                  "trace": (self.trace_markets, self.trace_steps, 2)}
+        v = ks_paper_state_view()
+        bufs = {}
+        for f in fields:
+            dt, per = PAPER_STATE_FIELDS[f]
+            t = torch.empty(shapes[per], dtype=getattr(torch, _TORCH_DT[dt]))
+            bufs[f] = t
+            setattr(v, f, t.data_ptr() if t.numel() else None)
+        _check(load().ks_paper_read_state(self.handle, ctypes.byref(v), _stream_ptr(stream)), "ks_paper_read_state")
+        return {f: t.numpy().view(PAPER_STATE_FIELDS[f][0]).copy() for f, t in bufs.items()}

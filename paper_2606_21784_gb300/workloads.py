@@ -16,6 +16,17 @@ Five workloads, one per benchmark configuration of the method:
 ``mixed_32768``     32768 markets, L in {256..2048}, A log-uniform in
                     [128, 8192], S=10000, 25% MLP agents.
 
+The paper's own agent model (tick-aggregated book, NOISE / MOMENTUM / MAKER
+agents around the mid price, SplitMix64 draws; ``PaperEnsemble``) on the
+shapes of the paper's throughput tables (L=128, S=500):
+
+``paper_8192_1024`` 8192 markets, A=1024 (the paper's peak configuration).
+``paper_8192_256``  8192 markets, A=256 (the paper's fixed workload).
+
+The paper does not publish Delta_noise, P_mkt, q_max or Delta_maker; the
+values below are this build's choice (the standard mix alpha_mom = 0.15,
+alpha_maker = 0.15 is the paper's).
+
 The uneven ensembles draw (L, A) per market from numpy's PCG64 with a fixed
 instance seed; the simulation seed is separate.
 """
@@ -39,6 +50,11 @@ _MIX_CARRY = dict(
     mlp_pct=0, tie_rule=0,
 )
 
+_PAPER_AGENTS = dict(
+    seed=1, noise_halfwidth=4, p_mkt_q32=CANCEL_005_Q32, qmax=10, maker_half_spread=1, mom_pct=15, maker_pct=15,
+    tie_rule=0,
+)
+
 WORKLOADS = {
     "plain_zi_64": dict(M=64, L=256, A=256, S=1000, params=_ZI_DISCARD),
     "plain_mix_8192": dict(M=8192, L=1024, A=4096, S=2000, params=_MIX_CARRY),
@@ -47,6 +63,8 @@ WORKLOADS = {
     "learned_4096": dict(M=4096, L=512, A=2048, S=2000, params=dict(_MIX_CARRY, mlp_pct=100)),
     "mixed_32768": dict(M=32768, L=None, A=None, S=10000, params=dict(_MIX_CARRY, mlp_pct=25),
                         instance=dict(kind="mixed", seed=5)),
+    "paper_8192_1024": dict(M=8192, L=128, A=1024, S=500, params=_PAPER_AGENTS, model="paper"),
+    "paper_8192_256": dict(M=8192, L=128, A=256, S=500, params=_PAPER_AGENTS, model="paper"),
 }
 
 

@@ -98,3 +98,44 @@ def test_null_handles_are_rejected():
     assert lib.ks_step_n(None, 1, None) == ks.KS_ERR_INVALID_ARG
     assert lib.ks_sync(None, None, 0) == ks.KS_ERR_INVALID_ARG
     assert lib.ks_read_state(None, None, None) == ks.KS_ERR_INVALID_ARG
+
+
+# --------------------------------------------------------------------------
+# the paper-agent ensemble (ks_paper_*)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("field,value,status", [
+    ("n_markets", 0, ks.KS_ERR_INVALID_ARG),
+    ("L", 1, ks.KS_ERR_UNSUPPORTED),
+    ("L", 5000, ks.KS_ERR_UNSUPPORTED),
+    ("A", -1, ks.KS_ERR_UNSUPPORTED),
+    ("A", 20000, ks.KS_ERR_UNSUPPORTED),
+    ("qmax", 0, ks.KS_ERR_INVALID_ARG),
+    ("qmax", 256, ks.KS_ERR_INVALID_ARG),
+    ("noise_halfwidth", -1, ks.KS_ERR_INVALID_ARG),
+    ("maker_half_spread", 200, ks.KS_ERR_INVALID_ARG),
+    ("mom_pct", 90, ks.KS_ERR_INVALID_ARG),
+    ("tie_rule", 3, ks.KS_ERR_INVALID_ARG),
+])
+def test_paper_validation_errors(field, value, status):
+    c = ks.make_paper_config(wl.workload("paper_8192_256", M=4))
+    setattr(c, field, value)
+    n = ctypes.c_size_t(0)
+    assert ks.load().ks_paper_workspace_size(ctypes.byref(c), ctypes.byref(n)) == status
+    assert ks.load().ks_last_error()
+
+
+def test_paper_workspace_and_create_checks():
+    lib = ks.load()
+    w = wl.workload("paper_8192_1024")
+    c = ks.make_paper_config(w, trace_markets=2, trace_steps=10)
+    n = ctypes.c_size_t(0)
+    assert lib.ks_paper_workspace_size(ctypes.byref(c), ctypes.byref(n)) == ks.KS_OK
+    ML = w["M"] * w["L"]
+    assert 8 * ML <= n.value <= 8 * ML + 64 * w["M"] + 4096  # bid + ask books, 64 B of scalars, trace
+    h = ctypes.c_void_p(0)
+    assert lib.ks_paper_create(ctypes.byref(c), 256, n.value - 1, None, ctypes.byref(h)) == \
+        ks.KS_ERR_WORKSPACE_TOO_SMALL
+    assert lib.ks_paper_create(ctypes.byref(c), 257, n.value, None, ctypes.byref(h)) == ks.KS_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.ks_paper_step_n(None, 1, None) == ks.KS_ERR_INVALID_ARG
+    assert lib.ks_paper_sync(None, None, 0) == ks.KS_ERR_INVALID_ARG

@@ -1,0 +1,86 @@
+"""GPU parity of the paper-agent kernel (the paper's own NOISE / MOMENTUM /
+MAKER agents on a tick-aggregated book) against the oracle: the clearing
+trace of every step, the resting book and the market scalars, bit-exact."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2606_21784_gb300 import kineticsim as ks
+from paper_2606_21784_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_market(params, gs, m, L, A, steps, s0=0, trace=True):
+    bk = o.paper_init(m, L, A)
+    tp, tv = o.paper_run(params, bk, s0, steps)
+    if trace:
+        assert np.array_equal(gs["trace"][m, :steps, 0], tp), m
+        assert np.array_equal(gs["trace"][m, :steps, 1], tv), m
+    assert np.array_equal(gs["bid"][m], bk.bid), m
+    assert np.array_equal(gs["ask"][m], bk.ask), m
+    sc = bk.scalars()
+    assert int(gs["last_tick"][m]) == sc["last"] and int(gs["mid2"][m]) == sc["mid2"], m
+    assert int(gs["trades"][m]) == sc["trades"] and int(gs["last_volume"][m]) == sc["last_v"], m
+    assert int(gs["sum_price"][m]) == sc["sum_p"] and int(gs["sum_volume"][m]) == sc["sum_v"], m
+    assert int(gs["trace_hash"][m]) == sc["hash"], m
+
+
+def _run(w, steps, splits=None, launch=None, trace=True):
+    ens = ks.PaperEnsemble(w, trace_markets=w["M"] if trace else 0, trace_steps=steps if trace else 0)
+    if launch:
+        ens.set_launch(*launch)
+    for n in splits or [steps]:
+        ens.step(n)
+    assert ens.sync(timeout_ms=300_000) == ks.KS_OK
+    gs = ens.read_state()
+    ens.close()
+    return gs
+
+
+@pytest.mark.parametrize("L,A", [(128, 256), (100, 300), (64, 1024)])
+def test_every_market_and_step_matches_the_oracle(L, A):
+    w = wl.workload("paper_8192_256", M=20, L=L, A=A)
+    steps = 150
+    gs = _run(w, steps)
+    assert int(gs["step"][0]) == steps
+    for m in range(w["M"]):
+        _check_market(w["params"], gs, m, L, A, steps)
+
+
+def test_launch_shapes_and_split_calls_agree():
+    w = wl.workload("paper_8192_256", M=40, L=128, A=256)
+    ref = _run(w, 90, trace=False)
+    for launch, splits in (((128, 2), [90]), ((256, 1), [90]), ((128, 4), [30, 60]), ((256, 2), [1, 88, 1]),
+                           ((512, 16), [90]), ((128, 16), [45, 45])):
+        got = _run(w, 90, splits=splits, launch=launch, trace=False)
+        for f in ref:
+            assert np.array_equal(ref[f], got[f]), (launch, f)
+
+
+@pytest.mark.parametrize("over", [dict(tie_rule=1), dict(mom_pct=70, maker_pct=15), dict(mom_pct=0, maker_pct=100),
+                                  dict(noise_halfwidth=0, p_mkt_q32=0), dict(noise_halfwidth=40, qmax=255)])
+def test_rule_variants_match_the_oracle(over):
+    w = wl.workload("paper_8192_256", M=8, L=96, A=200, **over)
+    gs = _run(w, 120)
+    for m in range(w["M"]):
+        _check_market(w["params"], gs, m, 96, 200, 120)
+
+
+def test_edge_shapes():
+    for L, A in ((2, 5), (128, 0), (4096, 64), (7, 3)):
+        w = wl.workload("paper_8192_256", M=3, L=L, A=A, noise_halfwidth=min(4, L), maker_half_spread=1)
+        gs = _run(w, 40)
+        for m in range(3):
+            _check_market(w["params"], gs, m, L, A, 40)
+
+
+def test_full_size_peak_workload_sampled_markets():
+    """The paper's peak shape (8192 markets x 1024 agents, L=128, S=500):
+    the whole ensemble in the default launch, sampled markets against the oracle."""
+    w = wl.workload("paper_8192_1024")
+    gs = _run(w, w["S"], trace=False)
+    for m in (0, 1, 777, 4096, 8190, 8191):
+        _check_market(w["params"], gs, m, 128, 1024, w["S"], trace=False)
+    # every market traded and stayed on the grid
+    assert gs["trades"].min() > 0 and 0 <= gs["last_tick"].min() and gs["last_tick"].max() < 128
