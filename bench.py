@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--no-probes", action="store_true")
     ap.add_argument("--sim-steps", type=int, default=0, help="override S (profiling small cases)")
     ap.add_argument("--markets", type=int, default=0, help="override M (profiling small cases)")
-    ap.add_argument("--launch", default="", help="threads,agents_per_thread,reg_cap (skip the autotuner)")
+    ap.add_argument("--launch", default="",
+                    help="threads,agents_per_thread,reg_cap (paper workloads: threads,agents_per_thread,min_ctas); "
+                         "skips the autotuner")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / learned comparison runs")
     return ap.parse_args()
 
@@ -275,6 +277,49 @@ def compare_forms(ks, workloads, stream, plain_rate):
         out["batched_20000_tuned"] = {"error": str(e)[:200]}
     ens.close()
     out.update(learned_forms(ks, workloads, stream))
+    out["paper_table_ii"] = paper_forms(ks, workloads, stream)
+    return out
+
+
+# the paper's Table II (RTX 5090, its own agents, L=128, S=500): agent-events/s
+PAPER_TABLE_II = {(64, 256): 3.61e9, (256, 256): 1.35e10, (1024, 256): 3.69e10, (4096, 256): 4.73e10,
+                  (16384, 256): 5.39e10, (8192, 16): 8.41e9, (8192, 64): 2.84e10, (8192, 256): 5.16e10,
+                  (8192, 1024): 5.47e10}
+
+
+def paper_forms(ks, workloads, stream, reps: int = 3):
+    """The paper's own agent model (tick-aggregated book, NOISE / MOMENTUM /
+    MAKER agents, SplitMix64 draws) on every shape of the paper's throughput
+    table (markets sweep at A=256, agents sweep at 8192 markets; L=128,
+    S=500), each with its tuned launch, beside the paper's RTX 5090 numbers
+    (whose agent constants are unpublished: the comparison is of throughput
+    on the same shapes, not of identical simulations)."""
+    import torch
+
+    from paper_2606_21784_gb300 import autotune
+    out = {}
+    for (M, A), ref in PAPER_TABLE_II.items():
+        w = workloads.workload("paper_8192_256", M=M, A=A)
+        ens = ks.PaperEnsemble(w)
+        launch = autotune.apply(ens, w)
+        S = int(w["S"])
+        ens.step(50, stream)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ens.step(S, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        rate = float(M) * A * S / (best / 1e3)
+        out[f"M{M}_A{A}"] = {"events_per_s": rate, "ms_per_run": best, "paper_rtx5090": ref,
+                             "ratio_to_paper": rate / ref,
+                             "launch": {k: launch[k] for k in ("threads", "agents_per_thread", "min_ctas")}}
+        ens.close()
     return out
 
 
@@ -356,6 +401,8 @@ def run_ours(args):
     if args.markets:
         w["M"] = args.markets
     w = sharding.shard(w, rank, world)
+    if w.get("model") == "paper":
+        return run_paper(args, w, rank, world, dev)
     S = int(w["S"])
     blob = quick_policy()[0] if int(w["params"].get("mlp_pct", 0)) > 0 else None
     L_, A_ = workloads.sizes(w)
@@ -497,6 +544,72 @@ def run_ours(args):
             "clocks": clocks,
             "paper_context": {"value": 5.47e10, "hardware": "RTX 5090 (sm_120), L=128, S=500, M=8192, A=1024"},
         }
+        print(json.dumps(out), flush=True)
+    ens.close()
+    sharding.finalize()
+    return 0
+
+
+def run_paper(args, w, rank, world, dev):
+    """The paper's own agent model as the main workload (``--workload
+    paper_*``): same timing rules; the state is read back to the host in the
+    end-to-end leg (the model has no per-agent state to upload)."""
+    import torch
+
+    from paper_2606_21784_gb300 import autotune
+    from paper_2606_21784_gb300 import kineticsim as ks
+    from paper_2606_21784_gb300 import sharding
+    ens = ks.PaperEnsemble(w)
+    if args.launch:
+        nt, ak, mc = (int(x) for x in args.launch.split(","))
+        ens.set_launch(nt, ak, mc)
+    else:
+        autotune.apply(ens, w)
+    S = int(w["S"])
+    events_per_step = float(w["M"]) * w["A"] * S
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ens.step(S, stream)
+    torch.cuda.synchronize()
+    sharding.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0e = torch.cuda.Event(enable_timing=True)
+    t1e = torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for e0, e1 in ev:
+        e0.record(stream)
+        ens.step(S, stream)
+        e1.record(stream)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    sharding.barrier()
+    clocks = sampler.stop()
+    total_ms = sharding.max_over_ranks(t0e.elapsed_time(t1e), dev)
+    value = world * events_per_step * args.steps / (total_ms / 1e3)
+    if ens.sync(timeout_ms=600_000) != ks.KS_OK:
+        raise RuntimeError("paper ensemble reported a device error")
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(args.e2e_steps):
+        ens.step(S, stream)
+        st = ens.read_state(["bid", "ask", "last_tick", "trades", "sum_volume"], stream)
+        nbytes = sum(a.nbytes for a in st.values())
+    e2e_s = sharding.max_over_ranks(time.perf_counter() - t0, dev)
+    if rank == 0:
+        out = {"metric": "agent_events_per_s", "value": value, "unit": "events/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+               "data": "synthetic",
+               "config": {"workload": args.workload, "M": int(w["M"]), "L": int(w["L"]), "A": int(w["A"]), "S": S,
+                          "model": "the paper's agents (tick-aggregated book)", "launch": ens.get_launch(),
+                          "l2": "book state resident on chip; 1 MiB of global state per 256 markets"},
+               "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
+                       "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
+               "gpu_launches": 2 * args.steps, "roofline": None, "clocks": clocks,
+               "paper_context": {"value": PAPER_TABLE_II.get((int(w["M"]), int(w["A"]))),
+                                 "hardware": "RTX 5090 (sm_120), Table II"}}
         print(json.dumps(out), flush=True)
     ens.close()
     sharding.finalize()

@@ -324,15 +324,19 @@ typedef struct ks_paper_state_view {
 /* Workspace bytes, creation (init kernel queued on `stream`), steps [s, s+n)
  * in one persistent launch (asynchronous, capturable), state copies (then
  * `stream` is synchronised), launch shape (threads 128..1024, agents per
- * thread 1..16, threads * agents_per_thread >= A), deadline wait and error
- * word check, handle release: as the functions above of the same name. */
+ * thread 1..16, threads * agents_per_thread >= A; min_ctas 0 or 1 = the
+ * compiler's register choice, else the register cap of min_ctas resident
+ * CTAs per SM: 128 threads with 1 or 2 agents per thread at 8, with 4 or 8
+ * at 6), deadline wait and error word check, handle release: as the
+ * functions above of the same name. */
 ks_status ks_paper_workspace_size(const ks_paper_config* cfg, size_t* bytes);
 ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws_bytes, void* stream,
                           ks_paper_ensemble** out);
 ks_status ks_paper_step_n(ks_paper_ensemble* e, uint32_t n_steps, void* stream);
 ks_status ks_paper_read_state(ks_paper_ensemble* e, const ks_paper_state_view* dst, void* stream);
-ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread);
-ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread);
+ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread, int32_t min_ctas);
+ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread,
+                              int32_t* min_ctas);
 ks_status ks_paper_sync(ks_paper_ensemble* e, void* stream, uint32_t timeout_ms);
 ks_status ks_paper_destroy(ks_paper_ensemble* e);
 

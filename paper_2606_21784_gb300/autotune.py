@@ -178,8 +178,46 @@ def tune_batched(w: dict, L=None, A=None, steps: int = 20, max_sample: int = 121
     return out
 
 
+# compiled shapes of the paper-agent kernel: (threads per market, agents per thread, min resident CTAs)
+PAPER_SHAPES = ((32, 1, 1), (32, 2, 1), (32, 4, 1), (32, 1, 8), (32, 2, 8), (128, 1, 1), (128, 2, 1), (128, 4, 1),
+                (128, 8, 1), (128, 16, 1), (128, 1, 8), (128, 2, 8), (128, 4, 6), (128, 8, 6), (256, 1, 1),
+                (256, 2, 1), (256, 4, 1), (256, 8, 1), (256, 16, 1), (512, 16, 1), (1024, 16, 1))
+
+
+def tune_paper(w: dict, steps: int = 100, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Best launch of the paper-agent kernel for workload dict ``w``; applies nothing."""
+    M, L, A = int(w["M"]), int(w["L"]), int(w["A"])
+    key = f"paper|{_device_tag()}|L{L}|A{A}|M{M}"
+    if use_cache:
+        c = _cache_load().get(key)
+        if c:
+            return c
+    ens = ks.PaperEnsemble(w)
+    best = None
+    for nt, ak, mc in PAPER_SHAPES:
+        if nt * ak < A or nt * ak > 8 * max(A, 128):
+            continue
+        try:
+            ens.set_launch(nt, ak, mc)
+        except ks.KsError:
+            continue
+        rate = float(M) * A * steps / _time_steps(ens, steps)
+        if verbose:
+            print("paper", (nt, ak, mc), f"{rate:.3e}")
+        if best is None or rate > best[0]:
+            best = (rate, dict(threads=nt, agents_per_thread=ak, min_ctas=mc))
+    ens.close()
+    out = dict(best[1], events_per_s=best[0])
+    _cache_store(key, out)
+    return out
+
+
 def apply(ens, w: dict, use_cache: bool = True, verbose: bool = False) -> dict:
-    """Tunes and applies the launch of an Ensemble built from workload dict ``w``."""
+    """Tunes and applies the launch of an Ensemble (or PaperEnsemble) built from workload dict ``w``."""
+    if isinstance(ens, ks.PaperEnsemble):
+        best = tune_paper(w, use_cache=use_cache, verbose=verbose)
+        ens.set_launch(best["threads"], best["agents_per_thread"], best["min_ctas"])
+        return best
     if ens.batch_info()["batched"]:
         plan = tune_batched(w, ens.L, ens.A, use_cache=use_cache, verbose=verbose)
         ens.set_batch_plan(plan["cta_threads"], plan["buckets"])

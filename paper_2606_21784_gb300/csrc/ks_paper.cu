@@ -2,10 +2,12 @@
 // MAKER agents around the mid price, SplitMix64 draws of Sec. III-F) on a
 // tick-aggregated book, as a persistent kernel and its C ABI (ks_paper_*).
 //
-// One CTA runs one market at a time for all n steps of a call, markets dealt
-// round-robin.  Thread t owns agents [t*AK, t*AK+AK) (their classes packed
-// in one register) and ticks [t*LT, t*LT+LT) of the book in shared memory
-// (BUY[p] at word 2p, SELL[p] at 2p+1).  Step s, between four barriers:
+// A group of GT threads (a whole CTA, or one warp of a 128-thread CTA for
+// markets of up to 32 x AK agents) runs one market at a time for all n steps
+// of a call, markets dealt round-robin.  Thread t of the group owns agents
+// [t*AK, t*AK+AK) (their classes packed in one register) and ticks
+// [t*LT, t*LT+LT) of the book in shared memory (BUY[p] at word 2p, SELL[p]
+// at 2p+1).  Step s, between four group barriers:
 //   orders    every agent draws two SplitMix64 words and adds its order to the
 //             book with a shared reduction                   (Alg. 1, Phase 3)
 //   B1..B3    suffix / prefix scans by warp shuffles, lowest / highest
@@ -117,8 +119,7 @@ __device__ __forceinline__ void fold_best(int32_t* keys, int bb, int ba) {
 
 template <int NT, int AK, int LTC>
 __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, uint32_t s0, uint32_t n_steps,
-                                             const PaperSmem& sm) {
-  const int t = (int)threadIdx.x;
+                                             const PaperSmem& sm, int t, int bar) {
   const int lane = t & 31;
   const int wid = t >> 5;
   const int L = P.L, A = P.A;
@@ -133,7 +134,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   if (t < 4) sm.bbk[t] = (t & 1) ? L : -1;  // both parities: best bid -1, best ask L
   for (int i = t; i < 2 * book_len(L); i += NT) book[i] = 0;
   if (t < 8) sm.kx[t] = 0ull;
-  __syncthreads();
+  gsync<NT>(bar);
   {
     int bb = -1, ba = L;
     for (int i = 0; i < LT; ++i) {
@@ -167,7 +168,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   }
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
   const bool traced = m < P.trace_markets;
-  __syncthreads();
+  gsync<NT>(bar);
 
   for (uint32_t j = 0; j < n_steps; ++j) {
     const uint32_t s = s0 + j;
@@ -203,7 +204,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
       const int q = 1 + (int)__umulhi(w_qty, P.qmax);
       red_add_if(book_s + 4u * (uint32_t)(2 * tick + (int)sell), q, a < A);
     }
-    __syncthreads();  // B1: the step's orders are in the book
+    gsync<NT>(bar);  // B1: the step's orders are in the book
 
     // ---- clearing (Eq. 1-2) ---------------------------------------------------------------
     constexpr int R = LTC > 0 ? LTC : 1;
@@ -239,7 +240,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     if (lane == 0) sm.wD[wid] = sufB;
     if (lane == 31) sm.wS[wid] = preS;
     unsigned long long* kx = sm.kx + 4 * (j & 1);
-    __syncthreads();  // B2
+    gsync<NT>(bar);  // B2
     const int offD = (int)__reduce_add_sync(0xffffffffu, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
     const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
     const int D0 = offD + sufB;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
         if (tie1) atomicMax(kx + 2, kT);
       }
     }
-    __syncthreads();  // B3
+    gsync<NT>(bar);  // B3
     const unsigned long long kLo = kx[0], kHi = kx[1];
     const int vstar = (int)(kLo >> 12);
     const int p_lo = 4095 - (int)(kLo & 4095u);
@@ -365,7 +366,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
         tr[1] = vstar;
       }
     }
-    __syncthreads();  // B5: next mid keys complete, book empty
+    gsync<NT>(bar);  // B5: next mid keys complete, book empty
   }
   if (t == 0) {
     int32_t* mo = P.mi32 + (size_t)m * PMI32;
@@ -378,27 +379,37 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     mo64[1] = sumv;
     mo64[2] = (int64_t)hash;
   }
-  __syncthreads();  // shared memory is reused by the CTA's next market
+  gsync<NT>(bar);  // shared memory is reused by the group's next market
 }
 
-template <int NT, int AK>
-__global__ void __launch_bounds__(NT) paper_kernel(PaperParams P, uint32_t n_steps) {
+// Shared memory per group, 16-byte aligned.
+__host__ __device__ inline size_t paper_group_bytes(int L) { return (paper_smem_bytes(L) + 15) & ~(size_t)15; }
+
+// CTA of NT threads in groups of GT (NT / GT markets in parallel; GT = 32
+// groups synchronise with __syncwarp, larger ones with named barriers).
+// MINB > 1: compiled for at least MINB resident CTAs per SM (a register cap).
+template <int NT, int GT, int AK, int MINB>
+__global__ void __launch_bounds__(NT, MINB) paper_kernel(PaperParams P, uint32_t n_steps) {
+  static_assert(GT == 32 || GT == NT, "groups are one warp or the whole CTA");
+  constexpr int G = NT / GT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t s0 = (uint32_t)(*P.step);
-  const PaperSmem sm = paper_carve(smem_raw, P.L);
-  const int LT = (P.L + NT - 1) / NT;
+  const int g = (int)threadIdx.x / GT;
+  const PaperSmem sm = paper_carve(smem_raw + (size_t)g * paper_group_bytes(P.L), P.L);
+  const int LT = (P.L + GT - 1) / GT;
   const int LTsel = ((LT == 1 || LT == 2 || LT == 4 || LT == 8) && (P.L % LT == 0)) ? LT : 0;
-  if (P.A > NT * AK) {
+  if (P.A > GT * AK) {
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(P.err, ERR_SHAPE);
     return;
   }
-  for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
+  const int t = (int)threadIdx.x % GT;
+  for (uint32_t m = blockIdx.x * G + g; m < P.M; m += gridDim.x * G) {
     switch (LTsel) {
-      case 1: paper_market<NT, AK, 1>(P, m, s0, n_steps, sm); break;
-      case 2: paper_market<NT, AK, 2>(P, m, s0, n_steps, sm); break;
-      case 4: paper_market<NT, AK, 4>(P, m, s0, n_steps, sm); break;
-      case 8: paper_market<NT, AK, 8>(P, m, s0, n_steps, sm); break;
-      default: paper_market<NT, AK, 0>(P, m, s0, n_steps, sm); break;
+      case 1: paper_market<GT, AK, 1>(P, m, s0, n_steps, sm, t, 0); break;
+      case 2: paper_market<GT, AK, 2>(P, m, s0, n_steps, sm, t, 0); break;
+      case 4: paper_market<GT, AK, 4>(P, m, s0, n_steps, sm, t, 0); break;
+      case 8: paper_market<GT, AK, 8>(P, m, s0, n_steps, sm, t, 0); break;
+      default: paper_market<GT, AK, 0>(P, m, s0, n_steps, sm, t, 0); break;
     }
   }
 }
@@ -423,20 +434,31 @@ __global__ void paper_init_kernel(PaperParams P) {
 __global__ void paper_step_bump(uint64_t* step, uint32_t n) { *step += n; }
 
 using PaperLaunchFn = void (*)(const PaperParams&, uint32_t, int, size_t, cudaStream_t);
-template <int NT, int AK>
+template <int NT, int GT, int AK, int MINB>
 void paper_launch(const PaperParams& p, uint32_t n, int grid, size_t smem, cudaStream_t st) {
-  paper_kernel<NT, AK><<<grid, NT, smem, st>>>(p, n);
+  paper_kernel<NT, GT, AK, MINB><<<grid, NT, smem, st>>>(p, n);
 }
 
 struct PaperVariant {
-  int threads, ak;
+  int threads;  // threads per market (group); a 32-thread group shares a 128-thread CTA with three others
+  int ak, min_ctas;
+  int cta_threads;
   PaperLaunchFn launch;
   const void* kernel;
 };
-#define KS_PV(NT, AK) PaperVariant{NT, AK, &paper_launch<NT, AK>, (const void*)&paper_kernel<NT, AK>}
-static const PaperVariant kPaperVariants[] = {KS_PV(128, 1),  KS_PV(128, 2),  KS_PV(128, 4),  KS_PV(128, 8),
-                                              KS_PV(128, 16), KS_PV(256, 1),  KS_PV(256, 2),  KS_PV(256, 4),
-                                              KS_PV(256, 8),  KS_PV(256, 16), KS_PV(512, 16), KS_PV(1024, 16)};
+#define KS_PV(NT, GT, AK, MB)                                                                  \
+  PaperVariant {                                                                               \
+    GT, AK, MB, NT, &paper_launch<NT, GT, AK, MB>, (const void*)&paper_kernel<NT, GT, AK, MB> \
+  }
+// (threads per market, agents per thread, 1 = compiler's register choice,
+// else the register cap of that many resident CTAs; the capped shapes do not spill)
+static const PaperVariant kPaperVariants[] = {
+    KS_PV(128, 32, 1, 1),    KS_PV(128, 32, 2, 1),    KS_PV(128, 32, 4, 1),    KS_PV(128, 32, 1, 8),
+    KS_PV(128, 32, 2, 8),    KS_PV(128, 128, 1, 1),   KS_PV(128, 128, 2, 1),   KS_PV(128, 128, 4, 1),
+    KS_PV(128, 128, 8, 1),   KS_PV(128, 128, 16, 1),  KS_PV(128, 128, 1, 8),   KS_PV(128, 128, 2, 8),
+    KS_PV(128, 128, 4, 6),   KS_PV(128, 128, 8, 6),   KS_PV(256, 256, 1, 1),   KS_PV(256, 256, 2, 1),
+    KS_PV(256, 256, 4, 1),   KS_PV(256, 256, 8, 1),   KS_PV(256, 256, 16, 1),  KS_PV(512, 512, 16, 1),
+    KS_PV(1024, 1024, 16, 1)};
 #undef KS_PV
 
 }  // namespace ks
@@ -515,20 +537,22 @@ ks_status validate(const ks_paper_config* c) {
   return KS_OK;
 }
 
-ks_status apply_launch(ks_paper_ensemble* e, int threads, int ak) {
+ks_status apply_launch(ks_paper_ensemble* e, int threads, int ak, int min_ctas) {
   const PaperVariant* v = nullptr;
   for (const auto& x : kPaperVariants)
-    if (x.threads == threads && x.ak == ak) v = &x;
-  if (!v) return fail(KS_ERR_INVALID_ARG, "no paper-agent kernel for this (threads, agents_per_thread)");
+    if (x.threads == threads && x.ak == ak && x.min_ctas == std::max(min_ctas, 1)) v = &x;
+  if (!v) return fail(KS_ERR_INVALID_ARG, "no paper-agent kernel for this (threads, agents_per_thread, min_ctas)");
   if ((int64_t)threads * ak < e->A) return fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below A");
-  const size_t smem = paper_smem_bytes(e->L);
+  const int G = v->cta_threads / v->threads;  // markets per CTA
+  const size_t smem = (size_t)G * paper_group_bytes(e->L);
+  if (smem > 200 * 1024) return fail(KS_ERR_UNSUPPORTED, "launch shape needs more shared memory than a CTA has");
   KSP_CUDA(cudaFuncSetAttribute(v->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v->kernel, threads, smem));
+  KSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v->kernel, v->cta_threads, smem));
   if (occ < 1) return fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
   e->var = v;
   e->smem = smem;
-  e->grid = (int)std::min<int64_t>((int64_t)e->M, (int64_t)occ * e->num_sms);
+  e->grid = (int)std::min<int64_t>(((int64_t)e->M + G - 1) / G, (int64_t)occ * e->num_sms);
   return KS_OK;
 }
 
@@ -603,11 +627,14 @@ ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws
     delete e;
     return cuda_status(ce, "paper_init_kernel");
   }
-  // default shape: 128 threads (one tick each at L = 128), up to 16 agents per thread
-  int nt = 128;
+  // default shape (measured on GB300 at L = 128): a warp per market up to 64
+  // agents, else 128 threads per market with up to 16 agents each, under the
+  // register caps that do not spill
+  int nt = cfg->A <= 64 ? 32 : 128;
   while (nt < 1024 && (int64_t)nt * 16 < cfg->A) nt *= 2;
-  int ak = next_pow2(std::max(1, (cfg->A + nt - 1) / nt));
-  s = apply_launch(e, nt, std::min(ak, 16));
+  const int ak = std::min(16, next_pow2(std::max(1, (cfg->A + nt - 1) / nt)));
+  const int mc = nt == 32 ? 1 : ((nt == 128 && ak <= 2) ? 8 : ((nt == 128 && ak <= 8) ? 6 : 1));
+  s = apply_launch(e, nt, ak, mc);
   if (s != KS_OK) {
     delete e;
     return s;
@@ -654,15 +681,17 @@ ks_status ks_paper_read_state(ks_paper_ensemble* e, const ks_paper_state_view* v
   return KS_OK;
 }
 
-ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread) {
+ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread, int32_t min_ctas) {
   if (!e) return fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
-  return apply_launch(e, threads, agents_per_thread);
+  return apply_launch(e, threads, agents_per_thread, min_ctas);
 }
 
-ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread) {
-  if (!e || !threads || !agents_per_thread) return fail(KS_ERR_INVALID_ARG, "NULL argument");
+ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread,
+                              int32_t* min_ctas) {
+  if (!e || !threads || !agents_per_thread || !min_ctas) return fail(KS_ERR_INVALID_ARG, "NULL argument");
   *threads = e->var->threads;
   *agents_per_thread = e->var->ak;
+  *min_ctas = e->var->min_ctas;
   return KS_OK;
 }
 

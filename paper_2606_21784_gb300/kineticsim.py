@@ -167,8 +167,8 @@ def load(build_if_missing: bool = True):
         "ks_paper_create": ([P(ks_paper_config), vp, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
         "ks_paper_step_n": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
         "ks_paper_read_state": ([vp, P(ks_paper_state_view), vp], ctypes.c_int),
-        "ks_paper_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
-        "ks_paper_get_launch": ([vp, P(ctypes.c_int32), P(ctypes.c_int32)], ctypes.c_int),
+        "ks_paper_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "ks_paper_get_launch": ([vp, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)], ctypes.c_int),
         "ks_paper_sync": ([vp, vp, ctypes.c_uint32], ctypes.c_int),
         "ks_paper_destroy": ([vp], ctypes.c_int),
     }
@@ -602,13 +602,15 @@ class PaperEnsemble:
     def step(self, n: int, stream=None):
         _check(load().ks_paper_step_n(self.handle, int(n), _stream_ptr(stream)), "ks_paper_step_n")
 
-    def set_launch(self, threads: int, agents_per_thread: int):
-        _check(load().ks_paper_set_launch(self.handle, int(threads), int(agents_per_thread)), "ks_paper_set_launch")
+    def set_launch(self, threads: int, agents_per_thread: int, min_ctas: int = 1):
+        _check(load().ks_paper_set_launch(self.handle, int(threads), int(agents_per_thread), int(min_ctas)),
+               "ks_paper_set_launch")
 
     def get_launch(self) -> dict:
-        t, k = ctypes.c_int32(), ctypes.c_int32()
-        _check(load().ks_paper_get_launch(self.handle, ctypes.byref(t), ctypes.byref(k)), "ks_paper_get_launch")
-        return {"threads": t.value, "agents_per_thread": k.value}
+        t, k, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ks_paper_get_launch(self.handle, ctypes.byref(t), ctypes.byref(k), ctypes.byref(c)),
+               "ks_paper_get_launch")
+        return {"threads": t.value, "agents_per_thread": k.value, "min_ctas": c.value}
 
     def sync(self, timeout_ms: int = 0, stream=None) -> int:
         return int(load().ks_paper_sync(self.handle, _stream_ptr(stream), int(timeout_ms)))

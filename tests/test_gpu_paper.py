@@ -51,11 +51,28 @@ def test_every_market_and_step_matches_the_oracle(L, A):
 def test_launch_shapes_and_split_calls_agree():
     w = wl.workload("paper_8192_256", M=40, L=128, A=256)
     ref = _run(w, 90, trace=False)
-    for launch, splits in (((128, 2), [90]), ((256, 1), [90]), ((128, 4), [30, 60]), ((256, 2), [1, 88, 1]),
-                           ((512, 16), [90]), ((128, 16), [45, 45])):
+    for launch, splits in (((128, 2, 1), [90]), ((256, 1, 1), [90]), ((128, 4, 1), [30, 60]),
+                           ((256, 2, 1), [1, 88, 1]), ((512, 16, 1), [90]), ((128, 16, 1), [45, 45]),
+                           ((128, 2, 8), [90]), ((128, 8, 6), [60, 30]), ((128, 4, 6), [90])):
         got = _run(w, 90, splits=splits, launch=launch, trace=False)
         for f in ref:
             assert np.array_equal(ref[f], got[f]), (launch, f)
+
+
+def test_warp_per_market_shapes_agree():
+    w = wl.workload("paper_8192_256", M=37, L=128, A=100)
+    ref = _run(w, 80, launch=(128, 1, 1))
+    for m in range(w["M"]):
+        _check_market(w["params"], ref, m, 128, 100, 80)
+    for launch in ((32, 4, 1), (256, 1, 1), (128, 1, 8)):
+        got = _run(w, 80, launch=launch, splits=[25, 55])
+        for f in ref:
+            assert np.array_equal(ref[f], got[f]), (launch, f)
+    w = wl.workload("paper_8192_256", M=9, L=128, A=64)
+    ref = _run(w, 60, launch=(32, 2, 8))
+    got = _run(w, 60, launch=(128, 1, 1))
+    for f in ref:
+        assert np.array_equal(ref[f], got[f]), f
 
 
 @pytest.mark.parametrize("over", [dict(tie_rule=1), dict(mom_pct=70, maker_pct=15), dict(mom_pct=0, maker_pct=100),
