@@ -3,7 +3,7 @@
 // tick-aggregated book, as a persistent kernel and its C ABI (ks_paper_*).
 //
 // A group of GT threads (a whole CTA, or one warp of a 128-thread CTA for
-// markets of up to 32 x AK agents) runs one market at a time for all n steps
+// markets of up to 32 x AK agents; AK up to 32) runs one market at a time for all n steps
 // of a call, markets dealt round-robin.  Thread t of the group owns agents
 // [t*AK, t*AK+AK) (their classes packed in one register) and ticks
 // [t*LT, t*LT+LT) of the book in shared memory (BUY[p] at word 2p, SELL[p]
@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <chrono>
 #include <thread>
+#include <type_traits>
 
 #include "kineticsim.h"
 #include "ks_market.cuh"
@@ -158,13 +159,14 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   // ---- agent classes (channel 2 of step 0), two bits per agent ----------------------------
   const uint64_t gid0 = (uint64_t)(P.market_base + m) * (uint64_t)A + (uint64_t)(t * AK);
   const uint64_t abase = P.seed + SM64_GID * gid0;  // + gamma * (8 s + c) + SM64_GID * k
-  uint32_t cls = 0;
+  using ClassWord = typename std::conditional<(AK > 16), uint64_t, uint32_t>::type;
+  ClassWord cls = 0;
 #pragma unroll
   for (int k = 0; k < AK; ++k) {
     const uint32_t w = (uint32_t)(sm64_mix(abase + SM64_GID * (uint64_t)k + 2ull * SM64_GAMMA) >> 32);
     const uint32_t pct = __umulhi(w, 100u);
     const uint32_t c = pct < P.maker_pct ? PAPER_MAKER : (pct < P.maker_pct + P.mom_pct ? PAPER_MOMENTUM : PAPER_NOISE);
-    cls |= c << (2 * k);
+    cls |= (ClassWord)c << (2 * k);
   }
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
   const bool traced = m < P.trace_markets;
@@ -187,7 +189,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
       const uint64_t u1 = sm64_mix(c0 + SM64_GAMMA);
       const uint32_t w_mkt = (uint32_t)(u0 >> 32), w_coin = (uint32_t)u0;
       const uint32_t w_price = (uint32_t)(u1 >> 32), w_qty = (uint32_t)u1;
-      const uint32_t c = (cls >> (2 * k)) & 3u;
+      const uint32_t c = (uint32_t)(cls >> (2 * k)) & 3u;
       const bool maker = c == PAPER_MAKER;
       const bool mom = c == PAPER_MOMENTUM;
       const uint32_t coin = w_coin >> 31;
@@ -454,7 +456,8 @@ struct PaperVariant {
 // else the register cap of that many resident CTAs; the capped shapes do not spill)
 static const PaperVariant kPaperVariants[] = {
     KS_PV(128, 32, 1, 1),    KS_PV(128, 32, 2, 1),    KS_PV(128, 32, 4, 1),    KS_PV(128, 32, 1, 8),
-    KS_PV(128, 32, 2, 8),    KS_PV(128, 128, 1, 1),   KS_PV(128, 128, 2, 1),   KS_PV(128, 128, 4, 1),
+    KS_PV(128, 32, 2, 8),    KS_PV(128, 32, 8, 1),    KS_PV(128, 32, 8, 6),    KS_PV(128, 32, 16, 1),
+    KS_PV(128, 32, 32, 1),    KS_PV(128, 128, 1, 1),   KS_PV(128, 128, 2, 1),   KS_PV(128, 128, 4, 1),
     KS_PV(128, 128, 8, 1),   KS_PV(128, 128, 16, 1),  KS_PV(128, 128, 1, 8),   KS_PV(128, 128, 2, 8),
     KS_PV(128, 128, 4, 6),   KS_PV(128, 128, 8, 6),   KS_PV(256, 256, 1, 1),   KS_PV(256, 256, 2, 1),
     KS_PV(256, 256, 4, 1),   KS_PV(256, 256, 8, 1),   KS_PV(256, 256, 16, 1),  KS_PV(512, 512, 16, 1),
@@ -627,13 +630,13 @@ ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws
     delete e;
     return cuda_status(ce, "paper_init_kernel");
   }
-  // default shape (measured on GB300 at L = 128): a warp per market up to 64
-  // agents, else 128 threads per market with up to 16 agents each, under the
-  // register caps that do not spill
-  int nt = cfg->A <= 64 ? 32 : 128;
+  // default shape (measured on GB300 at L = 128 with 8192 markets): a warp per
+  // market up to 256 agents, else 128 threads per market with up to 16 agents
+  // each, under the register caps that won
+  int nt = cfg->A <= 256 ? 32 : 128;
   while (nt < 1024 && (int64_t)nt * 16 < cfg->A) nt *= 2;
   const int ak = std::min(16, next_pow2(std::max(1, (cfg->A + nt - 1) / nt)));
-  const int mc = nt == 32 ? 1 : ((nt == 128 && ak <= 2) ? 8 : ((nt == 128 && ak <= 8) ? 6 : 1));
+  const int mc = nt == 32 ? (ak == 8 ? 6 : 1) : ((nt == 128 && ak <= 2) ? 8 : ((nt == 128 && ak <= 8) ? 6 : 1));
   s = apply_launch(e, nt, ak, mc);
   if (s != KS_OK) {
     delete e;

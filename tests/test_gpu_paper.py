@@ -53,7 +53,8 @@ def test_launch_shapes_and_split_calls_agree():
     ref = _run(w, 90, trace=False)
     for launch, splits in (((128, 2, 1), [90]), ((256, 1, 1), [90]), ((128, 4, 1), [30, 60]),
                            ((256, 2, 1), [1, 88, 1]), ((512, 16, 1), [90]), ((128, 16, 1), [45, 45]),
-                           ((128, 2, 8), [90]), ((128, 8, 6), [60, 30]), ((128, 4, 6), [90])):
+                           ((128, 2, 8), [90]), ((128, 8, 6), [60, 30]), ((128, 4, 6), [90]), ((32, 8, 1), [90]),
+                           ((32, 8, 6), [40, 50]), ((32, 32, 1), [90])):
         got = _run(w, 90, splits=splits, launch=launch, trace=False)
         for f in ref:
             assert np.array_equal(ref[f], got[f]), (launch, f)
@@ -64,7 +65,7 @@ def test_warp_per_market_shapes_agree():
     ref = _run(w, 80, launch=(128, 1, 1))
     for m in range(w["M"]):
         _check_market(w["params"], ref, m, 128, 100, 80)
-    for launch in ((32, 4, 1), (256, 1, 1), (128, 1, 8)):
+    for launch in ((32, 4, 1), (256, 1, 1), (128, 1, 8), (32, 8, 6), (32, 16, 1), (32, 32, 1)):
         got = _run(w, 80, launch=launch, splits=[25, 55])
         for f in ref:
             assert np.array_equal(ref[f], got[f]), (launch, f)
