@@ -1,0 +1,39 @@
+"""The stylized-fact statistics of the composition sweep on traces whose
+answers are known in closed form."""
+import numpy as np
+
+from paper_2606_21784_gb300 import dynamics
+
+
+def _trace(prices, volume=10):
+    p = np.asarray(prices, np.int32)
+    t = np.zeros((1 if p.ndim == 1 else p.shape[0], p.shape[-1], 2), np.int32)
+    t[:, :, 0] = p
+    t[:, :, 1] = np.where(p >= 0, volume, 0)
+    return t
+
+
+def test_constant_price_has_no_volatility():
+    f = dynamics.facts(_trace([64] * 50), L=128)
+    assert f["volatility"] == 0 and f["volume_per_step"] == 10 and f["mean_price"] == 64
+
+
+def test_bid_ask_bounce_has_lag1_autocorrelation_minus_one():
+    f = dynamics.facts(_trace([65, 64] * 200), L=128)  # returns +1, -1, +1, ...
+    assert abs(f["acf_r"][0] + 1) < 0.01 and abs(f["acf_r"][1] - 1) < 0.01
+    assert abs(f["volatility"] - 1) < 0.01
+
+
+def test_symmetric_steps_have_excess_kurtosis_minus_two():
+    rng = np.random.default_rng(0)
+    steps = rng.choice([-1, 1], size=(20, 2000))
+    prices = 5000 + np.cumsum(steps, axis=1)  # stays on the grid: no step reads as a missing trade
+    f = dynamics.facts(_trace(prices), L=10000)
+    assert abs(f["excess_kurtosis"] + 2) < 0.05  # a +/-1 coin has kurtosis 1
+    assert abs(f["acf_r"][0]) < 0.02 and abs(f["acf_abs_r"][0]) < 0.02
+
+
+def test_steps_without_trade_keep_the_last_price():
+    f = dynamics.facts(_trace([66, -1, -1, 66, 70]), L=128)  # returns 2, 0, 0, 0, 4 from L/2 = 64
+    assert f["volume_per_step"] == 6.0  # 10 on three trading steps out of five
+    assert abs(f["mean_price"] - (66 + 66 + 66 + 66 + 70) / 5) < 1e-12

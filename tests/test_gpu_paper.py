@@ -102,3 +102,15 @@ def test_full_size_peak_workload_sampled_markets():
         _check_market(w["params"], gs, m, 128, 1024, w["S"], trace=False)
     # every market traded and stayed on the grid
     assert gs["trades"].min() > 0 and 0 <= gs["last_tick"].min() and gs["last_tick"].max() < 128
+
+
+def test_composition_sweep_runs_and_momentum_raises_volatility():
+    from paper_2606_21784_gb300 import dynamics
+    r = dynamics.sweep(alphas=[0.0, 0.15, 0.5], M=16, S=400)
+    f = r["facts"]
+    assert f[0.5]["volatility"] > 1.5 * f[0.0]["volatility"] > 0
+    assert all(x["volume_per_step"] > 0 for x in f.values())
+    # the sweep's markets are the oracle's: one configuration's trace, bit-exact
+    w = wl.workload("paper_8192_256", M=16, L=128, A=256, mom_pct=50, maker_pct=15)
+    gs = _run(w, 400)
+    _check_market(w["params"], gs, 5, 128, 256, 400)
