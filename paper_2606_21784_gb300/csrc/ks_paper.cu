@@ -89,11 +89,10 @@ struct PaperSmem {
   int32_t* bbk;                  // [2][2] best bid (max) / best ask (min) of the resting book per parity
   int32_t* wD;                   // [32]
   int32_t* wS;                   // [32]
-  int32_t* rem;                  // [2]
 };
 
 __host__ __device__ inline size_t paper_smem_bytes(int L) {
-  return (size_t)4 * 2 * book_len(L) + 8 * 8 + 4 * 4 + 4 * 64 + 16;
+  return (size_t)4 * 2 * book_len(L) + 8 * 8 + 4 * 4 + 4 * 64;
 }
 
 __device__ __forceinline__ PaperSmem paper_carve(unsigned char* raw, int L) {
@@ -103,7 +102,6 @@ __device__ __forceinline__ PaperSmem paper_carve(unsigned char* raw, int L) {
   s.bbk = reinterpret_cast<int32_t*>(s.kx + 8);
   s.wD = s.bbk + 4;
   s.wS = s.wD + 32;
-  s.rem = s.wS + 32;
   return s;
 }
 
