@@ -55,14 +55,39 @@ def parse():
 PLAIN_SOURCES = ("ks_device.cuh", "ks_internal.h", "ks_market.cuh", "ks_plain.cuh")
 
 
-def kernel_source_hash() -> str:
-    """Hash of the plain kernel's sources; ncu counters are only valid for the kernel they were taken on."""
+def strip_comments(src: str) -> str:
+    """C/C++ source without comments and whitespace (string and character literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            if not c.isspace():
+                out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def kernel_source_hash(d: str | None = None) -> str:
+    """Hash of the plain kernel's code (comments and whitespace removed); ncu counters are
+    only valid for the kernel they were taken on."""
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2606_21784_gb300", "csrc")
+    d = d or os.path.join(ROOT, "paper_2606_21784_gb300", "csrc")
     for fn in sorted(os.listdir(d)):
         if fn in PLAIN_SOURCES or fn.startswith("ks_plain_nt"):
             h.update(fn.encode())
-            h.update(open(os.path.join(d, fn), "rb").read())
+            h.update(strip_comments(open(os.path.join(d, fn), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -277,7 +302,7 @@ def compare_forms(ks, workloads, stream, plain_rate):
         out["batched_20000_tuned"] = {"error": str(e)[:200]}
     ens.close()
     out.update(learned_forms(ks, workloads, stream))
-    out["paper_table_ii"] = paper_forms(ks, workloads, stream)
+    out["paper_table_iii"] = paper_forms(ks, workloads, stream)
     out["paper_stylized_facts"] = stylized_facts()
     return out
 
@@ -297,8 +322,8 @@ def stylized_facts():
             "paper_values": {k: {str(a): v for a, v in d.items()} for k, d in dynamics.PAPER_FACTS.items()}}
 
 
-# the paper's Table II (RTX 5090, its own agents, L=128, S=500): agent-events/s
-PAPER_TABLE_II = {(64, 256): 3.61e9, (256, 256): 1.35e10, (1024, 256): 3.69e10, (4096, 256): 4.73e10,
+# the paper's Table III (RTX 5090, its own agents, L=128, S=500): agent-events/s
+PAPER_TABLE_III = {(64, 256): 3.61e9, (256, 256): 1.35e10, (1024, 256): 3.69e10, (4096, 256): 4.73e10,
                   (16384, 256): 5.39e10, (8192, 16): 8.41e9, (8192, 64): 2.84e10, (8192, 256): 5.16e10,
                   (8192, 1024): 5.47e10}
 
@@ -314,7 +339,7 @@ def paper_forms(ks, workloads, stream, reps: int = 3):
 
     from paper_2606_21784_gb300 import autotune
     out = {}
-    for (M, A), ref in PAPER_TABLE_II.items():
+    for (M, A), ref in PAPER_TABLE_III.items():
         w = workloads.workload("paper_8192_256", M=M, A=A)
         ens = ks.PaperEnsemble(w)
         launch = autotune.apply(ens, w)
@@ -624,8 +649,8 @@ def run_paper(args, w, rank, world, dev):
                "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
                "gpu_launches": 2 * args.steps, "roofline": None, "clocks": clocks,
-               "paper_context": {"value": PAPER_TABLE_II.get((int(w["M"]), int(w["A"]))),
-                                 "hardware": "RTX 5090 (sm_120), Table II"}}
+               "paper_context": {"value": PAPER_TABLE_III.get((int(w["M"]), int(w["A"]))),
+                                 "hardware": "RTX 5090 (sm_120), Table III"}}
         print(json.dumps(out), flush=True)
     ens.close()
     sharding.finalize()

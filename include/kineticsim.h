@@ -152,7 +152,7 @@ typedef struct ks_state_view {
   int64_t* sum_price;    /* [M] sum of p* over trading steps                      */
   int64_t* sum_volume;   /* [M] sum of V* over steps                             */
   uint64_t* trace_hash;  /* [M] h <- mix64(h ^ (p*<<32 | V*) ^ step*0x9E3779B97F4A7C15),
-                            mix64 = SplitMix64 finaliser (Sec. III-F); p* = -1 when V* = 0 */
+                            mix64 = SplitMix64 finaliser (Sec. III-G); p* = -1 when V* = 0 */
   uint64_t* step;        /* [1] absolute step counter                            */
   int32_t* trace;        /* [trace_markets*trace_steps*2] (p*, V*) per market and step */
 } ks_state_view;
@@ -277,7 +277,7 @@ ks_status ks_destroy(ks_ensemble* e);
  *    sells at round(mid + maker_half_spread); never marketable.
  * Quantity 1 + floor(qmax u).  round() is to the nearest integer with ties to
  * even; ticks are clamped to [0, L).
- * Draws (SplitMix64, Sec. III-F): u(gid, s, c) = mix64(seed +
+ * Draws (SplitMix64, Sec. III-G): u(gid, s, c) = mix64(seed +
  * 0x9E3779B97F4A7C15 * (gid * 2^35 + 8 s + c)), the output number
  * gid * 2^35 + 8 s + c of the generator with state `seed`, gid = (market_base
  * + m) * A + a.  Channel 0: high word = marketable draw (marketable iff below

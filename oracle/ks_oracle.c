@@ -21,7 +21,7 @@
  *    draws keyed by (seed, market, agent, step)); see the function comments.
  *  - Philox4x32-10 is written from Salmon, Moraes, Dror and Shaw, "Parallel
  *    random numbers: as easy as 1, 2, 3", SC'11.
- *  - The trace hash uses the SplitMix64 finaliser printed in Sec. III-F.
+ *  - The trace hash uses the SplitMix64 finaliser printed in Sec. III-G.
  *  - The MLP policy (32 -> 64 -> 64 -> 3 side + 33 offset + 1 log-qty logits,
  *    ReLU) forward and backward are plain fp64 loops; the behaviour-cloning
  *    loss is cross-entropy on side and offset plus squared error on
@@ -85,7 +85,7 @@ static int32_t ko_clamp(int64_t x, int32_t lo, int32_t hi) {
   return (int32_t)x;
 }
 
-/* SplitMix64 finaliser (Sec. III-F) used to fold the clearing trace. */
+/* SplitMix64 finaliser (Sec. III-G) used to fold the clearing trace. */
 static uint64_t ko_mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
@@ -705,7 +705,7 @@ done:
 /* ======================================================================== */
 /* The paper's own agents (Sec. III-C, "Agent Decision and Order            */
 /* Aggregation") on a tick-aggregated book with SplitMix64 draws (Sec.      */
-/* III-F).  Readings where the paper is silent (each marked READING):        */
+/* III-G).  Readings where the paper is silent (each marked READING):        */
 /*  - draws: u(gid, s, c) = mix64(seed + 0x9E3779B97F4A7C15 * (gid * 2^35 +   */
 /*    8 s + c)) mod 2^64, i.e. output number gid*2^35 + 8s + c of the         */
 /*    SplitMix64 generator with state `seed` (Steele, Lea, Flood, OOPSLA      */

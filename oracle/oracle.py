@@ -429,7 +429,7 @@ def simulate(params: dict, m: int, L: int, A: int, steps: int, replay=None, mlp_
 
 
 # ---------------------------------------------------------------------------
-# The paper's own agents on a tick-aggregated book (Sec. III-C, III-F)
+# The paper's own agents on a tick-aggregated book (Sec. III-C, III-G)
 # ---------------------------------------------------------------------------
 def make_paper_params(p: dict) -> PaperParams:
     return PaperParams(int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(p["noise_halfwidth"]), int(p["p_mkt_q32"]),

@@ -230,7 +230,7 @@ __device__ __forceinline__ uint32_t decide_tab(uint32_t slot, uint4 w, const Cla
   return (slot & W_STATIC) | qty | (sell31 >> 23) | ((uint32_t)tick << W_TICK_SHIFT);
 }
 
-// SplitMix64 finaliser (Sec. III-F) folding the per-step clearing trace.
+// SplitMix64 finaliser (Sec. III-G) folding the per-step clearing trace.
 __device__ __forceinline__ uint64_t trace_mix(uint64_t h, uint32_t step, int32_t pstar, int32_t vol) {
   uint64_t z = h ^ (((uint64_t)(uint32_t)pstar << 32) | (uint64_t)(uint32_t)vol) ^
                ((uint64_t)step * 0x9E3779B97F4A7C15ull);

@@ -26,7 +26,7 @@
 //   agent index at the marginal ticks, Sec. IV-C) and draws step s+1's
 //   cancellation and new order (Philox4x32-10).                  (Phase 5)
 // Global memory is touched only when a market is loaded and stored, so the
-// traffic does not grow with the number of steps (Sec. III-E).
+// traffic does not grow with the number of steps (Sec. III-F).
 #pragma once
 
 #include <stdint.h>

@@ -1,5 +1,5 @@
 // ks_paper.cu -- the paper's own agent model (Sec. III-C NOISE / MOMENTUM /
-// MAKER agents around the mid price, SplitMix64 draws of Sec. III-F) on a
+// MAKER agents around the mid price, SplitMix64 draws of Sec. III-G) on a
 // tick-aggregated book, as a persistent kernel and its C ABI (ks_paper_*).
 //
 // A group of GT threads (a whole CTA, or one warp of a 128-thread CTA for
@@ -63,7 +63,7 @@ struct PaperParams {
   uint64_t* step;
 };
 
-// ---- SplitMix64 (Steele, Lea, Flood, OOPSLA 2014; mixer as printed in Sec. III-F) ----
+// ---- SplitMix64 (Steele, Lea, Flood, OOPSLA 2014; mixer as printed in Sec. III-G) ----
 constexpr uint64_t SM64_GAMMA = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t SM64_GID = SM64_GAMMA << 35;  // counter step of one agent id (gid * 2^35)
 

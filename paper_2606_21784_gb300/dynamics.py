@@ -1,4 +1,4 @@
-"""Market-composition sweep of the paper's own agent model (Sec. V,
+"""Market-composition sweep of the paper's own agent model (Sec. IV-J,
 "Emergent Market Dynamics and Parameter Sweeps").
 
 The fraction of momentum agents alpha_mom runs from 0 to 0.70 in steps of
@@ -22,7 +22,7 @@ import numpy as np
 from . import kineticsim as ks
 from . import workloads
 
-# The paper's reported values (Sec. V): volatility 0.95 at alpha_mom = 0 and
+# The paper's reported values (Sec. IV-J): volatility 0.95 at alpha_mom = 0 and
 # 25.19 at 0.70; volume per step 169.0 at 0; ACF at lag 1 of r -0.34 and of
 # |r| 0.18 at alpha_mom = 0.15.
 PAPER_FACTS = {"volatility": {0.0: 0.95, 0.70: 25.19}, "volume_per_step": {0.0: 169.0},

@@ -1,6 +1,6 @@
 """Pins of the oracle's paper-agent mode (the paper's own NOISE / MOMENTUM /
 MAKER agents on a tick-aggregated book, Sec. III-C, with SplitMix64 draws,
-Sec. III-F).
+Sec. III-G).
 
 Expected values come from the published SplitMix64 sequence, from the rules
 as the paper states them (checked as properties of many draws, not by

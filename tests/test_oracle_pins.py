@@ -270,7 +270,7 @@ def test_trace_hash_and_stats_fold_the_trace():
 def test_zero_intelligence_price_stays_near_centre():
     # Symmetric ZI order flow around the last price keeps the clearing price
     # near its start L/2 (the paper's mean clearing price sits at about L/2,
-    # Table I); with L = 256 the mean over 64 markets stays within a few ticks.
+    # Table II); with L = 256 the mean over 64 markets stays within a few ticks.
     params = _small("plain_zi_64")
     means = []
     for m in range(16):
