@@ -328,13 +328,38 @@ PAPER_TABLE_III = {(64, 256): 3.61e9, (256, 256): 1.35e10, (1024, 256): 3.69e10,
                   (8192, 1024): 5.47e10}
 
 
+# the paper's Naive CUDA engine on the same shapes (Table III)
+PAPER_NAIVE = {(64, 256): 6.39e7, (256, 256): 1.95e8, (1024, 256): 7.56e8, (4096, 256): 3.09e9,
+               (16384, 256): 1.14e10, (8192, 16): 8.01e8, (8192, 64): 2.58e9, (8192, 256): 6.13e9,
+               (8192, 1024): 8.89e9}
+# median per-step latency at 4096 markets x 256 agents (Sec. IV-I), microseconds
+PAPER_STEP_LATENCY_US = {"persistent": 22.1, "naive": 339.3}
+
+
+def _time_best(run, stream, reps):
+    import torch
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
 def paper_forms(ks, workloads, stream, reps: int = 3):
     """The paper's own agent model (tick-aggregated book, NOISE / MOMENTUM /
     MAKER agents, SplitMix64 draws) on every shape of the paper's throughput
     table (markets sweep at A=256, agents sweep at 8192 markets; L=128,
     S=500), each with its tuned launch, beside the paper's RTX 5090 numbers
     (whose agent constants are unpublished: the comparison is of throughput
-    on the same shapes, not of identical simulations)."""
+    on the same shapes, not of identical simulations).  Each shape also runs
+    the naive engine (one thread per market, book in global memory, one
+    launch per step): the paper's ablation of its two design choices."""
     import torch
 
     from paper_2606_21784_gb300 import autotune
@@ -346,20 +371,23 @@ def paper_forms(ks, workloads, stream, reps: int = 3):
         S = int(w["S"])
         ens.step(50, stream)
         torch.cuda.synchronize()
-        best = None
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ens.step(S, stream)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            best = ms if best is None else min(best, ms)
-        rate = float(M) * A * S / (best / 1e3)
+        best = _time_best(lambda: ens.step(S, stream), stream, reps)
+        ens.step_naive(5, stream)
+        torch.cuda.synchronize()
+        naive = _time_best(lambda: ens.step_naive(S, stream), stream, reps)
+        if ens.sync(timeout_ms=600_000) != ks.KS_OK:
+            raise RuntimeError("paper ensemble reported a device error")
+        ev = float(M) * A * S
+        rate, nrate = ev / (best / 1e3), ev / (naive / 1e3)
+        pn = PAPER_NAIVE[(M, A)]
         out[f"M{M}_A{A}"] = {"events_per_s": rate, "ms_per_run": best, "paper_rtx5090": ref,
                              "ratio_to_paper": rate / ref,
-                             "launch": {k: launch[k] for k in ("threads", "agents_per_thread", "min_ctas")}}
+                             "launch": {k: launch[k] for k in ("threads", "agents_per_thread", "min_ctas")},
+                             "naive_events_per_s": nrate, "speedup_over_naive": rate / nrate,
+                             "paper_naive": pn, "paper_speedup_over_naive": ref / pn}
+        if (M, A) == (4096, 256):
+            out["step_latency_us_4096x256"] = {"persistent": 1e3 * best / S, "naive": 1e3 * naive / S,
+                                               "paper": PAPER_STEP_LATENCY_US}
         ens.close()
     return out
 

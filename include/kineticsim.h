@@ -335,6 +335,14 @@ ks_status ks_paper_workspace_size(const ks_paper_config* cfg, size_t* bytes);
 ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws_bytes, void* stream,
                           ks_paper_ensemble** out);
 ks_status ks_paper_step_n(ks_paper_ensemble* e, uint32_t n_steps, void* stream);
+/* The naive engine of the paper's work-depth comparison and ablation (Sec.
+ * III-F, Sec. IV-I): steps [s, s+n) of the same ensemble as n launches of one
+ * thread per market, the book kept in global memory (the resting rows are read
+ * and the residual written back every step) and clearing by one serial sweep.
+ * Same model and draws as ks_paper_step_n, so the two give bit-identical state
+ * and may be mixed on one ensemble.  Asynchronous on `stream`; no shape limit
+ * on A beyond the configuration's. */
+ks_status ks_paper_step_n_naive(ks_paper_ensemble* e, uint32_t n_steps, void* stream);
 ks_status ks_paper_read_state(ks_paper_ensemble* e, const ks_paper_state_view* dst, void* stream);
 ks_status ks_paper_set_launch(ks_paper_ensemble* e, int32_t threads, int32_t agents_per_thread, int32_t min_ctas);
 ks_status ks_paper_get_launch(const ks_paper_ensemble* e, int32_t* threads, int32_t* agents_per_thread,

@@ -82,6 +82,48 @@ __device__ __forceinline__ int round_even_2p33(int32_t hi, uint32_t lo) {
   return q + (up ? 1 : 0);
 }
 
+// ---- one agent's decision (Sec. III-C), shared by the persistent and the naive kernel ----
+// abase = seed + gamma * gid * 2^35 is the agent's counter origin.
+
+// Class of the agent: percentile of channel 2 at step 0 (MAKER below maker_pct,
+// then MOMENTUM below maker_pct + mom_pct, else NOISE).
+__device__ __forceinline__ uint32_t paper_class(const PaperParams& P, uint64_t abase) {
+  const uint32_t w = (uint32_t)(sm64_mix(abase + 2ull * SM64_GAMMA) >> 32);
+  const uint32_t pct = __umulhi(w, 100u);
+  return pct < P.maker_pct ? PAPER_MAKER : (pct < P.maker_pct + P.mom_pct ? PAPER_MOMENTUM : PAPER_NOISE);
+}
+
+struct PaperOrder {
+  int tick, q;
+  uint32_t sell;
+};
+
+// Order of agent a (class c) at step s: c0 = abase + gamma * 8s is the counter
+// of channel 0 (channel 1 follows it); mid2 = 2 * mid, ret the sign of the mid's
+// last change.
+__device__ __forceinline__ PaperOrder paper_order(const PaperParams& P, uint64_t c0, uint32_t c, uint32_t a,
+                                                  uint32_t s, int mid2, int ret) {
+  const uint64_t u0 = sm64_mix(c0);
+  const uint64_t u1 = sm64_mix(c0 + SM64_GAMMA);
+  const uint32_t w_mkt = (uint32_t)(u0 >> 32), w_coin = (uint32_t)u0;
+  const uint32_t w_price = (uint32_t)(u1 >> 32), w_qty = (uint32_t)u1;
+  const bool maker = c == PAPER_MAKER;
+  const bool mom = c == PAPER_MOMENTUM;
+  const uint32_t coin = w_coin >> 31;
+  PaperOrder o;
+  o.sell = maker ? (a + s) & 1u : ((mom && ret != 0) ? (uint32_t)(ret < 0) : coin);
+  const bool mkt = !maker && w_mkt < P.p_mkt;
+  // round(mid + eta) (noise), round(mid +/- 1) (momentum), round(mid -/+ D) (maker):
+  // the value times 2^33 is base2 * 2^32 + scale * w
+  const int base2 = maker ? mid2 + (o.sell ? P.maker2 : -P.maker2) : (mom ? mid2 + (o.sell ? -2 : 2) : mid2 - P.noise2);
+  const uint32_t scale = (maker || mom) ? 0u : P.eta4;
+  const uint64_t prod = (uint64_t)scale * (uint64_t)w_price;
+  const int rounded = round_even_2p33(base2 + (int32_t)(prod >> 32), (uint32_t)prod);
+  o.tick = mkt ? (o.sell ? 0 : P.L - 1) : min(max(rounded, 0), P.L - 1);
+  o.q = 1 + (int)__umulhi(w_qty, P.qmax);
+  return o;
+}
+
 // Shared memory of one market.
 struct PaperSmem {
   int32_t* book;                 // 2 * book_len(L) words
@@ -160,12 +202,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   using ClassWord = typename std::conditional<(AK > 16), uint64_t, uint32_t>::type;
   ClassWord cls = 0;
 #pragma unroll
-  for (int k = 0; k < AK; ++k) {
-    const uint32_t w = (uint32_t)(sm64_mix(abase + SM64_GID * (uint64_t)k + 2ull * SM64_GAMMA) >> 32);
-    const uint32_t pct = __umulhi(w, 100u);
-    const uint32_t c = pct < P.maker_pct ? PAPER_MAKER : (pct < P.maker_pct + P.mom_pct ? PAPER_MOMENTUM : PAPER_NOISE);
-    cls |= (ClassWord)c << (2 * k);
-  }
+  for (int k = 0; k < AK; ++k) cls |= (ClassWord)paper_class(P, abase + SM64_GID * (uint64_t)k) << (2 * k);
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
   const bool traced = m < P.trace_markets;
   gsync<NT>(bar);
@@ -182,27 +219,9 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
 #pragma unroll
     for (int k = 0; k < AK; ++k) {
       const int a = t * AK + k;
-      const uint64_t c0 = sbase + SM64_GID * (uint64_t)k;
-      const uint64_t u0 = sm64_mix(c0);
-      const uint64_t u1 = sm64_mix(c0 + SM64_GAMMA);
-      const uint32_t w_mkt = (uint32_t)(u0 >> 32), w_coin = (uint32_t)u0;
-      const uint32_t w_price = (uint32_t)(u1 >> 32), w_qty = (uint32_t)u1;
-      const uint32_t c = (uint32_t)(cls >> (2 * k)) & 3u;
-      const bool maker = c == PAPER_MAKER;
-      const bool mom = c == PAPER_MOMENTUM;
-      const uint32_t coin = w_coin >> 31;
-      const uint32_t sell = maker ? ((uint32_t)a + s) & 1u : ((mom && ret != 0) ? (uint32_t)(ret < 0) : coin);
-      const bool mkt = !maker && w_mkt < P.p_mkt;
-      // round(mid + eta) (noise), round(mid +/- 1) (momentum), round(mid -/+ D) (maker):
-      // the value times 2^33 is base2 * 2^32 + scale * w
-      const int base2 = maker ? mid2 + (sell ? P.maker2 : -P.maker2)
-                              : (mom ? mid2 + (sell ? -2 : 2) : mid2 - P.noise2);
-      const uint32_t scale = (maker || mom) ? 0u : P.eta4;
-      const uint64_t prod = (uint64_t)scale * (uint64_t)w_price;
-      const int rounded = round_even_2p33(base2 + (int32_t)(prod >> 32), (uint32_t)prod);
-      const int tick = mkt ? (sell ? 0 : L - 1) : min(max(rounded, 0), L - 1);
-      const int q = 1 + (int)__umulhi(w_qty, P.qmax);
-      red_add_if(book_s + 4u * (uint32_t)(2 * tick + (int)sell), q, a < A);
+      const PaperOrder o = paper_order(P, sbase + SM64_GID * (uint64_t)k, (uint32_t)(cls >> (2 * k)) & 3u,
+                                       (uint32_t)a, s, mid2, ret);
+      red_add_if(book_s + 4u * (uint32_t)(2 * o.tick + (int)o.sell), o.q, a < A);
     }
     gsync<NT>(bar);  // B1: the step's orders are in the book
 
@@ -433,6 +452,115 @@ __global__ void paper_init_kernel(PaperParams P) {
 
 __global__ void paper_step_bump(uint64_t* step, uint32_t n) { *step += n; }
 
+// ---- the naive engine: one thread per market, one launch per step (Sec. III-F, Sec. IV-I) ----
+// Same model, decisions and draws as paper_kernel (paper_class / paper_order),
+// without its two design choices: the book stays in global memory (each step
+// reads the resting rows for the best bid / ask, aggregates the step's orders
+// into the same rows and writes the residual back: Theta(L) loads and stores
+// per market and step) and clearing is one serial sweep per market (scans and
+// argmax in one upward pass from the total demand, then the residual pass).
+constexpr int PAPER_NAIVE_THREADS = 128;
+
+__global__ void __launch_bounds__(PAPER_NAIVE_THREADS) paper_naive_kernel(PaperParams P) {
+  const uint32_t m = blockIdx.x * PAPER_NAIVE_THREADS + threadIdx.x;
+  if (m >= P.M) return;
+  const uint32_t s = (uint32_t)(*P.step);
+  const int L = P.L, A = P.A;
+  int32_t* bid = P.bid + (size_t)m * (size_t)L;
+  int32_t* ask = P.ask + (size_t)m * (size_t)L;
+  int32_t* mi = P.mi32 + (size_t)m * PMI32;
+  int64_t* m64 = P.mi64 + (size_t)m * PMI64;
+
+  // mid of the resting book; the rows are then reused for the step's orders
+  int bb = -1, ba = L;
+  for (int p = 0; p < L; ++p) {
+    if (bid[p] > 0) bb = p;
+    if (ask[p] > 0 && ba == L) ba = p;
+    bid[p] = 0;
+    ask[p] = 0;
+  }
+  const int last0 = mi[0];
+  const int mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * last0;
+  const int pmid2 = mi[1];
+  const int ret = (mid2 > pmid2) - (mid2 < pmid2);
+
+  // orders of step s, agent by agent
+  const uint64_t mbase = P.seed + SM64_GID * ((uint64_t)(P.market_base + m) * (uint64_t)A);
+  const uint64_t sofs = SM64_GAMMA * (8ull * (uint64_t)s);
+  int Dtot = 0;
+  for (int a = 0; a < A; ++a) {
+    const uint64_t abase = mbase + SM64_GID * (uint64_t)a;
+    const PaperOrder o = paper_order(P, abase + sofs, paper_class(P, abase), (uint32_t)a, s, mid2, ret);
+    if (o.sell) {
+      ask[o.tick] += o.q;
+    } else {
+      bid[o.tick] += o.q;
+      Dtot += o.q;
+    }
+  }
+
+  // clearing (Eq. 1-2): D = D_cum[p] and S = S_cum[p] in one upward sweep
+  const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
+  int D = Dtot, Sb = 0;
+  int bestV = -1, lo = 0, hi = 0;
+  int v1 = -1, imb1 = 0, p1 = 0;
+  for (int p = 0; p < L; ++p) {
+    const int S = Sb + ask[p];
+    const int v = min(D, S);
+    if (v > bestV) {
+      bestV = v;
+      lo = p;
+    }
+    if (v >= bestV) hi = p;
+    if (tie1) {
+      const int imb = min(abs(D - S), (1 << 22) - 1);
+      if (v > v1 || (v == v1 && imb < imb1)) {
+        v1 = v;
+        imb1 = imb;
+        p1 = p;
+      }
+    }
+    D -= bid[p];
+    Sb = S;
+  }
+  const int vstar = max(bestV, 0);
+  const bool trade = vstar > 0;
+  const int pstar = tie1 ? p1 : lo;
+
+  // residual: buys fill from the top down to the highest maximiser, sells from
+  // the bottom up to the lowest one (the marginal ticks, rationed)
+  if (trade) {
+    D = Dtot;
+    Sb = 0;
+    for (int p = 0; p < L; ++p) {
+      const int b = bid[p], sq = ask[p];
+      const int rb = vstar - (D - b);
+      const int rs = vstar - Sb;
+      bid[p] = p > hi ? 0 : (p == hi ? b - rb : b);
+      ask[p] = p < lo ? 0 : (p == lo ? sq - rs : sq);
+      D -= b;
+      Sb += sq;
+    }
+  }
+
+  // market scalars
+  const int pt = trade ? pstar : -1;
+  mi[0] = trade ? pstar : last0;
+  mi[1] = mid2;
+  if (trade) {
+    mi[2] += 1;
+    m64[0] += pstar;
+  }
+  mi[3] = vstar;
+  m64[1] += vstar;
+  m64[2] = (int64_t)trace_mix((uint64_t)m64[2], s, pt, vstar);
+  if (m < P.trace_markets && s < P.trace_steps) {
+    int32_t* tr = P.trace + ((size_t)m * P.trace_steps + s) * 2;
+    tr[0] = pt;
+    tr[1] = vstar;
+  }
+}
+
 using PaperLaunchFn = void (*)(const PaperParams&, uint32_t, int, size_t, cudaStream_t);
 template <int NT, int GT, int AK, int MINB>
 void paper_launch(const PaperParams& p, uint32_t n, int grid, size_t smem, cudaStream_t st) {
@@ -451,7 +579,7 @@ struct PaperVariant {
     GT, AK, MB, NT, &paper_launch<NT, GT, AK, MB>, (const void*)&paper_kernel<NT, GT, AK, MB> \
   }
 // (threads per market, agents per thread, 1 = compiler's register choice,
-// else the register cap of that many resident CTAs; the capped shapes do not spill)
+// else the register cap of that many resident CTAs; 32 x 8 at 6 spills a few words)
 static const PaperVariant kPaperVariants[] = {
     KS_PV(128, 32, 1, 1),    KS_PV(128, 32, 2, 1),    KS_PV(128, 32, 4, 1),    KS_PV(128, 32, 1, 8),
     KS_PV(128, 32, 2, 8),    KS_PV(128, 32, 8, 1),    KS_PV(128, 32, 8, 6),    KS_PV(128, 32, 16, 1),
@@ -652,6 +780,19 @@ ks_status ks_paper_step_n(ks_paper_ensemble* e, uint32_t n_steps, void* stream) 
   KSP_CUDA(cudaGetLastError());
   paper_step_bump<<<1, 1, 0, st>>>(e->p.step, n_steps);
   KSP_CUDA(cudaGetLastError());
+  return KS_OK;
+}
+
+ks_status ks_paper_step_n_naive(ks_paper_ensemble* e, uint32_t n_steps, void* stream) {
+  if (!e) return fail(KS_ERR_INVALID_ARG, "ensemble is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = (int)((e->p.M + PAPER_NAIVE_THREADS - 1) / PAPER_NAIVE_THREADS);
+  for (uint32_t i = 0; i < n_steps; ++i) {
+    paper_naive_kernel<<<grid, PAPER_NAIVE_THREADS, 0, st>>>(e->p);
+    KSP_CUDA(cudaGetLastError());
+    paper_step_bump<<<1, 1, 0, st>>>(e->p.step, 1);
+    KSP_CUDA(cudaGetLastError());
+  }
   return KS_OK;
 }
 

@@ -31,8 +31,8 @@ EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_stat
            "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
            "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward", "ks_set_capture", "ks_bc_grad",
            "ks_adam_step", "ks_mlp_export", "ks_paper_workspace_size", "ks_paper_create", "ks_paper_step_n",
-           "ks_paper_read_state", "ks_paper_set_launch", "ks_paper_get_launch", "ks_paper_sync",
-           "ks_paper_destroy")
+           "ks_paper_step_n_naive", "ks_paper_read_state", "ks_paper_set_launch", "ks_paper_get_launch",
+           "ks_paper_sync", "ks_paper_destroy")
 KS_MLP_NPARAM = 8677
 
 KS_RECORD_WORDS = 22
@@ -166,6 +166,7 @@ def load(build_if_missing: bool = True):
         "ks_paper_workspace_size": ([P(ks_paper_config), P(ctypes.c_size_t)], ctypes.c_int),
         "ks_paper_create": ([P(ks_paper_config), vp, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
         "ks_paper_step_n": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
+        "ks_paper_step_n_naive": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
         "ks_paper_read_state": ([vp, P(ks_paper_state_view), vp], ctypes.c_int),
         "ks_paper_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "ks_paper_get_launch": ([vp, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)], ctypes.c_int),
@@ -601,6 +602,10 @@ class PaperEnsemble:
 
     def step(self, n: int, stream=None):
         _check(load().ks_paper_step_n(self.handle, int(n), _stream_ptr(stream)), "ks_paper_step_n")
+
+    def step_naive(self, n: int, stream=None):
+        """n steps by the naive engine (one thread per market, one launch per step)."""
+        _check(load().ks_paper_step_n_naive(self.handle, int(n), _stream_ptr(stream)), "ks_paper_step_n_naive")
 
     def set_launch(self, threads: int, agents_per_thread: int, min_ctas: int = 1):
         _check(load().ks_paper_set_launch(self.handle, int(threads), int(agents_per_thread), int(min_ctas)),

@@ -114,3 +114,48 @@ def test_composition_sweep_runs_and_momentum_raises_volatility():
     w = wl.workload("paper_8192_256", M=16, L=128, A=256, mom_pct=50, maker_pct=15)
     gs = _run(w, 400)
     _check_market(w["params"], gs, 5, 128, 256, 400)
+
+
+def _run_engines(w, plan, trace=True):
+    """plan: list of (engine, n) with engine 'p' (persistent) or 'n' (naive)."""
+    steps = sum(n for _, n in plan)
+    ens = ks.PaperEnsemble(w, trace_markets=w["M"] if trace else 0, trace_steps=steps if trace else 0)
+    for eng, n in plan:
+        (ens.step if eng == "p" else ens.step_naive)(n)
+    assert ens.sync(timeout_ms=300_000) == ks.KS_OK
+    gs = ens.read_state()
+    ens.close()
+    return gs
+
+
+@pytest.mark.parametrize("L,A,over", [(128, 256, {}), (100, 300, {}), (64, 1024, {}), (96, 200, dict(tie_rule=1)),
+                                      (7, 3, dict(noise_halfwidth=4, maker_half_spread=1)), (128, 0, {})])
+def test_naive_engine_matches_the_oracle(L, A, over):
+    """The naive engine (one thread per market, book in global memory, serial
+    clearing) against the oracle: every market and step, bit-exact."""
+    w = wl.workload("paper_8192_256", M=21, L=L, A=A, **over)
+    steps = 120
+    gs = _run_engines(w, [("n", steps)])
+    assert int(gs["step"][0]) == steps
+    for m in range(w["M"]):
+        _check_market(w["params"], gs, m, L, A, steps)
+
+
+def test_engines_mix_on_one_ensemble():
+    w = wl.workload("paper_8192_256", M=300, L=128, A=256)
+    ref = _run_engines(w, [("p", 90)])
+    for plan in ([("n", 90)], [("p", 40), ("n", 30), ("p", 20)], [("n", 1), ("p", 88), ("n", 1)]):
+        got = _run_engines(w, plan)
+        for f in ref:
+            assert np.array_equal(ref[f], got[f]), (plan, f)
+
+
+def test_naive_engine_full_fixed_workload_equals_persistent():
+    """The paper's fixed workload (8192 markets x 256 agents, L=128, S=500):
+    the two engines leave identical state in every market."""
+    w = wl.workload("paper_8192_256")
+    a = _run_engines(w, [("p", w["S"])], trace=False)
+    b = _run_engines(w, [("n", w["S"])], trace=False)
+    for f in a:
+        assert np.array_equal(a[f], b[f]), f
+    _check_market(w["params"], b, 4321, 128, 256, w["S"], trace=False)
