@@ -723,6 +723,19 @@ done:
 /*    tick whenever the spread is odd, a ratchet that walks the price to the  */
 /*    top of the grid.  Ticks are clamped to [0, L).                           */
 /*  - the first step's previous mid is the opening mid L/2 (integer part).   */
+/*  - sliding window (Sec. III-A: the grid is a local window of L ticks      */
+/*    around the trading zone; the recentring rule is not given).  With      */
+/*    `window` set, absolute tick = base + window tick.  At the start of a    */
+/*    step, after the mid is found, the window moves when the mid is more    */
+/*    than L/4 from its centre c = L/2: by k = 2 floor((2 mid - 2c) / 4)     */
+/*    ticks, an even number, so that ties-to-even rounding in the window is  */
+/*    the same rounding in absolute ticks.  The mid and the last price move  */
+/*    with it (the sign of the mid change is taken before the move); the     */
+/*    resting book is not moved because the step's own orders replace it.    */
+/*    Orders beyond the window are clamped to its edge                       */
+/*    (executed as marketable); marketable orders go to the window's edges.  */
+/*    Traces then record the absolute last price after each step (carried   */
+/*    on steps without trade) and V*; Sum p* and the hash take absolute p*.  */
 /* ======================================================================== */
 #define KO_PAPER_NOISE 0
 #define KO_PAPER_MOMENTUM 1
@@ -737,7 +750,7 @@ typedef struct {
   int32_t mom_pct;           /* alpha_mom in percent                          */
   int32_t maker_pct;         /* alpha_maker in percent                        */
   int32_t tie_rule;
-  int32_t pad_;
+  int32_t window;            /* 1: sliding window with recentring            */
 } ko_paper_params;
 
 typedef struct {
@@ -748,6 +761,7 @@ typedef struct {
   int64_t sum_p;
   int64_t sum_v;
   uint64_t hash;
+  int64_t base;    /* absolute tick of window tick 0 (0 without a window)    */
 } ko_paper_market;
 
 /* floor(num / den) for den > 0 */
@@ -834,7 +848,8 @@ int ko_paper_run(const ko_paper_params* P, uint32_t market, int32_t L, int32_t A
   int64_t* scum = (int64_t*)calloc((size_t)L, sizeof(int64_t));
   int64_t* vol = (int64_t*)calloc((size_t)L, sizeof(int64_t));
   int32_t* cls = (int32_t*)calloc((size_t)(A > 0 ? A : 1), sizeof(int32_t));
-  if (!buy || !sell || !dcum || !scum || !vol || !cls) return -2;
+  int rc = 0;
+  if (!buy || !sell || !dcum || !scum || !vol || !cls) { rc = -2; goto done; }
   for (int32_t a = 0; a < A; ++a) cls[a] = ko_paper_class(P, (uint64_t)market * (uint64_t)A + (uint64_t)a);
   for (uint32_t j = 0; j < n; ++j) {
     uint32_t s = s0 + j;
@@ -846,6 +861,16 @@ int ko_paper_run(const ko_paper_params* P, uint32_t market, int32_t L, int32_t A
       if (ask[p] > 0) ba = p;
     int32_t mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * ms->last;
     int32_t ret = (mid2 > ms->mid2) - (mid2 < ms->mid2);
+    if (P->window) {
+      /* recentre when |mid - L/2| > L/4 (in half ticks: |mid2 - c2| > L/2) */
+      int32_t dev = mid2 - 2 * (L / 2);
+      if (dev > L / 2 || dev < -(L / 2)) {
+        int32_t k = 2 * (int32_t)ko_floor_div(dev, 4);
+        ms->base += k;
+        mid2 -= 2 * k;
+        ms->last -= k;
+      }
+    }
     /* the step's orders */
     for (int32_t p = 0; p < L; ++p) buy[p] = sell[p] = 0;
     for (int32_t a = 0; a < A; ++a) {
@@ -867,25 +892,27 @@ int ko_paper_run(const ko_paper_params* P, uint32_t market, int32_t L, int32_t A
         if (p < cr.p_sell) na = 0;
         else if (p == cr.p_sell) na = sell[p] - (cr.vstar - below_s);
       }
-      if (nb > 0x7FFFFFFF || na > 0x7FFFFFFF) return -3;
+      if (nb > 0x7FFFFFFF || na > 0x7FFFFFFF) { rc = -3; goto done; }
       bid[p] = (int32_t)nb;
       ask[p] = (int32_t)na;
     }
+    if (cr.vstar > 0x7FFFFFFF) { rc = -3; goto done; }
+    int32_t pabs = cr.vstar > 0 ? (int32_t)(ms->base + cr.pstar) : -1;  /* absolute p*, -1 without trade */
     if (cr.vstar > 0) {
       ms->last = cr.pstar;
       ms->trades += 1;
-      ms->sum_p += cr.pstar;
+      ms->sum_p += ms->base + cr.pstar;
     }
-    if (cr.vstar > 0x7FFFFFFF) return -3;
     ms->sum_v += cr.vstar;
     ms->last_v = (int32_t)cr.vstar;
     ms->mid2 = mid2;
-    ms->hash = ko_trace_hash_update(ms->hash, s, cr.pstar, (int32_t)cr.vstar);
+    ms->hash = ko_trace_hash_update(ms->hash, s, pabs, (int32_t)cr.vstar);
     if (trace) {
-      trace[2 * j] = cr.pstar;
+      trace[2 * j] = P->window ? (int32_t)(ms->base + ms->last) : pabs;
       trace[2 * j + 1] = (int32_t)cr.vstar;
     }
   }
+done:
   free(buy); free(sell); free(dcum); free(scum); free(vol); free(cls);
-  return 0;
+  return rc;
 }

@@ -94,13 +94,13 @@ MLP_IN, MLP_H, MLP_OUT, N_RAW, REC_WORDS = 32, 64, 37, 18, 22
 class PaperParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("noise_halfwidth", ctypes.c_int32), ("p_mkt_q32", ctypes.c_uint32),
                 ("qmax", ctypes.c_int32), ("maker_half_spread", ctypes.c_int32), ("mom_pct", ctypes.c_int32),
-                ("maker_pct", ctypes.c_int32), ("tie_rule", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("maker_pct", ctypes.c_int32), ("tie_rule", ctypes.c_int32), ("window", ctypes.c_int32)]
 
 
 class PaperMarket(ctypes.Structure):
     _fields_ = [("last", ctypes.c_int32), ("mid2", ctypes.c_int32), ("trades", ctypes.c_int32),
                 ("last_v", ctypes.c_int32), ("sum_p", ctypes.c_int64), ("sum_v", ctypes.c_int64),
-                ("hash", ctypes.c_uint64)]
+                ("hash", ctypes.c_uint64), ("base", ctypes.c_int64)]
 
 
 PAPER_NOISE, PAPER_MOMENTUM, PAPER_MAKER = 0, 1, 2
@@ -434,7 +434,7 @@ def simulate(params: dict, m: int, L: int, A: int, steps: int, replay=None, mlp_
 def make_paper_params(p: dict) -> PaperParams:
     return PaperParams(int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(p["noise_halfwidth"]), int(p["p_mkt_q32"]),
                        int(p["qmax"]), int(p["maker_half_spread"]), int(p["mom_pct"]), int(p["maker_pct"]),
-                       int(p.get("tie_rule", 0)), 0)
+                       int(p.get("tie_rule", 0)), int(p.get("window", 0)))
 
 
 def splitmix64_draw(seed: int, gid: int, step: int, channel: int) -> int:
@@ -466,7 +466,8 @@ class PaperBook:
     sc: PaperMarket = field(default_factory=PaperMarket)
 
     def scalars(self) -> dict:
-        return {k: int(getattr(self.sc, k)) for k in ("last", "mid2", "trades", "last_v", "sum_p", "sum_v", "hash")}
+        return {k: int(getattr(self.sc, k))
+                for k in ("last", "mid2", "trades", "last_v", "sum_p", "sum_v", "hash", "base")}
 
 
 def paper_init(market: int, L: int, A: int) -> PaperBook:

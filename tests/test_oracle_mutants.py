@@ -50,6 +50,13 @@ MUTANTS = {
                               "if (pct <= P->maker_pct) return KO_PAPER_MAKER;"),
     "paper_noise_width": ("int64_t num = ((int64_t)mid2 - 2 * D) * (1ll << 32) + 4 * D * (int64_t)w_price;",
                           "int64_t num = ((int64_t)mid2 - 2 * D) * (1ll << 32) + 2 * D * (int64_t)w_price;"),
+    # the sliding window
+    "window_odd_shift": ("int32_t k = 2 * (int32_t)ko_floor_div(dev, 4);", "int32_t k = (int32_t)ko_floor_div(dev, 2);"),
+    "window_last_not_moved": ("        ms->last -= k;\n", "        ms->last -= 0;\n"),
+    "window_trigger_band": ("if (dev > L / 2 || dev < -(L / 2)) {", "if (dev > L / 4 || dev < -(L / 4)) {"),
+    "window_trace_relative": ("trace[2 * j] = P->window ? (int32_t)(ms->base + ms->last) : pabs;",
+                              "trace[2 * j] = P->window ? ms->last : pabs;"),
+    "window_sum_relative": ("ms->sum_p += ms->base + cr.pstar;", "ms->sum_p += cr.pstar;"),
 }
 
 

@@ -10,6 +10,7 @@ call auction that fix the residual book uniquely.
 import os
 
 import numpy as np
+import pytest
 
 import oracle as o
 
@@ -212,3 +213,75 @@ def test_makers_keep_a_noise_market_near_the_opening_price():
         bk, tp, tv = o.paper_simulate(params, m, 128, 256, 300)
         means.append(tp[tp >= 0].mean())
     assert abs(np.mean(means) - 64) < 6
+
+
+# ---- sliding window (Sec. III-A) ------------------------------------------------------------
+def _drift_params(**over):
+    p = dict(seed=11, noise_halfwidth=4, p_mkt_q32=0, qmax=10, maker_half_spread=1, mom_pct=70, maker_pct=15,
+             tie_rule=0, window=0)
+    p.update(over)
+    return p
+
+
+def _carried_price(tp, start):
+    """Last clearing price after every step from a trace whose p* is -1 without trade."""
+    out, last = np.empty(len(tp), np.int64), start
+    for i, p in enumerate(tp):
+        last = p if p >= 0 else last
+        out[i] = last
+    return out
+
+
+@pytest.mark.parametrize("market,seed,mom,A", [(0, 7, 30, 200), (1, 7, 30, 200), (3, 5, 70, 200), (5, 7, 15, 200),
+                                               (1, 7, 30, 5), (3, 7, 70, 3)])
+def test_window_is_a_translation_of_a_large_grid(market, seed, mom, A):
+    """Without marketable orders no order reaches the edge of a 64-tick window
+    or of a 16384-tick grid, so the window must reproduce the large grid
+    exactly, translated by the difference of the opening prices (8160, even).
+    Momentum makes the price run away (up in market 1, down in market 0); the
+    thin markets (A = 3, 5) trade on fewer than half of the steps and often
+    leave a one-sided book, where the mid falls back to the last price."""
+    S, Lw, Lb = 1500, 64, 16384
+    off = Lb // 2 - Lw // 2
+    bw = o.paper_init(market, Lw, A)
+    tw_p, tw_v = o.paper_run(_drift_params(seed=seed, mom_pct=mom, window=1), bw, 0, S)
+    bb = o.paper_init(market, Lb, A)
+    tb_p, tb_v = o.paper_run(_drift_params(seed=seed, mom_pct=mom), bb, 0, S)
+    price_b = _carried_price(tb_p, Lb // 2)
+    assert 64 < price_b.min() and price_b.max() < Lb - 64          # the large grid never reached its edges
+    assert price_b.max() - price_b.min() > Lw                      # wider than the window: it had to move
+    assert np.array_equal(tw_v, tb_v)
+    assert np.array_equal(tw_p.astype(np.int64), price_b - off)   # absolute last price after every step
+    sw, sb = bw.scalars(), bb.scalars()
+    assert sw["trades"] == sb["trades"] and sw["sum_v"] == sb["sum_v"]
+    assert sw["sum_p"] == sb["sum_p"] - off * sb["trades"]
+    assert sw["base"] + sw["last"] == sb["last"] - off and sb["base"] == 0
+    # the resting book is the large grid's, seen through the window
+    lo = sw["base"] + off
+    assert np.array_equal(bw.bid, bb.bid[lo:lo + Lw]) and np.array_equal(bw.ask, bb.ask[lo:lo + Lw])
+    assert bb.bid.sum() == bw.bid.sum() and bb.ask.sum() == bw.ask.sum()
+
+
+def test_window_recentres_by_even_shifts_onto_the_centre():
+    """Step by step: the window moves only when the mid is more than L/4 from
+    the centre, always by an even number of ticks, and the moved mid lands
+    within one tick of the centre; otherwise it stays."""
+    L, A = 64, 150
+    params = _drift_params(mom_pct=60, p_mkt_q32=214748365, window=1)  # P_mkt = 0.05
+    bk = o.paper_init(2, L, A)
+    moves = 0
+    for s in range(1200):
+        base0 = bk.scalars()["base"]
+        # the mid this step starts from, in the current window
+        bb = int(np.nonzero(bk.bid)[0].max()) if bk.bid.any() else -1
+        ba = int(np.nonzero(bk.ask)[0].min()) if bk.ask.any() else L
+        mid2 = bb + ba if (bb >= 0 and ba < L) else 2 * bk.scalars()["last"]
+        o.paper_run(params, bk, s, 1)
+        k = bk.scalars()["base"] - base0
+        if abs(mid2 - L) > L // 2:
+            assert k % 2 == 0 and k != 0
+            assert bk.scalars()["mid2"] == mid2 - 2 * k and L <= mid2 - 2 * k < L + 4
+            moves += 1
+        else:
+            assert k == 0 and bk.scalars()["mid2"] == mid2
+    assert moves >= 5
