@@ -310,15 +310,21 @@ def compare_forms(ks, workloads, stream, plain_rate):
 def stylized_facts():
     """The paper's market-composition sweep (alpha_mom 0..0.70, alpha_maker
     0.15, 64 markets x 1000 steps, A=256, L=128) with the paper's own agent
-    model: volatility, excess kurtosis, volume per step and lag-1
-    autocorrelations per configuration, and the sweep's device time (the paper
-    quotes under 0.25 s for its sweep)."""
+    model, on a sliding window and on a fixed grid: volatility, excess
+    kurtosis, volume per step and lag-1 autocorrelations per configuration,
+    and the sweep's device time (the paper quotes under 0.25 s for its
+    sweep)."""
     from paper_2606_21784_gb300 import dynamics
+
+    def rows(r):
+        return {f"{a:.2f}": {"volatility": round(f["volatility"], 3), "price_std": round(f["price_std"], 2),
+                             "excess_kurtosis": round(f["excess_kurtosis"], 2),
+                             "volume_per_step": round(f["volume_per_step"], 1), "acf_r_lag1": round(f["acf_r"][0], 3),
+                             "acf_abs_r_lag1": round(f["acf_abs_r"][0], 3)} for a, f in r["facts"].items()}
     r = dynamics.sweep()
-    rows = {f"{a:.2f}": {"volatility": round(f["volatility"], 3), "excess_kurtosis": round(f["excess_kurtosis"], 2),
-                         "volume_per_step": round(f["volume_per_step"], 1), "acf_r_lag1": round(f["acf_r"][0], 3),
-                         "acf_abs_r_lag1": round(f["acf_abs_r"][0], 3)} for a, f in r["facts"].items()}
-    return {"by_alpha_mom": rows, "device_seconds": r["device_seconds"], "agent_events": r["agent_events"],
+    fixed = dynamics.sweep(window=False)
+    return {"by_alpha_mom": rows(r), "by_alpha_mom_fixed_grid": rows(fixed), "device_seconds": r["device_seconds"],
+            "agent_events": r["agent_events"],
             "paper_values": {k: {str(a): v for a, v in d.items()} for k, d in dynamics.PAPER_FACTS.items()}}
 
 

@@ -284,6 +284,16 @@ ks_status ks_destroy(ks_ensemble* e);
  * p_mkt_q32), low word = side coin (sell iff >= 2^31); channel 1: high word =
  * price draw w (eta = -D + 2 D w / 2^32), low word = quantity draw (u =
  * w / 2^32); channel 2 at step 0: high word = class draw.
+ * Sliding window (Sec. III-A; window = 1): the L ticks are a window onto an
+ * unbounded grid, absolute tick = window_base + window tick, window_base 0 at
+ * creation.  At the start of a step, once the mid is known, the window moves
+ * if the mid is more than L/4 from its centre L/2 (integer part): by
+ * k = 2 floor((2 mid - 2 (L/2)) / 4) ticks, an even number (so ties-to-even
+ * rounding is the same in both coordinates), which puts the mid back within
+ * one tick of the centre; the mid and the last price move with it.  Orders
+ * beyond the window are clamped to its edges, marketable orders go to them.
+ * The trace then records the absolute last price after each step (carried
+ * on steps without trade); sum_price and the trace hash take absolute p*.
  */
 typedef struct ks_paper_config {
   uint32_t n_markets;          /* M >= 1                                          */
@@ -300,7 +310,7 @@ typedef struct ks_paper_config {
   int32_t tie_rule;            /* ks_tie_rule                                     */
   uint32_t trace_markets;      /* markets 0..trace_markets-1 record (p*, V*) per step */
   uint32_t trace_steps;        /* trace capacity in steps                         */
-  int32_t pad_;
+  int32_t window;              /* 0: fixed grid; 1: sliding window (see above)    */
 } ks_paper_config;
 
 typedef struct ks_paper_ensemble ks_paper_ensemble;
@@ -316,9 +326,11 @@ typedef struct ks_paper_state_view {
   int32_t* last_volume;  /* [M] V* of the latest step                          */
   int64_t* sum_price;    /* [M] sum of p* over trading steps                   */
   int64_t* sum_volume;   /* [M] sum of V* over steps                           */
-  uint64_t* trace_hash;  /* [M] as ks_state_view::trace_hash                   */
+  uint64_t* trace_hash;  /* [M] as ks_state_view::trace_hash (absolute p*)     */
   uint64_t* step;        /* [1] absolute step counter                          */
-  int32_t* trace;        /* [trace_markets*trace_steps*2] (p*, V*) per market and step */
+  int32_t* trace;        /* [trace_markets*trace_steps*2] (p*, V*) per market and step;
+                            with a window, (absolute last price after the step, V*) */
+  int64_t* window_base;  /* [M] absolute tick of window tick 0 (0 on a fixed grid) */
 } ks_paper_state_view;
 
 /* Workspace bytes, creation (init kernel queued on `stream`), steps [s, s+n)

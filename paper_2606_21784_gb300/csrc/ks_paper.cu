@@ -40,7 +40,7 @@ constexpr int PAPER_NOISE = 0;
 constexpr int PAPER_MOMENTUM = 1;
 constexpr int PAPER_MAKER = 2;
 constexpr int PMI32 = 8;  // last, mid2, trades, last_v
-constexpr int PMI64 = 4;  // sum_p, sum_v, hash
+constexpr int PMI64 = 4;  // sum_p, sum_v, hash, window origin
 
 struct PaperParams {
   uint32_t M, market_base;
@@ -53,6 +53,7 @@ struct PaperParams {
   int32_t maker2;     // 2 * maker_half_spread
   uint32_t mom_pct, maker_pct;
   int32_t tie_rule;
+  int32_t window;     // 1: sliding window with recentring
   uint32_t trace_markets, trace_steps;
   int32_t* bid;       // [M][L]
   int32_t* ask;       // [M][L]
@@ -124,24 +125,37 @@ __device__ __forceinline__ PaperOrder paper_order(const PaperParams& P, uint64_t
   return o;
 }
 
+// Sliding window (Sec. III-A): when the mid (mid2 = 2 mid, window ticks) is
+// more than L/4 from the window's centre, the window moves by an even number
+// of ticks k = 2 floor((mid2 - 2 (L/2)) / 4) so that the mid is back on the
+// centre (even, so ties-to-even rounding is the same in window and absolute
+// ticks).  Returns k (0: no move).
+__device__ __forceinline__ int window_shift(int mid2, int L) {
+  const int dev = mid2 - 2 * (L / 2);
+  if (dev <= L / 2 && dev >= -(L / 2)) return 0;
+  return 2 * ((dev - (dev & 3)) / 4);  // dev & 3 = dev mod 4 in two's complement
+}
+
 // Shared memory of one market.
 struct PaperSmem {
   int32_t* book;                 // 2 * book_len(L) words
   unsigned long long* kx;        // [2][4] argmax keys per parity
+  int64_t* wbase;                // window origin (absolute tick of window tick 0); thread 0 only
   int32_t* bbk;                  // [2][2] best bid (max) / best ask (min) of the resting book per parity
   int32_t* wD;                   // [32]
   int32_t* wS;                   // [32]
 };
 
 __host__ __device__ inline size_t paper_smem_bytes(int L) {
-  return (size_t)4 * 2 * book_len(L) + 8 * 8 + 4 * 4 + 4 * 64;
+  return (size_t)4 * 2 * book_len(L) + 8 * 8 + 8 + 4 * 4 + 4 * 64;
 }
 
 __device__ __forceinline__ PaperSmem paper_carve(unsigned char* raw, int L) {
   PaperSmem s;
   s.book = reinterpret_cast<int32_t*>(raw);
   s.kx = reinterpret_cast<unsigned long long*>(raw + (size_t)4 * 2 * book_len(L));
-  s.bbk = reinterpret_cast<int32_t*>(s.kx + 8);
+  s.wbase = reinterpret_cast<int64_t*>(s.kx + 8);
+  s.bbk = reinterpret_cast<int32_t*>(s.wbase + 1);
   s.wD = s.bbk + 4;
   s.wS = s.wD + 32;
   return s;
@@ -195,6 +209,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   const int64_t* m64 = P.mi64 + (size_t)m * PMI64;
   int64_t sump = m64[0], sumv = m64[1];
   uint64_t hash = (uint64_t)m64[2];
+  if (t == 0) *sm.wbase = m64[3];
 
   // ---- agent classes (channel 2 of step 0), two bits per agent ----------------------------
   const uint64_t gid0 = (uint64_t)(P.market_base + m) * (uint64_t)A + (uint64_t)(t * AK);
@@ -211,8 +226,14 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     const uint32_t s = s0 + j;
     const int32_t* keys = sm.bbk + 2 * (j & 1);
     const int bb = keys[0], ba = keys[1];
-    const int mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * last;
+    int mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * last;
     const int ret = (mid2 > pmid2) - (mid2 < pmid2);
+    if (P.window) {
+      const int k = window_shift(mid2, L);  // uniform over the group
+      mid2 -= 2 * k;
+      last -= k;
+      if (t == 0) *sm.wbase += k;
+    }
 
     // ---- orders of step s ---------------------------------------------------------------
     const uint64_t sbase = abase + SM64_GAMMA * (8ull * (uint64_t)s);
@@ -371,9 +392,10 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     if (trade) last = pstar;
     pmid2 = mid2;
     if (t == 0) {
-      const int pt = trade ? pstar : -1;
+      const int64_t base = *sm.wbase;
+      const int pt = trade ? (int)(base + pstar) : -1;  // absolute p*
       if (trade) {
-        sump += pstar;
+        sump += base + pstar;
         trades += 1;
       }
       sumv += vstar;
@@ -381,7 +403,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
       hash = trace_mix(hash, s, pt, vstar);
       if (traced && s < P.trace_steps) {
         int32_t* tr = P.trace + ((size_t)m * P.trace_steps + s) * 2;
-        tr[0] = pt;
+        tr[0] = P.window ? (int)(base + last) : pt;  // window: the absolute last price, carried
         tr[1] = vstar;
       }
     }
@@ -397,6 +419,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     mo64[0] = sump;
     mo64[1] = sumv;
     mo64[2] = (int64_t)hash;
+    mo64[3] = *sm.wbase;
   }
   gsync<NT>(bar);  // shared memory is reused by the group's next market
 }
@@ -479,10 +502,17 @@ __global__ void __launch_bounds__(PAPER_NAIVE_THREADS) paper_naive_kernel(PaperP
     bid[p] = 0;
     ask[p] = 0;
   }
-  const int last0 = mi[0];
-  const int mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * last0;
+  int last0 = mi[0];
+  int mid2 = (bb >= 0 && ba < L) ? bb + ba : 2 * last0;
   const int pmid2 = mi[1];
   const int ret = (mid2 > pmid2) - (mid2 < pmid2);
+  int64_t base = m64[3];
+  if (P.window) {
+    const int k = window_shift(mid2, L);
+    base += k;
+    mid2 -= 2 * k;
+    last0 -= k;
+  }
 
   // orders of step s, agent by agent
   const uint64_t mbase = P.seed + SM64_GID * ((uint64_t)(P.market_base + m) * (uint64_t)A);
@@ -543,20 +573,22 @@ __global__ void __launch_bounds__(PAPER_NAIVE_THREADS) paper_naive_kernel(PaperP
     }
   }
 
-  // market scalars
-  const int pt = trade ? pstar : -1;
-  mi[0] = trade ? pstar : last0;
+  // market scalars (prices in the trace, the sum and the hash are absolute)
+  const int pt = trade ? (int)(base + pstar) : -1;
+  const int last = trade ? pstar : last0;
+  mi[0] = last;
   mi[1] = mid2;
   if (trade) {
     mi[2] += 1;
-    m64[0] += pstar;
+    m64[0] += base + pstar;
   }
   mi[3] = vstar;
   m64[1] += vstar;
   m64[2] = (int64_t)trace_mix((uint64_t)m64[2], s, pt, vstar);
+  m64[3] = base;
   if (m < P.trace_markets && s < P.trace_steps) {
     int32_t* tr = P.trace + ((size_t)m * P.trace_steps + s) * 2;
-    tr[0] = pt;
+    tr[0] = P.window ? (int)(base + last) : pt;
     tr[1] = vstar;
   }
 }
@@ -661,6 +693,7 @@ ks_status validate(const ks_paper_config* c) {
   if (c->mom_pct + c->maker_pct > 100u) return fail(KS_ERR_INVALID_ARG, "mom_pct + maker_pct above 100");
   if (c->tie_rule != KS_TIE_LOWEST_TICK && c->tie_rule != KS_TIE_MIN_IMBALANCE)
     return fail(KS_ERR_INVALID_ARG, "unknown tie_rule");
+  if (c->window != 0 && c->window != 1) return fail(KS_ERR_INVALID_ARG, "window must be 0 or 1");
   // per-step volume: A orders of at most KS_MAX_QTY must fit int32 (and the 22-bit imbalance key)
   if ((int64_t)c->A * c->qmax >= (1ll << 31)) return fail(KS_ERR_UNSUPPORTED, "A * qmax above 2^31");
   return KS_OK;
@@ -730,6 +763,7 @@ ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws
   p.mom_pct = cfg->mom_pct;
   p.maker_pct = cfg->maker_pct;
   p.tie_rule = cfg->tie_rule;
+  p.window = cfg->window;
   p.trace_markets = std::min(cfg->trace_markets, cfg->n_markets);
   p.trace_steps = cfg->trace_markets ? cfg->trace_steps : 0;
   p.bid = (int32_t*)(ws + lay.bid);
@@ -811,7 +845,7 @@ ks_status ks_paper_read_state(ks_paper_ensemble* e, const ks_paper_state_view* v
       {v->last_tick, p.mi32 + 0, PMI32 * 4, 4}, {v->mid2, p.mi32 + 1, PMI32 * 4, 4},
       {v->trades, p.mi32 + 2, PMI32 * 4, 4},    {v->last_volume, p.mi32 + 3, PMI32 * 4, 4},
       {v->sum_price, p.mi64 + 0, PMI64 * 8, 8}, {v->sum_volume, p.mi64 + 1, PMI64 * 8, 8},
-      {v->trace_hash, p.mi64 + 2, PMI64 * 8, 8},
+      {v->trace_hash, p.mi64 + 2, PMI64 * 8, 8}, {v->window_base, p.mi64 + 3, PMI64 * 8, 8},
   };
   for (auto& f : fs)
     if (f.view) KSP_CUDA(cudaMemcpy2DAsync(f.view, f.width, f.dev, f.pitch, f.width, e->M, cudaMemcpyDefault, st));

@@ -8,12 +8,19 @@ the GPU (``PaperEnsemble``, one persistent launch per configuration).  From
 the per-step clearing trace (p*, V*) of every market the sweep reports the
 stylized facts the paper plots: the volatility of clearing-price returns,
 their excess kurtosis, the executed volume per step, and the
-autocorrelation of returns and of absolute returns.
+autocorrelation of returns and of absolute returns.  The paper's "price
+volatility (std dev)" is read as the standard deviation of returns
+(``volatility``); the standard deviation of the price level over the run
+(``price_std``) is reported beside it, since a market that trends at a steady
+rate has a small return deviation but a large price excursion.
 
 Returns are r_t = p_t - p_{t-1} of the last clearing tick p_t (unchanged on
 a step without trade), pooled over the markets of a configuration.  The
-paper's agent constants (Delta_noise, P_mkt, q_max, Delta_maker) are not
-published, so the numbers are this build's; the paper's values are context.
+markets run on a sliding price window (Sec. III-A) by default, so a trending
+price is not stopped by the edge of the grid; ``window=False`` runs them on a
+fixed grid of L ticks.  The paper's agent constants (Delta_noise, P_mkt,
+q_max, Delta_maker) are not published, so the numbers are this build's; the
+paper's values are context.
 """
 from __future__ import annotations
 
@@ -38,26 +45,30 @@ def _acf(x: np.ndarray, lags: int) -> np.ndarray:
     return np.array([(x[:, :-k] * x[:, k:]).sum() / den for k in range(1, lags + 1)])
 
 
-def facts(trace: np.ndarray, L: int, lags: int = 20) -> dict:
-    """Stylized facts of a clearing trace [M, S, 2] (p*, V*; p* = -1 without trade)."""
+def facts(trace: np.ndarray, L: int, lags: int = 20, window: bool = False) -> dict:
+    """Stylized facts of a clearing trace [M, S, 2]: (p*, V*) with p* = -1
+    without trade on a fixed grid; (absolute last price, V*) with a window."""
     p = trace[:, :, 0].astype(np.int64)
     v = trace[:, :, 1].astype(np.float64)
     M, S = p.shape
     price = np.empty((M, S + 1), np.float64)
     price[:, 0] = L // 2
-    for s in range(S):
-        price[:, s + 1] = np.where(p[:, s] >= 0, p[:, s], price[:, s])
+    if window:
+        price[:, 1:] = p
+    else:
+        for s in range(S):
+            price[:, s + 1] = np.where(p[:, s] >= 0, p[:, s], price[:, s])
     r = np.diff(price, axis=1)
     flat = r.ravel()
     sd = flat.std()
     kurt = float(((flat - flat.mean()) ** 4).mean() / sd**4 - 3.0) if sd > 0 else 0.0
-    return {"volatility": float(r.std(axis=1).mean()), "excess_kurtosis": kurt,
-            "volume_per_step": float(v.mean()), "acf_r": _acf(r, lags).tolist(),
+    return {"volatility": float(r.std(axis=1).mean()), "price_std": float(price[:, 1:].std(axis=1).mean()),
+            "excess_kurtosis": kurt, "volume_per_step": float(v.mean()), "acf_r": _acf(r, lags).tolist(),
             "acf_abs_r": _acf(np.abs(r), lags).tolist(), "mean_price": float(price[:, 1:].mean())}
 
 
 def sweep(alphas=None, M: int = 64, S: int = 1000, A: int = 256, L: int = 128, maker_pct: int = 15,
-          seed: int = 1, stream=None) -> dict:
+          seed: int = 1, window: bool = True, stream=None) -> dict:
     """Runs the composition sweep; returns {alpha_mom: facts} and the device seconds."""
     import torch
     alphas = [round(0.05 * i, 2) for i in range(15)] if alphas is None else list(alphas)
@@ -65,7 +76,7 @@ def sweep(alphas=None, M: int = 64, S: int = 1000, A: int = 256, L: int = 128, m
     secs = 0.0
     for a in alphas:
         w = workloads.workload("paper_8192_256", M=M, L=L, A=A, seed=seed, mom_pct=int(round(100 * a)),
-                               maker_pct=maker_pct)
+                               maker_pct=maker_pct, window=int(window))
         ens = ks.PaperEnsemble(w, trace_markets=M, trace_steps=S)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -76,6 +87,6 @@ def sweep(alphas=None, M: int = 64, S: int = 1000, A: int = 256, L: int = 128, m
         secs += e0.elapsed_time(e1) / 1e3
         if ens.sync(timeout_ms=600_000) != ks.KS_OK:
             raise RuntimeError("paper ensemble reported a device error")
-        out[a] = facts(ens.read_state(["trace"])["trace"], L)
+        out[a] = facts(ens.read_state(["trace"])["trace"], L, window=window)
         ens.close()
     return {"facts": out, "device_seconds": secs, "agent_events": float(len(alphas)) * M * S * A}

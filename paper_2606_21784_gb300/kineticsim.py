@@ -109,13 +109,13 @@ class ks_paper_config(ctypes.Structure):
                 ("A", ctypes.c_int32), ("seed", ctypes.c_uint64), ("noise_halfwidth", ctypes.c_int32),
                 ("p_mkt_q32", ctypes.c_uint32), ("qmax", ctypes.c_int32), ("maker_half_spread", ctypes.c_int32),
                 ("mom_pct", ctypes.c_uint32), ("maker_pct", ctypes.c_uint32), ("tie_rule", ctypes.c_int32),
-                ("trace_markets", ctypes.c_uint32), ("trace_steps", ctypes.c_uint32), ("pad_", ctypes.c_int32)]
+                ("trace_markets", ctypes.c_uint32), ("trace_steps", ctypes.c_uint32), ("window", ctypes.c_int32)]
 
 
 class ks_paper_state_view(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in (
         "bid", "ask", "last_tick", "mid2", "trades", "last_volume", "sum_price", "sum_volume", "trace_hash",
-        "step", "trace")]
+        "step", "trace", "window_base")]
 
 
 _lib = None
@@ -556,7 +556,7 @@ PAPER_STATE_FIELDS = {
     "bid": (np.int32, "book"), "ask": (np.int32, "book"), "last_tick": (np.int32, "market"),
     "mid2": (np.int32, "market"), "trades": (np.int32, "market"), "last_volume": (np.int32, "market"),
     "sum_price": (np.int64, "market"), "sum_volume": (np.int64, "market"), "trace_hash": (np.uint64, "market"),
-    "step": (np.uint64, "one"), "trace": (np.int32, "trace"),
+    "step": (np.uint64, "one"), "trace": (np.int32, "trace"), "window_base": (np.int64, "market"),
 }
 
 
@@ -566,7 +566,7 @@ def make_paper_config(w: dict, trace_markets: int = 0, trace_steps: int = 0) -> 
     return ks_paper_config(int(w["M"]), int(w.get("market_base", 0)), int(w["L"]), int(w["A"]),
                            int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(p["noise_halfwidth"]), int(p["p_mkt_q32"]),
                            int(p["qmax"]), int(p["maker_half_spread"]), int(p["mom_pct"]), int(p["maker_pct"]),
-                           int(p.get("tie_rule", 0)), int(trace_markets), int(trace_steps), 0)
+                           int(p.get("tie_rule", 0)), int(trace_markets), int(trace_steps), int(p.get("window", 0)))
 
 
 class PaperEnsemble:

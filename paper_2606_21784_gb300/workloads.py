@@ -52,7 +52,7 @@ _MIX_CARRY = dict(
 
 _PAPER_AGENTS = dict(
     seed=1, noise_halfwidth=4, p_mkt_q32=CANCEL_005_Q32, qmax=10, maker_half_spread=1, mom_pct=15, maker_pct=15,
-    tie_rule=0,
+    tie_rule=0, window=0,
 )
 
 WORKLOADS = {

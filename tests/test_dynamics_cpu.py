@@ -16,6 +16,13 @@ def _trace(prices, volume=10):
 def test_constant_price_has_no_volatility():
     f = dynamics.facts(_trace([64] * 50), L=128)
     assert f["volatility"] == 0 and f["volume_per_step"] == 10 and f["mean_price"] == 64
+    assert f["price_std"] == 0
+
+
+def test_steady_trend_has_no_return_volatility_but_a_price_excursion():
+    f = dynamics.facts(_trace(np.arange(62, -138, -2)), L=128, window=True)  # -2 every step from 64
+    assert f["volatility"] == 0
+    assert abs(f["price_std"] - np.arange(62, -138, -2).std()) < 1e-12
 
 
 def test_bid_ask_bounce_has_lag1_autocorrelation_minus_one():
@@ -37,3 +44,15 @@ def test_steps_without_trade_keep_the_last_price():
     f = dynamics.facts(_trace([66, -1, -1, 66, 70]), L=128)  # returns 2, 0, 0, 0, 4 from L/2 = 64
     assert f["volume_per_step"] == 6.0  # 10 on three trading steps out of five
     assert abs(f["mean_price"] - (66 + 66 + 66 + 66 + 70) / 5) < 1e-12
+
+
+def test_window_traces_take_the_absolute_price_as_is():
+    # a window trace records the absolute last price after every step, which
+    # may be negative or far outside [0, L); returns from L/2 = 64
+    t = np.zeros((1, 4, 2), np.int32)
+    t[0, :, 0] = [60, -5, -5, 300]
+    t[0, :, 1] = [3, 4, 0, 8]
+    f = dynamics.facts(t, L=128, window=True)
+    r = np.array([-4, -65, 0, 305], np.float64)
+    assert abs(f["volatility"] - r.std()) < 1e-12
+    assert f["volume_per_step"] == 3.75 and abs(f["mean_price"] - (60 - 5 - 5 + 300) / 4) < 1e-12

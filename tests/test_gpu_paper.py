@@ -24,6 +24,8 @@ def _check_market(params, gs, m, L, A, steps, s0=0, trace=True):
     assert int(gs["trades"][m]) == sc["trades"] and int(gs["last_volume"][m]) == sc["last_v"], m
     assert int(gs["sum_price"][m]) == sc["sum_p"] and int(gs["sum_volume"][m]) == sc["sum_v"], m
     assert int(gs["trace_hash"][m]) == sc["hash"], m
+    if "window_base" in gs:
+        assert int(gs["window_base"][m]) == sc["base"], m
 
 
 def _run(w, steps, splits=None, launch=None, trace=True):
@@ -108,12 +110,16 @@ def test_composition_sweep_runs_and_momentum_raises_volatility():
     from paper_2606_21784_gb300 import dynamics
     r = dynamics.sweep(alphas=[0.0, 0.15, 0.5], M=16, S=400)
     f = r["facts"]
-    assert f[0.5]["volatility"] > 1.5 * f[0.0]["volatility"] > 0
-    assert all(x["volume_per_step"] > 0 for x in f.values())
+    # on a sliding window momentum markets run away: the price level spreads
+    assert f[0.5]["price_std"] > 5 * f[0.0]["price_std"] > 0
+    assert all(x["volume_per_step"] > 0 and x["volatility"] > 0 for x in f.values())
     # the sweep's markets are the oracle's: one configuration's trace, bit-exact
-    w = wl.workload("paper_8192_256", M=16, L=128, A=256, mom_pct=50, maker_pct=15)
+    w = wl.workload("paper_8192_256", M=16, L=128, A=256, mom_pct=50, maker_pct=15, window=1)
     gs = _run(w, 400)
     _check_market(w["params"], gs, 5, 128, 256, 400)
+    # and on a fixed grid
+    r = dynamics.sweep(alphas=[0.0, 0.5], M=16, S=400, window=False)
+    assert r["facts"][0.5]["volatility"] > r["facts"][0.0]["volatility"] > 0
 
 
 def _run_engines(w, plan, trace=True):
@@ -159,3 +165,20 @@ def test_naive_engine_full_fixed_workload_equals_persistent():
     for f in a:
         assert np.array_equal(a[f], b[f]), f
     _check_market(w["params"], b, 4321, 128, 256, w["S"], trace=False)
+
+
+@pytest.mark.parametrize("L,A,mom,launch", [(64, 256, 30, None), (64, 200, 70, (128, 2, 1)), (128, 1024, 70, None),
+                                            (64, 5, 30, (32, 1, 1)), (40, 300, 50, (256, 2, 1))])
+def test_sliding_window_matches_the_oracle(L, A, mom, launch):
+    """Sliding window (runaway momentum markets, marketable orders at the
+    window's edges): every market and step of both engines against the oracle."""
+    w = wl.workload("paper_8192_256", M=13, L=L, A=A, mom_pct=mom, window=1)
+    steps = 300
+    gs = _run(w, steps, splits=[100, 200], launch=launch)
+    assert np.abs(gs["window_base"]).max() > L  # the windows travelled
+    for m in range(w["M"]):
+        _check_market(w["params"], gs, m, L, A, steps)
+    for plan in ([("n", steps)], [("p", 120), ("n", 60), ("p", 120)]):
+        got = _run_engines(w, plan)
+        for f in gs:
+            assert np.array_equal(gs[f], got[f]), (plan, f)
