@@ -153,6 +153,40 @@ struct RuleConsts {
   uint32_t rb_qmax;
 };
 
+// 256-bit global accesses (sm_100 and later): one lane moves a whole 32-byte
+// sector, so a warp's strided state accesses write no partial sectors.  The
+// address must be 32-byte aligned.
+__device__ __forceinline__ void ld_b32x8(const void* p, uint32_t (&v)[8]) {
+  asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_b32x8(void* p, const uint32_t (&v)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]),
+               "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void ld_b64x4(const void* p, int64_t (&v)[4]) {
+  asm volatile("ld.global.v4.b64 {%0,%1,%2,%3}, [%4];" : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_b64x4(void* p, const int64_t (&v)[4]) {
+  asm volatile("st.global.v4.b64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(v[0]), "l"(v[1]), "l"(v[2]), "l"(v[3]) : "memory");
+}
+
+// Asynchronous L2 prefetch of [p, p + bytes) (cp.async.bulk.prefetch.L2),
+// widened to 16-byte bounds.  The callers' ranges lie in workspace regions that
+// are 256-byte aligned and padded to 256 bytes, so the widened range stays in
+// the region.  Nothing waits for it.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+  uint64_t g;
+  asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(p));
+  const uint64_t lo = g & ~15ull;
+  const uint64_t n = ((g + bytes + 15ull) & ~15ull) - lo;
+  if (n > 0 && n < (1ull << 31))
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)n) : "memory");
+}
+
 // book[i] += v where pred holds, as one predicated shared-memory reduction
 // (no branch around it).
 __device__ __forceinline__ void red_add_if(uint32_t saddr, int v, bool pred) {

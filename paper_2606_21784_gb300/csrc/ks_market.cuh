@@ -583,7 +583,37 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   int cpend[REGACC ? AK : 1];  // cash since the last flush into sm.cash
   const int a0 = t * AK;
   const bool vec = (AK % 4 == 0) && ((aoff + a0) % 4 == 0) && (a0 + AK <= A);
-  if (vec) {
+  // 256-bit accesses: a thread's agents start on a 32-byte boundary of every array
+  const bool wide = (AK % 8 == 0) && vec && ((aoff + a0) % 8 == 0);
+  if constexpr (AK % 8 == 0) {
+    if (wide) {
+#pragma unroll
+      for (int k = 0; k < AK; k += 8) {
+        uint32_t sv[8], iv[8];
+        int64_t c0[4], c1[4];
+        ld_b32x8(P.slot + aoff + a0 + k, sv);
+        ld_b32x8(P.inv + aoff + a0 + k, iv);
+        ld_b64x4(P.cash + aoff + a0 + k, c0);
+        ld_b64x4(P.cash + aoff + a0 + k + 4, c1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          slot[k + i] = sv[i];
+          if constexpr (REGACC)
+            inv[k + i] = (int)iv[i];
+          else
+            sm.inv[(k + i) * NT + t] = (int)iv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          sm.cash[(k + i) * NT + t] = c0[i];
+          sm.cash[(k + 4 + i) * NT + t] = c1[i];
+        }
+      }
+    }
+  }
+  if (wide) {
+    // loaded above
+  } else if (vec) {
 #pragma unroll
     for (int k = 0; k < AK; k += 4) {
       const uint4 sv = *reinterpret_cast<const uint4*>(P.slot + aoff + a0 + k);
@@ -848,7 +878,39 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   }
 
   // ---- store ---------------------------------------------------------------------------
-  if (vec) {
+  if constexpr (AK % 8 == 0) {
+    if (wide) {
+#pragma unroll
+      for (int k = 0; k < AK; k += 8) {
+        uint32_t sv[8], iv[8];
+        int64_t c0[4], c1[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          sv[i] = slot[k + i];
+          if constexpr (REGACC)
+            iv[i] = (uint32_t)inv[k + i];
+          else
+            iv[i] = (uint32_t)sm.inv[(k + i) * NT + t];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          c0[i] = sm.cash[(k + i) * NT + t];
+          c1[i] = sm.cash[(k + 4 + i) * NT + t];
+          if constexpr (REGACC) {
+            c0[i] += cpend[k + i];
+            c1[i] += cpend[k + 4 + i];
+          }
+        }
+        st_b32x8(P.slot + aoff + a0 + k, sv);
+        st_b32x8(P.inv + aoff + a0 + k, iv);
+        st_b64x4(P.cash + aoff + a0 + k, c0);
+        st_b64x4(P.cash + aoff + a0 + k + 4, c1);
+      }
+    }
+  }
+  if (wide) {
+    // stored above
+  } else if (vec) {
 #pragma unroll
     for (int k = 0; k < AK; k += 4) {
       *reinterpret_cast<uint4*>(P.slot + aoff + a0 + k) = make_uint4(slot[k], slot[k + 1], slot[k + 2], slot[k + 3]);

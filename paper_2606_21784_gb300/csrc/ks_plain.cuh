@@ -6,6 +6,22 @@
 
 namespace ks {
 
+// Thread 0 of a CTA prefetches into L2 the state of the market it runs next
+// (order words, inventory, cash and scalars), so that the next market's state
+// loads find it there: the load of market m + grid overlaps market m.
+__device__ __forceinline__ void prefetch_next_market(const DevParams& P, uint32_t m) {
+  const uint32_t n = m + gridDim.x;
+  if (threadIdx.x != 0 || n >= P.M) return;
+  const int A = P.As ? P.As[n] : P.A_all;
+  const int64_t aoff = P.agent_off ? P.agent_off[n] : (int64_t)n * (int64_t)P.A_all;
+  if (A <= 0) return;
+  l2_prefetch(P.slot + aoff, (size_t)A * 4);
+  l2_prefetch(P.inv + aoff, (size_t)A * 4);
+  l2_prefetch(P.cash + aoff, (size_t)A * 8);
+  l2_prefetch(P.mi32 + (size_t)n * MI32_STRIDE, MI32_STRIDE * 4);
+  l2_prefetch(P.mi64 + (size_t)n * MI64_STRIDE, MI64_STRIDE * 8);
+}
+
 // Register-cap classes of the launch bounds: 0 = compiler's choice, 1 = 128
 // registers per thread (two 256-thread CTAs per SM), 2 = 85 (three).
 // Returns the launch bounds' minimum of resident CTAs.
@@ -38,14 +54,18 @@ __global__ void __launch_bounds__(NT, plain_min_ctas(NT, OCC)) plain_kernel(DevP
     mw.bar_id = 1 + wg;
     mw.phase = 0;
     mw.abort = false;
-    for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x)
+    for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
+      prefetch_next_market(P, m);
       run_market<NT, AK, false, true, false>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax, &mw, mc.sw);
+    }
     mlp_cta_teardown(mc);
   } else {
     constexpr bool REGACC = accounts_in_registers(BUDGET, AK, false);
     const Smem sm = carve<NT, AK, false, !REGACC>(smem_raw, P.Lmax);
-    for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x)
+    for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
+      prefetch_next_market(P, m);
       run_market<NT, AK, AGGR, false, REGACC>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax);
+    }
   }
 }
 
