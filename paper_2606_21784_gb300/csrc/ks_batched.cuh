@@ -33,7 +33,7 @@ __device__ __forceinline__ void run_item(const DevParams& P, const BatchArgs& B,
     const size_t gsz = group_smem_layout(BUDGET, GT, AK, (int)d.w, false, o);
     const Smem sm = carve<GT, AK, false, !REGACC>(raw + (size_t)g * gsz, (int)d.w);
     const int bar = (GT == NT) ? 0 : 1 + g;
-    run_market<GT, AK, false, false, REGACC>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w);
+    run_market<GT, AK, false, false, REGACC, true>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w);
   }
 }
 

@@ -554,10 +554,11 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
 // bar: the group's barrier id, Lcap: the largest L the group's shared memory
 // (sm) was carved for, REGACC: inventory and cash in registers (else in the
 // shared-memory columns sm.inv / sm.cash).
-template <int NT, int AK, bool AGGR, bool MLP, bool REGACC>
+template <int NT, int AK, bool AGGR, bool MLP, bool REGACC, bool FIT = false>
 __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t n_steps, const Smem& sm, int t,
                            int bar, int Lcap, MlpWG* mw = nullptr, const unsigned char* sw = nullptr) {
   static_assert(!(MLP && AGGR), "policy kernels use plain shared atomics");
+  static_assert(!(MLP && FIT), "policy rows map agents to threads by a / AK");
   static_assert(!(MLP && REGACC), "policy rows read the inventory from shared memory");
   static_assert(!MLP || (NT >= 128 && NT % 128 == 0), "policy groups are whole warpgroups");
   static_assert((AK & (AK - 1)) == 0 && AK <= 32, "agents per thread: a power of two (agent = a0 ^ k)");
@@ -581,8 +582,12 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   uint32_t slot[AK];
   int inv[REGACC ? AK : 1];
   int cpend[REGACC ? AK : 1];  // cash since the last flush into sm.cash
-  const int a0 = t * AK;
-  const bool vec = (AK % 4 == 0) && ((aoff + a0) % 4 == 0) && (a0 + AK <= A);
+  // FIT: the market's agents spread evenly over the group, akeff = ceil(A / NT)
+  // of the AK slots per thread (a market smaller than the group's capacity then
+  // takes fewer passes); else every thread owns AK agents.
+  const int akeff = FIT ? min(AK, (A + NT - 1) / NT) : AK;
+  const int a0 = t * akeff;
+  const bool vec = (AK % 4 == 0) && ((aoff + a0) % 4 == 0) && (a0 + AK <= A) && akeff == AK;
   // 256-bit accesses: a thread's agents start on a 32-byte boundary of every array
   const bool wide = (AK % 8 == 0) && vec && ((aoff + a0) % 8 == 0);
   if constexpr (AK % 8 == 0) {
@@ -634,7 +639,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 #pragma unroll
     for (int k = 0; k < AK; ++k) {
       const int a = a0 + k;
-      const bool v = a < A;
+      const bool v = a < A && k < akeff;
       slot[k] = v ? P.slot[aoff + a] : 0u;
       if constexpr (REGACC)
         inv[k] = v ? P.inv[aoff + a] : 0;
@@ -712,13 +717,15 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     uint32_t pflags = 0;
 #pragma unroll
     for (int k = 0; k < AK; ++k) {
+      if (FIT && k >= akeff) break;
       if constexpr (MLP) {
         bool pol = false;
         slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s,
                                           P.rk, &pol, &P, &sf, sm.inv[k * NT + t]);
         pflags |= pol ? (1u << k) : 0u;
       } else {
-        slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
+        const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
+        slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
       }
     }
     if constexpr (MLP) {
@@ -757,6 +764,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       uint32_t mB = 0, mS = 0;
 #pragma unroll
       for (int k = 0; k < AK; ++k) {
+        if (FIT && k >= akeff) break;
         const uint32_t st = slot[k] & W_ST;
         const uint32_t q = w_qty(slot[k]);
         mB += st == key_b ? q : 0u;
@@ -819,6 +827,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     constexpr int IL = (AK < 2 || MLP) ? 1 : 2;
 #pragma unroll
     for (int kb = 0; kb < AK; kb += IL) {
+      if (FIT && kb >= akeff) break;
       uint32_t sl[IL];
 #pragma unroll
       for (int i = 0; i < IL; ++i) {
@@ -854,7 +863,9 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
                                             P.rk, &pol, &P, &sf, sm.inv[k * NT + t]);
             pflags |= pol ? (1u << k) : 0u;
           } else {
-            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
+            const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
+            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0, a0 + k < A && (!FIT || k < akeff), sr, cthr, L, sm.ctab,
+                                      book_s, P.rk);
           }
         }
       }
@@ -937,7 +948,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 #pragma unroll
     for (int k = 0; k < AK; ++k) {
       const int a = a0 + k;
-      if (a < A) {
+      if (a < A && k < akeff) {
         P.slot[aoff + a] = slot[k];
         if constexpr (REGACC) {
           P.inv[aoff + a] = inv[k];
