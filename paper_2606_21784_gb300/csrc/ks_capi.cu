@@ -421,10 +421,25 @@ static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, siz
   return g;
 }
 
-// Default bucket shape: about 8 agents per thread.
+// Default bucket shape.  Rule-agent buckets spread a market over its group
+// (ceil(A / threads) agents per thread), so spare capacity costs little and
+// larger groups clear the book faster: 4 agents per thread up to A = 512 (128
+// threads), 8 up to 2048, 16 up to 8192, then 32, with at least 128 threads
+// (the autotuner's choices on uneven ensembles).  Policy buckets, and shapes a
+// CTA size does not compile, take the tightest fit at about 8 agents per thread.
 static bool default_shape(int nt, int Ac, int* gt, int* ak, bool mlp) {
   int n = 0;
   const int(*tab)[2] = batch_table(nt, &n, mlp);
+  if (!mlp) {
+    const int k = Ac <= 512 ? 4 : (Ac <= 2048 ? 8 : (Ac <= 8192 ? 16 : 32));
+    const int g = std::max(128, Ac / k);
+    for (int i = 0; i < n; ++i)
+      if (tab[i][0] == g && tab[i][1] == k && g <= nt) {
+        *gt = g;
+        *ak = k;
+        return true;
+      }
+  }
   int best = -1;
   long best_score = 0;
   for (int i = 0; i < n; ++i) {
