@@ -65,7 +65,7 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
     mw.bar_id = (GT == 128) ? bar : 8 + wc;
     mw.phase = 0;
     mw.abort = false;
-    run_market<GT, AK, false, true, false>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w, &mw,
+    run_market<GT, AK, false, true, false, true>(P, B.order[d.x + g], s0, n, sm, (int)threadIdx.x % GT, bar, (int)d.w, &mw,
                                     mc.sw);
   }
 }

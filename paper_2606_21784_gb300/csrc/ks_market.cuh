@@ -231,12 +231,13 @@ __device__ __forceinline__ int hist_at(const int (&hist)[KS_HISTORY], int lb) {
 // with its own activation buffer, accumulator columns and mbarrier in `mw`)
 // on the tensor cores and sample the actions (Philox stream 3 of step
 // sdec), then the owners place the orders.
-// The inventories of the flagged agents are in sm.inv.
+// The inventories of the flagged agents are in sm.inv; thread t owns agents
+// [t * akeff, t * akeff + akeff).
 template <int NT, int AK>
 __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm, MlpWG& mw, const unsigned char* sw,
                                              uint32_t (&slot)[AK], uint32_t pflags, int t, int bar, int a0, int A,
                                              int L, uint32_t sdec, uint32_t gm, const StepFeat& f, int last,
-                                             int64_t aoff, bool traced, int32_t* book) {
+                                             int64_t aoff, bool traced, int32_t* book, int akeff) {
   constexpr int NW = NT / 32;
   const int lane = t & 31;
   const int wid = t >> 5;
@@ -276,7 +277,8 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
       const int row = tile * 128 + (t & 127);
       const bool valid = row < total;
       const int a = valid ? (int)sm.rowbuf[row] : 0;
-      const int inv = valid ? sm.inv[(a % AK) * NT + a / AK] : 0;
+      const int ta = a / akeff;
+      const int inv = valid ? sm.inv[(a - ta * akeff) * NT + ta] : 0;
       float z[MLP_OUT];
       mlp_tile_logits(mw, sw, sm.cvec, (float)inv * (1.0f / 256.0f), z, P.err);
       if (valid) {
@@ -558,7 +560,6 @@ template <int NT, int AK, bool AGGR, bool MLP, bool REGACC, bool FIT = false>
 __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t n_steps, const Smem& sm, int t,
                            int bar, int Lcap, MlpWG* mw = nullptr, const unsigned char* sw = nullptr) {
   static_assert(!(MLP && AGGR), "policy kernels use plain shared atomics");
-  static_assert(!(MLP && FIT), "policy rows map agents to threads by a / AK");
   static_assert(!(MLP && REGACC), "policy rows read the inventory from shared memory");
   static_assert(!MLP || (NT >= 128 && NT % 128 == 0), "policy groups are whole warpgroups");
   static_assert((AK & (AK - 1)) == 0 && AK <= 32, "agents per thread: a power of two (agent = a0 ^ k)");
@@ -718,19 +719,20 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 #pragma unroll
     for (int k = 0; k < AK; ++k) {
       if (FIT && k >= akeff) break;
+      const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
       if constexpr (MLP) {
         bool pol = false;
-        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s,
-                                          P.rk, &pol, &P, &sf, sm.inv[k * NT + t]);
+        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk, &pol,
+                                          &P, &sf, sm.inv[k * NT + t]);
         pflags |= pol ? (1u << k) : 0u;
       } else {
-        const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
         slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
       }
     }
     if constexpr (MLP) {
       if (policy_on)
-        policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s0, gm, sf, last, aoff, traced, book);
+        policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s0, gm, sf, last, aoff, traced, book,
+                             akeff);
     }
   }
 
@@ -857,15 +859,15 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 #pragma unroll
         for (int i = 0; i < IL; ++i) {
           const int k = kb + i;
+          const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
+          const bool valid = a0 + k < A && (!FIT || k < akeff);
           if constexpr (MLP) {
             bool pol = false;
-            sl[i] = order_agent<AGGR, true>(sl[i], a0 + k, x0a ^ (uint32_t)k, a0 + k < A, sr, cthr, L, sm.ctab, book_s,
-                                            P.rk, &pol, &P, &sf, sm.inv[k * NT + t]);
+            sl[i] = order_agent<AGGR, true>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.ctab, book_s, P.rk, &pol, &P,
+                                            &sf, sm.inv[k * NT + t]);
             pflags |= pol ? (1u << k) : 0u;
           } else {
-            const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
-            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0, a0 + k < A && (!FIT || k < akeff), sr, cthr, L, sm.ctab,
-                                      book_s, P.rk);
+            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.ctab, book_s, P.rk);
           }
         }
       }
@@ -884,7 +886,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     if constexpr (MLP) {
       if (policy_on && more)
         policy_phase<NT, AK>(P, sm, *mw, sw, slot, pflags, t, bar, a0, A, L, s + 1, gm, sf, last, aoff, traced,
-                             book);
+                             book, akeff);
     }
   }
 
