@@ -338,6 +338,9 @@ PAPER_TABLE_III = {(64, 256): 3.61e9, (256, 256): 1.35e10, (1024, 256): 3.69e10,
 PAPER_NAIVE = {(64, 256): 6.39e7, (256, 256): 1.95e8, (1024, 256): 7.56e8, (4096, 256): 3.09e9,
                (16384, 256): 1.14e10, (8192, 16): 8.01e8, (8192, 64): 2.58e9, (8192, 256): 6.13e9,
                (8192, 1024): 8.89e9}
+# peak GPU global-memory footprint of the paper's engine across the market sweep
+# at A=256 (Table V), MB
+PAPER_FOOTPRINT_MB = {64: 0.14, 256: 0.54, 1024: 2.16, 4096: 8.66, 16384: 34.63}
 # median per-step latency at 4096 markets x 256 agents (Sec. IV-I), microseconds
 PAPER_STEP_LATENCY_US = {"persistent": 22.1, "naive": 339.3}
 
@@ -390,7 +393,10 @@ def paper_forms(ks, workloads, stream, reps: int = 3):
                              "ratio_to_paper": rate / ref,
                              "launch": {k: launch[k] for k in ("threads", "agents_per_thread", "min_ctas")},
                              "naive_events_per_s": nrate, "speedup_over_naive": rate / nrate,
-                             "paper_naive": pn, "paper_speedup_over_naive": ref / pn}
+                             "paper_naive": pn, "paper_speedup_over_naive": ref / pn,
+                             "workspace_mb": ens.ws_bytes / 1e6}
+        if A == 256 and M in PAPER_FOOTPRINT_MB:
+            out[f"M{M}_A{A}"]["paper_footprint_mb"] = PAPER_FOOTPRINT_MB[M]
         if (M, A) == (4096, 256):
             out["step_latency_us_4096x256"] = {"persistent": 1e3 * best / S, "naive": 1e3 * naive / S,
                                                "paper": PAPER_STEP_LATENCY_US}
