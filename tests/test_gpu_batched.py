@@ -129,3 +129,18 @@ def test_autotuner_plan_is_valid_and_invariant():
     _, got = _run(w, L, A, steps, plan=(plan["cta_threads"], plan["buckets"]))
     for f in ref:
         assert np.array_equal(ref[f], got[f]), f
+
+
+def test_agents_spread_over_a_large_group_edge_sizes():
+    """One 512 x 32 bucket for markets of 0 .. 16384 agents: a market gives each
+    thread ceil(A / 512) agents (one for A < 512, with most threads empty;
+    odd counts pair an agent with an empty slot), and every market and step
+    still matches the oracle."""
+    A = np.array([0, 1, 31, 33, 511, 513, 1000, 1537, 9000, 16384], np.int32)
+    L = np.array([128, 256, 512, 1024, 2048, 128, 256, 1024, 512, 2048], np.int32)
+    M, steps = len(A), 30
+    w = wl.workload("batched_20000", M=M)
+    ens, gs = _run(w, L, A, steps, plan=(512, [(2048, 16384, 512, 32)]), trace=M)
+    ref = oracle_markets(w["params"], range(M), L, A, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
