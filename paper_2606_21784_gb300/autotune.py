@@ -182,7 +182,8 @@ def tune_batched(w: dict, L=None, A=None, steps: int = 20, max_sample: int = 121
 PAPER_SHAPES = ((32, 1, 1), (32, 2, 1), (32, 4, 1), (32, 1, 8), (32, 2, 8), (32, 8, 1), (32, 8, 6), (32, 16, 1),
                 (32, 32, 1), (128, 1, 1), (128, 2, 1), (128, 4, 1),
                 (128, 8, 1), (128, 16, 1), (128, 1, 8), (128, 2, 8), (128, 4, 6), (128, 8, 6), (256, 1, 1),
-                (256, 2, 1), (256, 4, 1), (256, 8, 1), (256, 16, 1), (512, 16, 1), (1024, 16, 1))
+                (256, 2, 1), (256, 4, 1), (256, 8, 1), (256, 16, 1), (512, 16, 1), (1024, 16, 1),
+                (16, 1, 1), (16, 2, 1), (16, 4, 1), (16, 2, 8), (16, 4, 8))
 
 
 def tune_paper(w: dict, steps: int = 100, use_cache: bool = True, verbose: bool = False) -> dict:

@@ -161,12 +161,37 @@ __device__ __forceinline__ PaperSmem paper_carve(unsigned char* raw, int L) {
   return s;
 }
 
+// Groups narrower than a warp (GT = 16: two markets per warp) run their warp
+// collectives on their own lane segment: mask, width and leader below.
+template <int GT>
+__device__ __forceinline__ unsigned seg_mask() {
+  if constexpr (GT >= 32) {
+    return 0xffffffffu;
+  } else {
+    return ((1u << GT) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(GT - 1));
+  }
+}
+
+// Barrier of a market's group: the lane segment, the warp, or a named barrier.
+template <int GT>
+__device__ __forceinline__ void psync(int bar) {
+  if constexpr (GT < 32) {
+    __syncwarp(seg_mask<GT>());
+  } else {
+    gsync<GT>(bar);
+  }
+}
+
 // Local best bid (highest tick with resting buy quantity) and best ask
-// (lowest tick with resting sell quantity) folded into the shared keys.
+// (lowest tick with resting sell quantity) folded into the shared keys by
+// each warp's (or segment's) leader.
+template <int GT>
 __device__ __forceinline__ void fold_best(int32_t* keys, int bb, int ba) {
-  const int wbb = (int)__reduce_max_sync(0xffffffffu, (unsigned)(bb + 1)) - 1;
-  const int wba = (int)__reduce_min_sync(0xffffffffu, (unsigned)ba);
-  if ((threadIdx.x & 31) == 0) {
+  constexpr int W = GT < 32 ? GT : 32;
+  const unsigned fm = seg_mask<GT>();
+  const int wbb = (int)__reduce_max_sync(fm, (unsigned)(bb + 1)) - 1;
+  const int wba = (int)__reduce_min_sync(fm, (unsigned)ba);
+  if ((threadIdx.x & (W - 1)) == 0) {
     atomicMax(keys + 0, wbb);
     atomicMin(keys + 1, wba);
   }
@@ -175,8 +200,10 @@ __device__ __forceinline__ void fold_best(int32_t* keys, int bb, int ba) {
 template <int NT, int AK, int LTC>
 __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, uint32_t s0, uint32_t n_steps,
                                              const PaperSmem& sm, int t, int bar) {
-  const int lane = t & 31;
+  const int lane = t & 31;  // lane within the group's warp or segment
   const int wid = t >> 5;
+  constexpr int W = NT < 32 ? NT : 32;  // lanes that scan and reduce together
+  const unsigned FM = seg_mask<NT>();
   const int L = P.L, A = P.A;
   const int LT = (L + NT - 1) / NT;
   const int p0 = t * LT;
@@ -189,7 +216,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   if (t < 4) sm.bbk[t] = (t & 1) ? L : -1;  // both parities: best bid -1, best ask L
   for (int i = t; i < 2 * book_len(L); i += NT) book[i] = 0;
   if (t < 8) sm.kx[t] = 0ull;
-  gsync<NT>(bar);
+  psync<NT>(bar);
   {
     int bb = -1, ba = L;
     for (int i = 0; i < LT; ++i) {
@@ -199,7 +226,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
         if (P.ask[moff + p] > 0 && ba == L) ba = p;
       }
     }
-    fold_best(sm.bbk, bb, ba);
+    fold_best<NT>(sm.bbk, bb, ba);
   }
   const int32_t* mi = P.mi32 + (size_t)m * PMI32;
   int last = mi[0];
@@ -220,7 +247,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
   for (int k = 0; k < AK; ++k) cls |= (ClassWord)paper_class(P, abase + SM64_GID * (uint64_t)k) << (2 * k);
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
   const bool traced = m < P.trace_markets;
-  gsync<NT>(bar);
+  psync<NT>(bar);
 
   for (uint32_t j = 0; j < n_steps; ++j) {
     const uint32_t s = s0 + j;
@@ -244,7 +271,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
                                        (uint32_t)a, s, mid2, ret);
       red_add_if(book_s + 4u * (uint32_t)(2 * o.tick + (int)o.sell), o.q, a < A);
     }
-    gsync<NT>(bar);  // B1: the step's orders are in the book
+    psync<NT>(bar);  // B1: the step's orders are in the book
 
     // ---- clearing (Eq. 1-2) ---------------------------------------------------------------
     constexpr int R = LTC > 0 ? LTC : 1;
@@ -271,18 +298,18 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     }
     int sufB = sumB, preS = sumS;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int vb = __shfl_down_sync(0xffffffffu, sufB, d);
-      const int vs = __shfl_up_sync(0xffffffffu, preS, d);
-      if (lane + d < 32) sufB += vb;
+    for (int d = 1; d < W; d <<= 1) {
+      const int vb = __shfl_down_sync(FM, sufB, d, W);
+      const int vs = __shfl_up_sync(FM, preS, d, W);
+      if (lane + d < W) sufB += vb;
       if (lane >= d) preS += vs;
     }
     if (lane == 0) sm.wD[wid] = sufB;
-    if (lane == 31) sm.wS[wid] = preS;
+    if (lane == W - 1) sm.wS[wid] = preS;
     unsigned long long* kx = sm.kx + 4 * (j & 1);
-    gsync<NT>(bar);  // B2
-    const int offD = (int)__reduce_add_sync(0xffffffffu, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
-    const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
+    psync<NT>(bar);  // B2
+    const int offD = (int)__reduce_add_sync(FM, (lane < NT / 32 && lane > wid) ? (unsigned)sm.wD[lane] : 0u);
+    const int offS = (int)__reduce_add_sync(FM, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
     const int D0 = offD + sufB;
     const int Sb0 = offS + preS - sumS;
     {
@@ -312,14 +339,14 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
         for (int i = 0; i < LT; ++i)
           if (p0 + i < L) visit(p0 + i, book[2 * (p0 + i)], book[2 * (p0 + i) + 1]);
       }
-      const int vw = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(bestV, 0));
+      const int vw = (int)__reduce_max_sync(FM, (unsigned)max(bestV, 0));
       const bool top = bestV == vw;
-      const uint32_t low = __reduce_min_sync(0xffffffffu, top ? (unsigned)lo : 4095u);
-      const uint32_t high = __reduce_max_sync(0xffffffffu, top ? (unsigned)hi : 0u);
+      const uint32_t low = __reduce_min_sync(FM, top ? (unsigned)lo : 4095u);
+      const uint32_t high = __reduce_max_sync(FM, top ? (unsigned)hi : 0u);
       if (tie1) {
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, kT, d);
+        for (int d = W / 2; d > 0; d >>= 1) {
+          const unsigned long long o = __shfl_xor_sync(FM, kT, d, W);
           kT = o > kT ? o : kT;
         }
       }
@@ -329,7 +356,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
         if (tie1) atomicMax(kx + 2, kT);
       }
     }
-    gsync<NT>(bar);  // B3
+    psync<NT>(bar);  // B3
     const unsigned long long kLo = kx[0], kHi = kx[1];
     const int vstar = (int)(kLo >> 12);
     const int p_lo = 4095 - (int)(kLo & 4095u);
@@ -381,7 +408,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
           }
         }
       }
-      fold_best(nkeys, nbb, nba);
+      fold_best<NT>(nkeys, nbb, nba);
     }
     if (t == 0) {
       // keys of the step after next start empty (this step read them already)
@@ -407,7 +434,7 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
         tr[1] = vstar;
       }
     }
-    gsync<NT>(bar);  // B5: next mid keys complete, book empty
+    psync<NT>(bar);  // B5: next mid keys complete, book empty
   }
   if (t == 0) {
     int32_t* mo = P.mi32 + (size_t)m * PMI32;
@@ -421,18 +448,19 @@ __device__ __forceinline__ void paper_market(const PaperParams& P, uint32_t m, u
     mo64[2] = (int64_t)hash;
     mo64[3] = *sm.wbase;
   }
-  gsync<NT>(bar);  // shared memory is reused by the group's next market
+  psync<NT>(bar);  // shared memory is reused by the group's next market
 }
 
 // Shared memory per group, 16-byte aligned.
 __host__ __device__ inline size_t paper_group_bytes(int L) { return (paper_smem_bytes(L) + 15) & ~(size_t)15; }
 
-// CTA of NT threads in groups of GT (NT / GT markets in parallel; GT = 32
-// groups synchronise with __syncwarp, larger ones with named barriers).
+// CTA of NT threads in groups of GT (NT / GT markets in parallel; GT = 16 and
+// GT = 32 groups synchronise with __syncwarp on their lanes, larger ones with
+// named barriers).
 // MINB > 1: compiled for at least MINB resident CTAs per SM (a register cap).
 template <int NT, int GT, int AK, int MINB>
 __global__ void __launch_bounds__(NT, MINB) paper_kernel(PaperParams P, uint32_t n_steps) {
-  static_assert(GT == 32 || GT == NT, "groups are one warp or the whole CTA");
+  static_assert(GT == 16 || GT == 32 || GT == NT, "groups are half a warp, one warp or the whole CTA");
   constexpr int G = NT / GT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t s0 = (uint32_t)(*P.step);
@@ -619,7 +647,8 @@ static const PaperVariant kPaperVariants[] = {
     KS_PV(128, 128, 8, 1),   KS_PV(128, 128, 16, 1),  KS_PV(128, 128, 1, 8),   KS_PV(128, 128, 2, 8),
     KS_PV(128, 128, 4, 6),   KS_PV(128, 128, 8, 6),   KS_PV(256, 256, 1, 1),   KS_PV(256, 256, 2, 1),
     KS_PV(256, 256, 4, 1),   KS_PV(256, 256, 8, 1),   KS_PV(256, 256, 16, 1),  KS_PV(512, 512, 16, 1),
-    KS_PV(1024, 1024, 16, 1)};
+    KS_PV(1024, 1024, 16, 1), KS_PV(128, 16, 1, 1),    KS_PV(128, 16, 2, 1),    KS_PV(128, 16, 4, 1),
+    KS_PV(128, 16, 2, 8),    KS_PV(128, 16, 4, 8)};
 #undef KS_PV
 
 }  // namespace ks
@@ -790,13 +819,19 @@ ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws
     delete e;
     return cuda_status(ce, "paper_init_kernel");
   }
-  // default shape (measured on GB300 at L = 128 with 8192 markets): a warp per
-  // market up to 256 agents, else 128 threads per market with up to 16 agents
-  // each, under the register caps that won
+  // default shape (measured on GB300 at L = 128 with 8192 markets): half a
+  // warp per market up to 32 agents, a warp up to 256 agents, else 128
+  // threads per market with up to 16 agents each, under the register caps
+  // that won
   int nt = cfg->A <= 256 ? 32 : 128;
   while (nt < 1024 && (int64_t)nt * 16 < cfg->A) nt *= 2;
-  const int ak = std::min(16, next_pow2(std::max(1, (cfg->A + nt - 1) / nt)));
-  const int mc = nt == 32 ? (ak == 8 ? 6 : 1) : ((nt == 128 && ak <= 2) ? 8 : ((nt == 128 && ak <= 8) ? 6 : 1));
+  int ak = std::min(16, next_pow2(std::max(1, (cfg->A + nt - 1) / nt)));
+  int mc = nt == 32 ? (ak == 8 ? 6 : 1) : ((nt == 128 && ak <= 2) ? 8 : ((nt == 128 && ak <= 8) ? 6 : 1));
+  if (cfg->A <= 32) {
+    nt = 16;
+    ak = 2;
+    mc = 8;
+  }
   s = apply_launch(e, nt, ak, mc);
   if (s != KS_OK) {
     delete e;

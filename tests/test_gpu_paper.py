@@ -182,3 +182,22 @@ def test_sliding_window_matches_the_oracle(L, A, mom, launch):
         got = _run_engines(w, plan)
         for f in gs:
             assert np.array_equal(gs[f], got[f]), (plan, f)
+
+
+@pytest.mark.parametrize("L,A,launch,over", [(128, 16, (16, 1, 1), {}), (128, 13, (16, 1, 1), dict(tie_rule=1)),
+                                             (128, 64, (16, 4, 1), {}), (128, 40, (16, 4, 8), dict(mom_pct=50, window=1)),
+                                             (128, 32, (16, 2, 8), {}), (128, 1, (16, 2, 1), {}),
+                                             (100, 20, (16, 2, 1), {}), (40, 64, (16, 4, 1), dict(window=1))])
+def test_half_warp_groups_match_the_oracle(L, A, launch, over):
+    """Two markets per warp (16-lane groups, each with its own segment of
+    shuffles, reductions and barriers): every market and step of an odd
+    number of markets, so one warp's second segment runs out of markets
+    first, against the oracle and the one-warp shape."""
+    w = wl.workload("paper_8192_256", M=23, L=L, A=A, **over)
+    steps = 120
+    gs = _run(w, steps, splits=[50, 70], launch=launch)
+    for m in range(w["M"]):
+        _check_market(w["params"], gs, m, L, A, steps)
+    ref = _run(w, steps, launch=(32, 2, 1) if A <= 64 else None)
+    for f in ref:
+        assert np.array_equal(ref[f], gs[f]), f
