@@ -557,6 +557,7 @@ def run_ours(args):
             sink = torch.empty(sms * 8 * 256 * 8, dtype=torch.uint8, device=dev)
             probes["smem_red_ops_per_s"] = time_probe(ks, ks.KS_PROBE_SMEM_RED, sms * 8, 20000, sink, stream)
             probes["mul_wide_per_s"] = time_probe(ks, ks.KS_PROBE_MUL_WIDE, sms * 8, 100000, sink, stream)
+            probes["mul_hilo_per_s"] = time_probe(ks, ks.KS_PROBE_MUL_HILO, sms * 8, 100000, sink, stream)
             probes["philox_blocks_per_s"] = time_probe(ks, ks.KS_PROBE_PHILOX, sms * 8, 20000, sink, stream)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -568,13 +569,15 @@ def run_ours(args):
             probes["state_io_gbs"] = io_bytes / (e0.elapsed_time(e1) / 1e3) / 1e9
             probes["sms"] = sms
         peaks = measured_peaks()
-        # ALU roofline: Philox needs 20 wide multiplies per agent-event; the
-        # per-SM rate R is the probe's (rounded to a power of two at the
-        # sampled clock), the peak is 152 SMs x R x 2070 MHz.
+        # ALU roofline: Philox needs 20 32 x 32 -> 64 products per agent-event;
+        # the per-SM rate R is the faster probe's (one mad.wide.u32, or a
+        # mul.hi and a mul.lo, per product), rounded to a power of two at the
+        # sampled clock; the peak is 152 SMs x R x 2070 MHz.
         sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1455.0
         R = None
-        if "mul_wide_per_s" in probes:
-            r = probes["mul_wide_per_s"] / (probes["sms"] * sm_mhz * 1e6)
+        rates = [probes[k] for k in ("mul_wide_per_s", "mul_hilo_per_s") if k in probes]
+        if rates:
+            r = max(rates) / (probes["sms"] * sm_mhz * 1e6)
             R = 2 ** round(np.log2(r))
         achieved = PHILOX_MULW_PER_EVENT * events_per_step / mean_launch_s / 1e12
         roofline = None
@@ -583,8 +586,9 @@ def run_ours(args):
             tr = profiled_traffic()
             roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmulwide/s",
                         "frac": achieved / peak, "traffic": tr,
-                        "peak_source": f"derived: {SM_COUNT_NOMINAL} SMs x {R} wide multiplies/clk/SM "
-                                       f"(per-SM rate from the mul-wide probe) x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
+                        "peak_source": f"derived: {SM_COUNT_NOMINAL} SMs x {R} products/clk/SM "
+                                       f"(per-SM rate of the faster product probe, mul.wide or mul.hi + mul.lo) "
+                                       f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
                         "algorithmic": f"{PHILOX_MULW_PER_EVENT} wide multiplies per agent-event x "
                                        f"{events_per_step:.4g} agent-events per launch",
                         "kernel": "plain_kernel", "launch_ms": statistics.mean(launch_ms)}

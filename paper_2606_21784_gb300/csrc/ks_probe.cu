@@ -42,6 +42,22 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_mul_wide(uint32_t iters, 
   sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = x;
 }
 
+// Eight independent chains x = hi(x * C) ^ lo(x * C) ^ j: one 32 x 32 -> 64 product
+// each, as a high-word and a low-word multiply (the form the Philox rounds use).
+__global__ void __launch_bounds__(PROBE_THREADS) probe_mul_hilo(uint32_t iters, uint64_t* sink) {
+  uint32_t x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = threadIdx.x + 977u * j + blockIdx.x;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = __umulhi(x[j], PH_MA) ^ (x[j] * PH_MA) ^ (uint32_t)j;
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc = acc * 31u + x[j];
+  sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = acc;
+}
+
 // The persistent kernel's per-agent draw (StepKey + step_draw_x0), one block per iteration.
 __global__ void __launch_bounds__(PROBE_THREADS) probe_philox(uint32_t iters, uint64_t* sink) {
   uint32_t rk[20];
@@ -78,6 +94,10 @@ extern "C" ks_status ks_probe(int kind, uint32_t blocks, uint32_t iters, void* s
     case KS_PROBE_PHILOX:
       ks::probe_philox<<<blocks, ks::PROBE_THREADS, 0, st>>>(iters, (uint64_t*)sink);
       *ops = lanes;
+      break;
+    case KS_PROBE_MUL_HILO:
+      ks::probe_mul_hilo<<<blocks, ks::PROBE_THREADS, 0, st>>>(iters, (uint64_t*)sink);
+      *ops = lanes * 8.0;
       break;
     default:
       return KS_ERR_INVALID_ARG;
