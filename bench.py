@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-PHILOX_MULW_PER_EVENT = 20  # Philox4x32-10: 10 rounds x 2 wide multiplies per agent-event
+PHILOX_MULW_PER_EVENT = 20  # Philox4x32-10: 10 rounds x 2 32x32->64 products per agent-event
 SM_COUNT_NOMINAL = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
 PROFILE = os.path.join(ROOT, "profiles", "plain_kernel_plain_mix_8192.md")
@@ -584,12 +584,12 @@ def run_ours(args):
         if R:
             peak = SM_COUNT_NOMINAL * R * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
             tr = profiled_traffic()
-            roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmulwide/s",
+            roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tproducts/s",
                         "frac": achieved / peak, "traffic": tr,
                         "peak_source": f"derived: {SM_COUNT_NOMINAL} SMs x {R} products/clk/SM "
                                        f"(per-SM rate of the faster product probe, mul.wide or mul.hi + mul.lo) "
                                        f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
-                        "algorithmic": f"{PHILOX_MULW_PER_EVENT} wide multiplies per agent-event x "
+                        "algorithmic": f"{PHILOX_MULW_PER_EVENT} 32x32->64 products per agent-event x "
                                        f"{events_per_step:.4g} agent-events per launch",
                         "kernel": "plain_kernel", "launch_ms": statistics.mean(launch_ms)}
         rooflines = {}
