@@ -239,8 +239,13 @@ ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l);
 
 /* Switches the ensemble to the batched kernel with the given plan; uploads the
  * work list on `stream` and synchronises it.  cta_threads: 512 or 1024.
- * Uneven ensembles start with a default plan (one bucket per power-of-two
- * (L, A) class, about 8 agents per thread, 512-thread CTAs). */
+ * Uneven ensembles start with a default plan: one bucket per power-of-two
+ * (L, A) class and 512-thread CTAs.  Rule-agent buckets up to A = 512 take
+ * 128 threads x 4 agents, up to 2048 A/8 threads x 8 (at least 128), up to
+ * 8192 A/16 x 16, above that 512 x 32; policy buckets take the tightest
+ * compiled fit near 8 agents per thread.  A market spreads its agents over
+ * its group, ceil(A / group_threads) consecutive agents per thread; results
+ * do not depend on the plan. */
 ks_status ks_set_batch_plan(ks_ensemble* e, int32_t cta_threads, const ks_bucket* buckets, int32_t n_buckets,
                             void* stream);
 
