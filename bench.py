@@ -49,6 +49,8 @@ def parse():
                     help="threads,agents_per_thread,reg_cap (paper workloads: threads,agents_per_thread,min_ctas); "
                          "skips the autotuner")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / learned comparison runs")
+    ap.add_argument("--engine", default="persistent", choices=["persistent", "naive"],
+                    help="paper-agent workloads: the persistent kernel or the naive one-thread-per-market engine")
     return ap.parse_args()
 
 
@@ -657,9 +659,11 @@ def run_paper(args, w, rank, world, dev):
         autotune.apply(ens, w)
     S = int(w["S"])
     events_per_step = float(w["M"]) * w["A"] * S
+    naive = args.engine == "naive"
+    run = ens.step_naive if naive else ens.step  # the naive engine: one launch per simulated step
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        ens.step(S, stream)
+        run(S, stream)
     torch.cuda.synchronize()
     sharding.barrier()
     sampler = ClockSampler(torch.cuda.current_device())
@@ -670,7 +674,7 @@ def run_paper(args, w, rank, world, dev):
     t0e.record(stream)
     for e0, e1 in ev:
         e0.record(stream)
-        ens.step(S, stream)
+        run(S, stream)
         e1.record(stream)
     t1e.record(stream)
     torch.cuda.synchronize()
@@ -680,13 +684,13 @@ def run_paper(args, w, rank, world, dev):
     value = world * events_per_step * args.steps / (total_ms / 1e3)
     if ens.sync(timeout_ms=600_000) != ks.KS_OK:
         raise RuntimeError("paper ensemble reported a device error")
-    ens.step(S, stream)  # one untimed round trip first, as in the main workload
+    run(S, stream)  # one untimed round trip first, as in the main workload
     ens.read_state(["bid", "ask", "last_tick", "trades", "sum_volume"], stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     nbytes = 0
     for _ in range(args.e2e_steps):
-        ens.step(S, stream)
+        run(S, stream)
         st = ens.read_state(["bid", "ask", "last_tick", "trades", "sum_volume"], stream)
         nbytes = sum(a.nbytes for a in st.values())
     e2e_s = sharding.max_over_ranks(time.perf_counter() - t0, dev)
@@ -696,13 +700,16 @@ def run_paper(args, w, rank, world, dev):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                "data": "synthetic",
                "config": {"workload": args.workload, "M": int(w["M"]), "L": int(w["L"]), "A": int(w["A"]), "S": S,
-                          "model": "the paper's agents (tick-aggregated book)", "launch": ens.get_launch(),
-                          "l2": "book state resident on chip; 1 MiB of global state per 256 markets"},
+                          "model": "the paper's agents (tick-aggregated book)", "engine": args.engine,
+                          "launch": "one thread per market, one launch per step" if naive else ens.get_launch(),
+                          "l2": ("book rows in global memory, read and written every step (L2-resident at "
+                                 "this size)" if naive else
+                                 "book state resident on chip; 1 MiB of global state per 256 markets")},
                "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
-               "gpu_launches": 2 * args.steps, "roofline": None, "clocks": clocks,
-               "paper_context": {"value": PAPER_TABLE_III.get((int(w["M"]), int(w["A"]))),
-                                 "hardware": "RTX 5090 (sm_120), Table III"}}
+               "gpu_launches": (2 * S if naive else 2) * args.steps, "roofline": None, "clocks": clocks,
+               "paper_context": {"value": (PAPER_NAIVE if naive else PAPER_TABLE_III).get((int(w["M"]), int(w["A"]))),
+                                 "hardware": "RTX 5090 (sm_120), Table III" + (", Naive CUDA" if naive else "")}}
         print(json.dumps(out), flush=True)
     ens.close()
     sharding.finalize()
