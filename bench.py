@@ -542,10 +542,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     sharding.barrier()
     t0 = time.perf_counter()
+    phases = []
     for _ in range(args.e2e_steps):
-        ks.ks_write_state(ens.handle, view, stream)   # host -> device: the step's inputs
+        a = time.perf_counter()
+        ks.ks_write_state(ens.handle, view, stream)   # host -> device: the step's inputs (syncs)
+        b = time.perf_counter()
         ks.ks_step_n(ens.handle, S, stream)
         ks.ks_read_state(ens.handle, view, stream)    # device -> host: the step's result (syncs)
+        phases.append((b - a, time.perf_counter() - b))
     e2e_s = time.perf_counter() - t0
     e2e_s = sharding.max_over_ranks(e2e_s, dev)
     e2e_value = world * events_per_step * args.e2e_steps / e2e_s
@@ -626,7 +630,10 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 (resident state {state_bytes / 2**20:.0f} MiB)",
                        "launch": launch, "parallelism": f"markets sharded over {world} GPU(s)"},
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": state_bytes,
-                    "d2h_bytes_per_step": state_bytes},
+                    "d2h_bytes_per_step": state_bytes,
+                    "breakdown_ms": {"write_state": round(1e3 * statistics.median(p[0] for p in phases), 2),
+                                     "step_and_read_state": round(1e3 * statistics.median(p[1] for p in phases), 2),
+                                     "device_launch": round(1e3 * mean_launch_s, 2)}},
             "gpu_launches": 2 * args.steps,
             "roofline": roofline,
             "rooflines": rooflines,
@@ -694,6 +701,19 @@ def run_paper(args, w, rank, world, dev):
         st = ens.read_state(["bid", "ask", "last_tick", "trades", "sum_volume"], stream)
         nbytes = sum(a.nbytes for a in st.values())
     e2e_s = sharding.max_over_ranks(time.perf_counter() - t0, dev)
+    roofline = None
+    if rank == 0 and not naive and not args.no_probes:
+        # ALU roofline: two SplitMix64 mixes per agent-event against the mix
+        # rate of a pure loop of the kernel's own mix routine (measured here)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        sink = torch.empty(sms * 8 * 256 * 8, dtype=torch.uint8, device=dev)
+        peak = time_probe(ks, ks.KS_PROBE_SPLITMIX, sms * 8, 2000, sink, stream)
+        achieved = 2.0 * events_per_step / (total_ms / args.steps / 1e3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gmix/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "measured: the kernel's SplitMix64 mix routine in a loop with nothing else",
+                    "algorithmic": f"2 SplitMix64 mixes per agent-event x {events_per_step:.4g} agent-events per launch",
+                    "kernel": "paper_kernel"}
     if rank == 0:
         out = {"metric": "agent_events_per_s", "value": value, "unit": "events/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -707,7 +727,7 @@ def run_paper(args, w, rank, world, dev):
                                  "book state resident on chip; 1 MiB of global state per 256 markets")},
                "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
-               "gpu_launches": (2 * S if naive else 2) * args.steps, "roofline": None, "clocks": clocks,
+               "gpu_launches": (2 * S if naive else 2) * args.steps, "roofline": roofline, "clocks": clocks,
                "paper_context": {"value": (PAPER_NAIVE if naive else PAPER_TABLE_III).get((int(w["M"]), int(w["A"]))),
                                  "hardware": "RTX 5090 (sm_120), Table III" + (", Naive CUDA" if naive else "")}}
         print(json.dumps(out), flush=True)

@@ -28,8 +28,10 @@ typedef enum ks_probe_kind {
   KS_PROBE_SMEM_RED = 0,  /* red.shared.add.u32, each lane on its own bank; ops = lane-atomics */
   KS_PROBE_MUL_WIDE = 1,  /* independent mad.wide.u32 chains; ops = wide multiplies            */
   KS_PROBE_PHILOX = 2,    /* the kernel's per-agent Philox4x32-10 draw; ops = blocks           */
-  KS_PROBE_MUL_HILO = 3   /* independent chains of 32 x 32 -> 64 products taken as mul.hi and
+  KS_PROBE_MUL_HILO = 3,  /* independent chains of 32 x 32 -> 64 products taken as mul.hi and
                              mul.lo (the Philox rounds' form); ops = products                 */
+  KS_PROBE_SPLITMIX = 4   /* the paper-agent kernel's two SplitMix64 mixes per agent-step, in a
+                             loop with nothing else; ops = mixes                              */
 } ks_probe_kind;
 
 /* Launches probe `kind` over `blocks` CTAs of 256 threads, `iters` iterations

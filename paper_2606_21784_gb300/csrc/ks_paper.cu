@@ -503,6 +503,25 @@ __global__ void paper_init_kernel(PaperParams P) {
 
 __global__ void paper_step_bump(uint64_t* step, uint32_t n) { *step += n; }
 
+// Roofline probe: the two SplitMix64 mixes of one agent-step (channels 0 and 1)
+// in a loop with nothing else, one agent per thread and iteration.
+__global__ void __launch_bounds__(256) probe_sm64(uint32_t iters, uint64_t* sink) {
+  uint64_t c = SM64_GID * (uint64_t)(blockIdx.x * 256u + threadIdx.x);
+  uint64_t acc = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const uint64_t u0 = sm64_mix(c), u1 = sm64_mix(c + SM64_GAMMA);
+    acc ^= u0 ^ (u1 << 1);
+    c += 8ull * SM64_GAMMA;
+  }
+  sink[(size_t)blockIdx.x * 256u + threadIdx.x] = acc;
+}
+
+// Launches probe_sm64 (256-thread blocks); returns the mixes it computes.
+double launch_probe_sm64(uint32_t blocks, uint32_t iters, uint64_t* sink, cudaStream_t st) {
+  probe_sm64<<<blocks, 256, 0, st>>>(iters, sink);
+  return 2.0 * (double)blocks * 256.0 * (double)iters;
+}
+
 // ---- the naive engine: one thread per market, one launch per step (Sec. III-F, Sec. IV-I) ----
 // Same model, decisions and draws as paper_kernel (paper_class / paper_order),
 // without its two design choices: the book stays in global memory (each step

@@ -78,6 +78,10 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_philox(uint32_t iters, ui
 
 }  // namespace ks
 
+namespace ks {
+double launch_probe_sm64(uint32_t blocks, uint32_t iters, uint64_t* sink, cudaStream_t st);
+}
+
 extern "C" ks_status ks_probe(int kind, uint32_t blocks, uint32_t iters, void* sink, void* stream, double* ops) {
   if (!sink || !ops || blocks == 0) return KS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -98,6 +102,9 @@ extern "C" ks_status ks_probe(int kind, uint32_t blocks, uint32_t iters, void* s
     case KS_PROBE_MUL_HILO:
       ks::probe_mul_hilo<<<blocks, ks::PROBE_THREADS, 0, st>>>(iters, (uint64_t*)sink);
       *ops = lanes * 8.0;
+      break;
+    case KS_PROBE_SPLITMIX:
+      *ops = ks::launch_probe_sm64(blocks, iters, (uint64_t*)sink, st);
       break;
     default:
       return KS_ERR_INVALID_ARG;

@@ -370,7 +370,7 @@ def ks_mlp_export(params, blob=None, stream=None):
     return blob
 
 
-KS_PROBE_SMEM_RED, KS_PROBE_MUL_WIDE, KS_PROBE_PHILOX, KS_PROBE_MUL_HILO = 0, 1, 2, 3
+KS_PROBE_SMEM_RED, KS_PROBE_MUL_WIDE, KS_PROBE_PHILOX, KS_PROBE_MUL_HILO, KS_PROBE_SPLITMIX = 0, 1, 2, 3, 4
 
 
 def ks_probe(kind: int, blocks: int, iters: int, sink_ptr: int, stream=None) -> float:
