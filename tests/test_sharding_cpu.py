@@ -54,3 +54,23 @@ def test_single_process_defaults():
     wl = sharding.shard(workloads.workload("plain_zi_64"), 0, 1)
     assert wl["market_base"] == 0
     assert sharding.max_over_ranks(3.0) == 3.0
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """The reference arm as the scaling run launches it: two ranks through
+    torch.distributed.run; rank 0 alone times the oracle and prints one JSON
+    line, the other rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "1", "--sim-steps", "5"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
