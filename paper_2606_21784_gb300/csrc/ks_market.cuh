@@ -404,11 +404,26 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
   const int D0 = offD + sufB;          // D_cum at my first tick
   const int Sb0 = offS + preS - sumS;  // S_cum just below my first tick
+  // A tick range with no orders (the rule-agent kernels): D and S are
+  // constant on it, so V is min(D0, Sb0) on every tick, its lowest and
+  // highest maximisers are the range's ends, and nothing in it changes.
+  const int cnt = LTC > 0 ? (mine ? LTC : 0) : max(0, min(LT, L - p0));  // in-grid ticks
+  const bool idle = !FEAT && cnt > 0 && sumB == 0 && sumS == 0;
   {
     int D = D0, Sb = Sb0;
     int bestV = -1, lo = 4095, hi = 0;
     unsigned long long kT = 0ull;
-    const int n = LTC > 0 ? (mine ? LTC : 0) : LT;
+    const int n = idle ? 0 : (LTC > 0 ? (mine ? LTC : 0) : LT);
+    if (idle) {
+      bestV = min(D0, Sb0);
+      lo = p0;
+      hi = p0 + cnt - 1;
+      if (tie1) {
+        const int imb = min(abs(D0 - Sb0), (1 << 22) - 1);
+        kT = ((unsigned long long)(uint32_t)bestV << 34) | ((unsigned long long)((1 << 22) - 1 - imb) << 12) |
+             (4095u - p0);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < (LTC > 0 ? LTC : 1); ++i) {
       // LTC == 0 runs this body in the loop below instead
@@ -429,7 +444,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
       }
     }
     if constexpr (LTC == 0) {
-      for (int i = 0; i < LT; ++i) {
+      for (int i = 0; i < n; ++i) {
         const int p = p0 + i;
         if (p < L) {
           const int b = book[2 * p];
@@ -479,7 +494,11 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   // marginal ticks publish R_b = V* - D_cum[p_hi + 1] and R_s = V* - S_cum[p_lo - 1];
   // a carried book keeps what did not trade, a discarded book is emptied.
   const int nl = trade ? c.pstar : last;  // last clearing tick after this step (policy depth)
-  if constexpr (LTC > 0) {
+  if (idle) {
+    // nothing rests here; a marginal tick in the range still publishes its remainder
+    if (trade && c.p_hi >= p0 && c.p_hi < p0 + cnt) sm.rem[0] = c.vstar - D0;
+    if (trade && c.p_lo >= p0 && c.p_lo < p0 + cnt) sm.rem[1] = c.vstar - Sb0;
+  } else if constexpr (LTC > 0) {
     if (mine) {
       int D = D0, Sb = Sb0;
 #pragma unroll
