@@ -495,7 +495,9 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   // a carried book keeps what did not trade, a discarded book is emptied.
   const int nl = trade ? c.pstar : last;  // last clearing tick after this step (policy depth)
   if (idle) {
-    // nothing rests here; a marginal tick in the range still publishes its remainder
+    // nothing rests here.  A marginal tick holds orders (D_cum drops right after
+    // p_hi, so BUY[p_hi] > 0; S_cum rises at p_lo, so SELL[p_lo] > 0), hence lies
+    // in no empty range; the remainders below keep the rule explicit regardless.
     if (trade && c.p_hi >= p0 && c.p_hi < p0 + cnt) sm.rem[0] = c.vstar - D0;
     if (trade && c.p_lo >= p0 && c.p_lo < p0 + cnt) sm.rem[1] = c.vstar - Sb0;
   } else if constexpr (LTC > 0) {
