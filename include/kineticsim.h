@@ -345,7 +345,8 @@ typedef struct ks_paper_state_view {
  * shape: `threads` per market (16: half a warp per market, eight markets
  * per 128-thread CTA, agents_per_thread 1, 2 or 4; 32: one warp per market,
  * four markets per 128-thread CTA, agents_per_thread 1, 2, 4, 8, 16 or 32;
- * 128, 256: agents per thread 1..16; 512, 1024: 16), threads *
+ * 64: agents per thread 4 or 8; 128, 256: agents per thread 1..16; 512,
+ * 1024: 16), threads *
  * agents_per_thread >= A; min_ctas 0 or 1 = the compiler's register choice,
  * else the register cap of min_ctas resident CTAs per SM (compiled: 16 x 2,
  * 16 x 4, 32 x 1, 32 x 2, 128 x 1 and 128 x 2 at 8; 32 x 8, 128 x 4 and

@@ -183,7 +183,7 @@ PAPER_SHAPES = ((32, 1, 1), (32, 2, 1), (32, 4, 1), (32, 1, 8), (32, 2, 8), (32,
                 (32, 32, 1), (128, 1, 1), (128, 2, 1), (128, 4, 1),
                 (128, 8, 1), (128, 16, 1), (128, 1, 8), (128, 2, 8), (128, 4, 6), (128, 8, 6), (256, 1, 1),
                 (256, 2, 1), (256, 4, 1), (256, 8, 1), (256, 16, 1), (512, 16, 1), (1024, 16, 1),
-                (16, 1, 1), (16, 2, 1), (16, 4, 1), (16, 2, 8), (16, 4, 8))
+                (16, 1, 1), (16, 2, 1), (16, 4, 1), (16, 2, 8), (16, 4, 8), (64, 4, 1), (64, 8, 1))
 
 
 def tune_paper(w: dict, steps: int = 100, use_cache: bool = True, verbose: bool = False) -> dict:

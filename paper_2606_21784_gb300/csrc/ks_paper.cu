@@ -667,7 +667,7 @@ static const PaperVariant kPaperVariants[] = {
     KS_PV(128, 128, 4, 6),   KS_PV(128, 128, 8, 6),   KS_PV(256, 256, 1, 1),   KS_PV(256, 256, 2, 1),
     KS_PV(256, 256, 4, 1),   KS_PV(256, 256, 8, 1),   KS_PV(256, 256, 16, 1),  KS_PV(512, 512, 16, 1),
     KS_PV(1024, 1024, 16, 1), KS_PV(128, 16, 1, 1),    KS_PV(128, 16, 2, 1),    KS_PV(128, 16, 4, 1),
-    KS_PV(128, 16, 2, 8),    KS_PV(128, 16, 4, 8)};
+    KS_PV(128, 16, 2, 8),    KS_PV(128, 16, 4, 8),    KS_PV(64, 64, 4, 1),     KS_PV(64, 64, 8, 1)};
 #undef KS_PV
 
 }  // namespace ks
@@ -841,7 +841,7 @@ ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws
   // default shape (measured on GB300 at L = 128 with 8192 markets): half a
   // warp per market up to 32 agents, a warp up to 256 agents, else 128
   // threads per market with up to 16 agents each, under the register caps
-  // that won
+  // that won; two warps per market when only 513 to 2048 markets share the GPU
   int nt = cfg->A <= 256 ? 32 : 128;
   while (nt < 1024 && (int64_t)nt * 16 < cfg->A) nt *= 2;
   int ak = std::min(16, next_pow2(std::max(1, (cfg->A + nt - 1) / nt)));
@@ -850,6 +850,11 @@ ks_status ks_paper_create(const ks_paper_config* cfg, void* workspace, size_t ws
     nt = 16;
     ak = 2;
     mc = 8;
+  } else if (cfg->A <= 512 && cfg->n_markets > 512 && cfg->n_markets <= 2048) {
+    // too few markets to fill the GPU one warp each: two warps per market
+    nt = 64;
+    ak = cfg->A <= 256 ? 4 : 8;
+    mc = 1;
   }
   s = apply_launch(e, nt, ak, mc);
   if (s != KS_OK) {

@@ -56,7 +56,7 @@ def test_launch_shapes_and_split_calls_agree():
     for launch, splits in (((128, 2, 1), [90]), ((256, 1, 1), [90]), ((128, 4, 1), [30, 60]),
                            ((256, 2, 1), [1, 88, 1]), ((512, 16, 1), [90]), ((128, 16, 1), [45, 45]),
                            ((128, 2, 8), [90]), ((128, 8, 6), [60, 30]), ((128, 4, 6), [90]), ((32, 8, 1), [90]),
-                           ((32, 8, 6), [40, 50]), ((32, 32, 1), [90])):
+                           ((32, 8, 6), [40, 50]), ((32, 32, 1), [90]), ((64, 4, 1), [90]), ((64, 8, 1), [30, 60])):
         got = _run(w, 90, splits=splits, launch=launch, trace=False)
         for f in ref:
             assert np.array_equal(ref[f], got[f]), (launch, f)
@@ -201,3 +201,17 @@ def test_half_warp_groups_match_the_oracle(L, A, launch, over):
     ref = _run(w, steps, launch=(32, 2, 1) if A <= 64 else None)
     for f in ref:
         assert np.array_equal(ref[f], gs[f]), f
+
+
+def test_default_launch_for_mid_sized_ensembles():
+    """513 to 2048 markets of 33 to 512 agents default to two warps per market;
+    sampled markets match the oracle every step."""
+    w = wl.workload("paper_8192_256", M=700, L=128, A=150)
+    ens = ks.PaperEnsemble(w, trace_markets=w["M"], trace_steps=60)
+    assert ens.get_launch()["threads"] == 64
+    ens.step(60)
+    assert ens.sync(timeout_ms=300_000) == ks.KS_OK
+    gs = ens.read_state()
+    ens.close()
+    for m in (0, 1, 349, 698, 699):
+        _check_market(w["params"], gs, m, 128, 150, 60)
