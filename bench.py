@@ -544,12 +544,16 @@ def run_ours(args):
     t0 = time.perf_counter()
     phases = []
     for _ in range(args.e2e_steps):
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
         a = time.perf_counter()
         ks.ks_write_state(ens.handle, view, stream)   # host -> device: the step's inputs (syncs)
         b = time.perf_counter()
+        k0.record(stream)
         ks.ks_step_n(ens.handle, S, stream)
+        k1.record(stream)
         ks.ks_read_state(ens.handle, view, stream)    # device -> host: the step's result (syncs)
-        phases.append((b - a, time.perf_counter() - b))
+        phases.append((b - a, time.perf_counter() - b, k0.elapsed_time(k1) / 1e3))
     e2e_s = time.perf_counter() - t0
     e2e_s = sharding.max_over_ranks(e2e_s, dev)
     e2e_value = world * events_per_step * args.e2e_steps / e2e_s
@@ -633,6 +637,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": state_bytes,
                     "breakdown_ms": {"write_state": round(1e3 * statistics.median(p[0] for p in phases), 2),
                                      "step_and_read_state": round(1e3 * statistics.median(p[1] for p in phases), 2),
+                                     "kernel_in_round_trip": round(1e3 * statistics.median(p[2] for p in phases), 2),
                                      "device_launch": round(1e3 * mean_launch_s, 2)}},
             "gpu_launches": 2 * args.steps,
             "roofline": roofline,
