@@ -150,3 +150,26 @@ def test_error_word_clear_and_sync_deadline():
     assert ens.sync(timeout_ms=60_000) == ks.KS_OK
     assert ks.ks_error_word(ens.handle) == 0
     torch.cuda.synchronize()
+
+
+def test_plain_kernel_state_paths_on_uneven_offsets():
+    """The plain kernel's 256-bit, 128-bit and scalar state paths: markets whose
+    agent offsets fall on 32-byte, 16-byte and unaligned boundaries (offsets
+    0, 4096, 8188, 9189, ... agents), every step against the oracle; then a
+    zero-step launch (load, rebuild the book, store) leaves the state unchanged."""
+    import torch
+    As = np.array([4096, 4092, 1001, 4088, 8, 7, 4096, 2048], np.int32)
+    Ls = np.full(len(As), 512, np.int32)
+    w = wl.workload("plain_mix_8192", M=len(As))
+    steps = 30
+    ens, gs = _run_gpu(w, steps, trace_markets=len(As), launch=dict(threads=256, agents_per_thread=16), L=Ls, A=As)
+    assert ens.batch_info()["batched"] == 0
+    ref = oracle_markets(w["params"], range(len(As)), Ls, As, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
+    before = ens.read_state()
+    ks.ks_probe_state_io(ens.handle)
+    torch.cuda.synchronize()
+    after = ens.read_state()
+    for f in before:
+        assert np.array_equal(before[f], after[f]), f
