@@ -404,11 +404,11 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   const int offS = (int)__reduce_add_sync(0xffffffffu, (lane < wid) ? (unsigned)sm.wS[lane] : 0u);
   const int D0 = offD + sufB;          // D_cum at my first tick
   const int Sb0 = offS + preS - sumS;  // S_cum just below my first tick
-  // A tick range with no orders (the rule-agent kernels): D and S are
-  // constant on it, so V is min(D0, Sb0) on every tick, its lowest and
-  // highest maximisers are the range's ends, and nothing in it changes.
+  // A tick range with no orders: D and S are constant on it, so V is
+  // min(D0, Sb0) on every tick, its lowest and highest maximisers are the
+  // range's ends, and nothing in it changes (policy depth there is zero).
   const int cnt = LTC > 0 ? (mine ? LTC : 0) : max(0, min(LT, L - p0));  // in-grid ticks
-  const bool idle = !FEAT && cnt > 0 && sumB == 0 && sumS == 0;
+  const bool idle = cnt > 0 && sumB == 0 && sumS == 0;
   {
     int D = D0, Sb = Sb0;
     int bestV = -1, lo = 4095, hi = 0;
@@ -500,6 +500,14 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
     // in no empty range; the remainders below keep the rule explicit regardless.
     if (trade && c.p_hi >= p0 && c.p_hi < p0 + cnt) sm.rem[0] = c.vstar - D0;
     if (trade && c.p_lo >= p0 && c.p_lo < p0 + cnt) sm.rem[1] = c.vstar - Sb0;
+    if constexpr (FEAT) {
+      // the policy depth around the last tick: zero on an empty range
+      const int f0 = max(p0, nl - 4), f1 = min(p0 + cnt - 1, nl + 4);
+      for (int p = f0; p <= f1; ++p) {
+        if (p > nl) sm.feat[p - nl - 1] = 0;
+        if (p < nl) sm.feat[4 + nl - p - 1] = 0;
+      }
+    }
   } else if constexpr (LTC > 0) {
     if (mine) {
       int D = D0, Sb = Sb0;
