@@ -4,10 +4,12 @@
  * The paper gives no hardware peaks for this method (its kernel is described as
  * arithmetic-bound, Sec. V).  These probes measure the ceilings the persistent
  * kernel is held against: conflict-free shared-memory atomic throughput (one
- * order aggregated per agent-event), 32x32->64-bit integer multiply throughput
- * (Philox4x32-10 needs 20 per agent-event), the Philox block rate of the
- * kernel's own draw routine, and the HBM bandwidth of the kernel's state load
- * and store phases.
+ * order aggregated per agent-event), 32x32->64-bit product throughput as one
+ * wide multiply or as a high-word and a low-word multiply (Philox4x32-10 needs
+ * 20 products per agent-event), the Philox block rate of the kernel's own
+ * draw routine, the SplitMix64 mix rate of the paper-agent kernel's routine
+ * (two mixes per agent-event), and the HBM bandwidth of the kernel's state
+ * load and store phases.
  *
  * Conventions as in kineticsim.h: KS_OK on success, work queued on `stream`,
  * the caller times it (CUDA events on the same stream).
