@@ -56,3 +56,25 @@ def test_window_traces_take_the_absolute_price_as_is():
     r = np.array([-4, -65, 0, 305], np.float64)
     assert abs(f["volatility"] - r.std()) < 1e-12
     assert f["volume_per_step"] == 3.75 and abs(f["mean_price"] - (60 - 5 - 5 + 300) / 4) < 1e-12
+
+
+def test_oracle_sweep_momentum_runs_away_on_a_window():
+    """The composition sweep's finding on the oracle itself (CPU, small): on a
+    sliding window the spread of the price level grows with the momentum
+    share, while without momentum the price stays near its start and returns
+    reverse at lag 1 (bid-ask bounce)."""
+    import oracle as o
+    from paper_2606_21784_gb300 import workloads as wl
+
+    def run(mom):
+        w = wl.workload("paper_8192_256", M=6, L=128, A=128, mom_pct=mom, maker_pct=15, window=1)
+        tr = np.zeros((6, 300, 2), np.int32)
+        for m in range(6):
+            bk = o.paper_init(m, 128, 128)
+            tp, tv = o.paper_run(w["params"], bk, 0, 300)
+            tr[m, :, 0], tr[m, :, 1] = tp, tv
+        return dynamics.facts(tr, 128, window=True)
+
+    f0, f50 = run(0), run(50)
+    assert f50["price_std"] > 5 * f0["price_std"]
+    assert f0["acf_r"][0] < -0.1 and f0["volume_per_step"] > 0
