@@ -35,6 +35,23 @@ MUTANTS = {
     "mlp_mse_factor": ("dz[KO_OUT - 1] = 2.0 * e;", "dz[KO_OUT - 1] = e;"),
     "mlp_sample_le": ("if (u < c) return i;", "if (u <= c) return i;"),
     "mlp_qty_rounding": ("double q = floor(exp(z[KO_OUT - 1]) + 0.5);", "double q = floor(exp(z[KO_OUT - 1]));"),
+    # the policy's raw features and its optimiser
+    "features_sides_swapped": ("raw[9 + k] = (pa >= 0 && pa < L) ? (int32_t)sell[pa] : 0;",
+                               "raw[9 + k] = (pa >= 0 && pa < L) ? (int32_t)buy[pa] : 0;"),
+    "features_k_off_by_one": ("int32_t pa = ms->last + k, pb = ms->last - k;",
+                              "int32_t pa = ms->last + k - 1, pb = ms->last - k + 1;"),
+    "features_grid_edge": ("raw[13 + k] = (pb >= 0 && pb < L)", "raw[13 + k] = (pb > 0 && pb < L)"),
+    "features_after_cancellation": (
+        "        if (ag->qty[a] <= 0) continue;\n        if (ag->side[a] == 0) buy[",
+        "        uint32_t cw[4];\n        ko_draw(P->seed, s, (uint32_t)a, m, 0u, cw);\n"
+        "        if (ag->qty[a] <= 0 || (P->carry_book && cw[0] < P->cancel_thresh)) continue;\n"
+        "        if (ag->side[a] == 0) buy["),
+    "adam_no_bias_correction": ("w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);",
+                                "w[i] -= lr * m[i] / (sqrt(v[i]) + eps);"),
+    "adam_eps_inside_sqrt": ("w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);",
+                             "w[i] -= lr * (m[i] / c1) / sqrt(v[i] / c2 + eps);"),
+    "adam_b1_in_second_moment": ("v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];",
+                                 "v[i] = b1 * v[i] + (1.0 - b1) * g[i] * g[i];"),
     # the paper-agent mode
     "paper_maker_parity": ("sd = (int32_t)(((int64_t)a + (int64_t)s) % 2);",
                            "sd = (int32_t)(((int64_t)a + (int64_t)s + 1) % 2);"),
