@@ -167,7 +167,9 @@ typedef struct ks_launch {
   int32_t reg_cap;            /* register cap class: 0 compiler's choice, 1 at most
                                  128 registers per thread (two 256-thread CTAs per
                                  SM), 2 at most 85 (three; 128- and 256-thread CTAs
-                                 with 1, 2 or 4 agents per thread, aggregate = 0);
+                                 with 1, 2 or 4 agents per thread, aggregate = 0),
+                                 3 at most 64 (32 warps per SM; 512 x 8 and
+                                 1024 x 4, aggregate = 0);
                                  policy-capable kernels: 0 or 1 */
 } ks_launch;
 
@@ -417,6 +419,11 @@ typedef struct ks_capture {
   unsigned long long* record_count;
   uint32_t* decisions;
   unsigned long long* policy_count;  /* device counter += policy decisions evaluated (NULL = off) */
+  /* FP32 logits of every policy decision of the traced markets, [trace_steps]
+   * [agents of the traced markets][37], indexed like `decisions` (absolute
+   * step, ensemble agent index); entries without a decision are left as they
+   * are (NULL = off; needs trace_markets and trace_steps). */
+  float* logits;
 } ks_capture;
 
 /* Sets the ensemble's captures (NULL fields switch a capture off).  Capturing
@@ -447,10 +454,13 @@ ks_status ks_mlp_forward(const void* params, const float* X, int64_t n, float* Z
  *  - More than KS_NOALLOC_MAX_MARKETS markets: KS_ERR_UNSUPPORTED.
  *  - The ensemble's device must be current: else KS_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for the life of the process; the
+ *    entry point does not survive a cudaDeviceReset of that device.
  *  - Every call shares the array and overwrites it (it clears the ticket and
- *    copies the schedule from the host on `stream` before the launch), so
- *    calls that overlap on the GPU, on any streams, race.
+ *    copies the schedule from pageable host memory on `stream` before the
+ *    launch), so calls that overlap on the GPU, on any streams, race.
+ *  - A call on a stream that is being captured returns KS_ERR_UNSUPPORTED:
+ *    the host copy of the schedule cannot be recorded safely.
  * Otherwise as ks_step_n: steps [s, s + n_steps), results identical.
  */
 #define KS_NOALLOC_MAX_MARKETS 32768

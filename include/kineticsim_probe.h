@@ -32,8 +32,15 @@ typedef enum ks_probe_kind {
   KS_PROBE_PHILOX = 2,    /* the kernel's per-agent Philox4x32-10 draw; ops = blocks           */
   KS_PROBE_MUL_HILO = 3,  /* independent chains of 32 x 32 -> 64 products taken as mul.hi and
                              mul.lo (the Philox rounds' form); ops = products                 */
-  KS_PROBE_SPLITMIX = 4   /* the paper-agent kernel's two SplitMix64 mixes per agent-step, in a
+  KS_PROBE_SPLITMIX = 4,  /* the paper-agent kernel's two SplitMix64 mixes per agent-step, in a
                              loop with nothing else; ops = mixes                              */
+  KS_PROBE_WAIT_TIMEOUT = 5 /* failure detection, not a roofline: one warpgroup runs the policy
+                             path's bounded tensor-core wait on an mbarrier that nothing
+                             arrives at (no MMA issued), which must give up after its poll
+                             limit (well under a few seconds) and return; `blocks` and
+                             `iters` are ignored, uint32 sink[0] receives the error word
+                             (0x8 on a timeout) and sink[1] is 1 when the warpgroup stayed
+                             aborted for its next wait; ops = 1                             */
 } ks_probe_kind;
 
 /* Launches probe `kind` over `blocks` CTAs of 256 threads, `iters` iterations

@@ -534,7 +534,10 @@ typedef struct {
  *              KO_REC_WORDS int32 each: raw features (KO_NRAW), side,
  *              offset index, qty, agent class.  The offset counts toward
  *              the opposite side (tick - last for a buy, last - tick for a
- *              sell), clamped to [-16, 16], plus 16. */
+ *              sell), clamped to [-16, 16], plus 16;
+ *  logit_out:  with mlp_w, the fp64 logits of every policy decision, entry
+ *              (j * A + a) * KO_OUT for step j of the call and agent a
+ *              (entries without a decision are not written). */
 #define KO_REC_WORDS (KO_NRAW + 4)
 typedef struct {
   const double* mlp_w;
@@ -545,6 +548,7 @@ typedef struct {
   int64_t rec_count;
   int64_t mlp_checked;
   int64_t mlp_mismatch;
+  double* logit_out;
 } ko_options;
 
 /* Market-level raw features at the start of a step (see ko_mlp_features). */
@@ -560,16 +564,18 @@ static void ko_raw_features(const ko_market_scalars* ms, int32_t L, const int64_
   }
 }
 
-/* The policy's decision for agent a at step s (fp64). */
+/* The policy's decision for agent a at step s (fp64); z_out (nullable)
+ * receives its logits. */
 static void ko_mlp_decide(const ko_params* P, const double* w, uint32_t m, int32_t L, int32_t A, uint32_t s,
                           int32_t a, const int32_t* raw_mkt, int32_t inv, int32_t last, int32_t* side,
-                          int32_t* tick, int32_t* qty) {
+                          int32_t* tick, int32_t* qty, double* z_out) {
   int32_t raw[KO_NRAW];
   memcpy(raw, raw_mkt, sizeof(raw));
   raw[8] = inv;
   double x[KO_IN], z[KO_OUT];
   ko_mlp_features(raw, A, x);
   ko_mlp_forward(w, x, 1, z);
+  if (z_out) memcpy(z_out, z, sizeof(z));
   uint32_t u[4];
   ko_draw(P->seed, s, (uint32_t)a, m, 3u, u);
   int32_t oi;
@@ -626,13 +632,15 @@ int ko_run_market(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agent
           if (sd < 0 || sd > 2 || (sd < 2 && (tk < 0 || tk >= L || q <= 0))) { rc = -6; goto done; }
           if (mlp_w) {
             int32_t os, ot, oq;
-            ko_mlp_decide(P, mlp_w, m, L, A, s, a, raw_mkt, ag->inv[a], ms->last, &os, &ot, &oq);
+            ko_mlp_decide(P, mlp_w, m, L, A, s, a, raw_mkt, ag->inv[a], ms->last, &os, &ot, &oq,
+                          opt->logit_out ? opt->logit_out + ((size_t)j * (size_t)A + (size_t)a) * KO_OUT : NULL);
             opt->mlp_checked += 1;
             if (os != sd || (sd < 2 && (ot != tk || oq != q))) opt->mlp_mismatch += 1;
           }
         } else {
           if (!mlp_w) { rc = -5; goto done; }
-          ko_mlp_decide(P, mlp_w, m, L, A, s, a, raw_mkt, ag->inv[a], ms->last, &sd, &tk, &q);
+          ko_mlp_decide(P, mlp_w, m, L, A, s, a, raw_mkt, ag->inv[a], ms->last, &sd, &tk, &q,
+                        opt->logit_out ? opt->logit_out + ((size_t)j * (size_t)A + (size_t)a) * KO_OUT : NULL);
         }
         if (sd == 2) continue; /* pass: no order this step */
         ag->side[a] = sd;

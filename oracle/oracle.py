@@ -85,7 +85,7 @@ class _Replay(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("mlp_w", ctypes.c_void_p), ("rec_agents", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("rec_out", ctypes.c_void_p), ("rec_cap", ctypes.c_int64), ("rec_count", ctypes.c_int64),
-                ("mlp_checked", ctypes.c_int64), ("mlp_mismatch", ctypes.c_int64)]
+                ("mlp_checked", ctypes.c_int64), ("mlp_mismatch", ctypes.c_int64), ("logit_out", ctypes.c_void_p)]
 
 
 MLP_IN, MLP_H, MLP_OUT, N_RAW, REC_WORDS = 32, 64, 37, 18, 22
@@ -305,7 +305,7 @@ def init_market(params: dict, m: int, L: int, A: int) -> Market:
 
 
 def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trace: bool = True, mlp_w=None,
-               rec_agents: int = 0, rec_cap: int = 0, stats: dict | None = None):
+               rec_agents: int = 0, rec_cap: int = 0, stats: dict | None = None, want_logits: bool = False):
     """Advance ``mk`` in place over steps [s0, s0+n).  Returns (trace_p, trace_v) or None.
 
     ``replay``: optional dict of int32 arrays ``side``, ``tick``, ``qty`` of shape (n, A)
@@ -313,7 +313,9 @@ def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trac
     parameters (MLP agents decide with them, or are checked against them when
     replaying).  ``rec_agents`` / ``rec_cap``: record rule decisions of agents
     a < rec_agents.  ``stats`` (optional dict) receives ``records`` (int32
-    [count, 22]), ``mlp_checked`` and ``mlp_mismatch``.
+    [count, 22]), ``mlp_checked`` and ``mlp_mismatch``, and with
+    ``want_logits`` (needs ``mlp_w``) ``logits``: fp64 [n, A, 37] of every
+    policy decision, NaN where no policy decision was taken.
     """
     P = make_params(params)
     tp = np.zeros(max(n, 1), np.int32)
@@ -332,6 +334,11 @@ def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trac
         assert w.size == mlp_nparam()
         keep.append(w)
         opt.mlp_w = _ptr(w)
+    logits = None
+    if want_logits:
+        assert mlp_w is not None
+        logits = np.full((max(n, 1), max(mk.A, 1), MLP_OUT), np.nan, np.float64)
+        opt.logit_out = _ptr(logits)
     rec = None
     if rec_agents > 0 and rec_cap > 0:
         rec = np.zeros((rec_cap, REC_WORDS), np.int32)
@@ -348,6 +355,8 @@ def run_market(params: dict, mk: Market, s0: int, n: int, replay=None, want_trac
         stats["records"] = rec[: opt.rec_count] if rec is not None else np.zeros((0, REC_WORDS), np.int32)
         stats["mlp_checked"] = int(opt.mlp_checked)
         stats["mlp_mismatch"] = int(opt.mlp_mismatch)
+        if logits is not None:
+            stats["logits"] = logits[:n, :mk.A]
     return (tp[:n], tv[:n]) if want_trace else None
 
 

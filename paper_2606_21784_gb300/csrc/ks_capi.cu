@@ -904,16 +904,17 @@ ks_status ks_set_capture(ks_ensemble* e, const ks_capture* c) {
   if (!e || !c) return arg_fail(KS_ERR_INVALID_ARG, "NULL argument");
   if (c->records && (!c->record_count || c->record_capacity == 0))
     return arg_fail(KS_ERR_INVALID_ARG, "records need record_count and a capacity");
-  if (c->decisions && (e->cfg.trace_markets == 0 || e->cfg.trace_steps == 0))
-    return arg_fail(KS_ERR_INVALID_ARG, "decision capture needs trace_markets and trace_steps");
+  if ((c->decisions || c->logits) && (e->cfg.trace_markets == 0 || e->cfg.trace_steps == 0))
+    return arg_fail(KS_ERR_INVALID_ARG, "decision and logit captures need trace_markets and trace_steps");
   DevParams& p = e->dp;
   p.rec = c->records;
   p.rec_count = c->record_count;
   p.rec_cap = c->records ? c->record_capacity : 0;
   p.rec_agents = c->records ? c->record_agents : 0;
   p.dec_trace = c->decisions;
+  p.logit_trace = c->logits;
   p.pol_count = c->policy_count;
-  const bool want = e->cfg.mlp_pct > 0 || c->records != nullptr || c->decisions != nullptr;
+  const bool want = e->cfg.mlp_pct > 0 || c->records != nullptr || c->decisions != nullptr || c->logits != nullptr;
   if (want == e->mlp) return KS_OK;
   // switch between the rule-only and the policy-capable kernels, keeping the mode
   e->mlp = want;
@@ -969,7 +970,8 @@ ks_status internal_launch_batched(ks_ensemble* e, uint32_t n_steps, const BatchA
                    : e->b_threads == 512 ? launch_batched_512(e->dp, n_steps, b, e->b_grid, e->b_smem, st)
                                          : launch_batched_1024(e->dp, n_steps, b, e->b_grid, e->b_smem, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "batched launch");
-  step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, e->b_args.ticket, n_steps);
+  // re-arm the ticket this launch took its items from (b.ticket, not the workspace's)
+  step_bump_kernel<<<1, 1, 0, st>>>((uint64_t*)e->dp.step, b.ticket, n_steps);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "step counter");
   return KS_OK;

@@ -64,6 +64,7 @@ struct DevParams {
   uint32_t* dec_trace;       // [trace_steps][dec_trace_agents] policy decisions of traced markets
   unsigned long long* pol_count;  // policy decisions evaluated
   uint64_t dec_trace_agents; // agents of markets 0..trace_markets-1
+  float* logit_trace;        // [trace_steps][dec_trace_agents][MLP_OUT] policy logits of traced markets
 };
 
 // A persistent launch of the plain kernel template.

@@ -284,6 +284,11 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
       if (valid) {
         const uint4 w = philox_rk(sdec, (uint32_t)a, gm, 3u, P.rk);
         sm.rowbuf[row] = mlp_decision(z, w, last, L, P.rb_qmax);
+        if (traced && P.logit_trace && sdec < P.trace_steps) {
+          float* zo = P.logit_trace + ((size_t)sdec * P.dec_trace_agents + (size_t)(aoff + a)) * MLP_OUT;
+#pragma unroll
+          for (int i = 0; i < MLP_OUT; ++i) zo[i] = z[i];
+        }
       }
     }
   }

@@ -137,9 +137,11 @@ __device__ __forceinline__ void mlp_issue(const MlpWG& g, uint32_t act_addr, uin
   mma_commit(g.bar);
 }
 
-// Waits for the layer's MMAs: the issuing thread polls the mbarrier, the
-// others wait at the warpgroup's named barrier, which also spreads a timeout.
-__device__ __forceinline__ void mlp_wait(MlpWG& g, uint32_t* err) {
+// The bounded part of a layer wait: the issuing thread polls the mbarrier
+// (at most MLP_WAIT_LIMIT times), the others wait at the warpgroup's named
+// barrier, which also spreads a timeout.  On the first timeout the warpgroup
+// records ERR_MLP_WAIT and stops waiting (and issuing) for good.
+__device__ __forceinline__ void mlp_wait_bounded(MlpWG& g, uint32_t* err) {
   bool ok = true;
   if ((threadIdx.x & 127) == 0) ok = g.abort ? false : mbar_wait_bounded(g.bar, g.phase, MLP_WAIT_LIMIT);
   const bool any_fail = named_sync_or(g.bar_id, 128, !ok) || g.abort;
@@ -148,6 +150,11 @@ __device__ __forceinline__ void mlp_wait(MlpWG& g, uint32_t* err) {
     if ((threadIdx.x & 127) == 0) atomicOr(err, ERR_MLP_WAIT);
   }
   g.phase ^= 1u;
+}
+
+// Waits for the layer's MMAs.
+__device__ __forceinline__ void mlp_wait(MlpWG& g, uint32_t* err) {
+  mlp_wait_bounded(g, err);
   tc_fence_after();
 }
 

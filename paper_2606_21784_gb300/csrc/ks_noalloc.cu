@@ -36,7 +36,10 @@ constexpr int NA_MAX_DEVICES = 64;
 static uint32_t* g_scratch_addr[NA_MAX_DEVICES];
 static std::mutex g_scratch_mu;
 
-// Device address of the static array on device `dev` (which is current).
+// Device address of the static array on device `dev` (which is current),
+// looked up on the first call on that device and kept for the process.  A
+// cudaDeviceReset unloads the module and with it the array, so the kept
+// address is stale afterwards: this entry point does not survive a reset.
 static ks_status scratch_address(int dev, uint32_t** out) {
   if (dev < 0 || dev >= NA_MAX_DEVICES) return KS_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -68,7 +71,15 @@ extern "C" ks_status ks_step_n_noalloc(ks_ensemble* e, uint32_t n_steps, void* s
   s = scratch_address(dev, &base);
   if (s != KS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  // the array keeps the previous call's contents: the ticket must start at zero
+  // Each call copies the schedule from the ensemble's host vectors, which
+  // ks_set_batch_plan may free later: a captured graph would replay reads of
+  // that memory, so a capturing stream is refused.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return KS_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return KS_ERR_UNSUPPORTED;
+  // the array keeps the previous call's contents: the ticket must start at
+  // zero (the step-counter kernel re-arms it after every launch; clearing it
+  // here too covers a launch that failed before re-arming it)
   if (cudaMemsetAsync(base, 0, 64 * sizeof(uint32_t), st) != cudaSuccess) return KS_ERR_CUDA;
   if (cudaMemcpyAsync(base + NA_ORDER, order, (size_t)nm * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return KS_ERR_CUDA;

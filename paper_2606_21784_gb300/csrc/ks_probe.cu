@@ -4,6 +4,7 @@
 
 #include "kineticsim_probe.h"
 #include "ks_device.cuh"
+#include "ks_mlp.cuh"
 
 namespace ks {
 
@@ -76,6 +77,38 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_philox(uint32_t iters, ui
   sink[(size_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = x;
 }
 
+// One warpgroup runs the policy path's bounded layer wait on an mbarrier that
+// nothing ever arrives at (no tensor-core operation is issued, none is in
+// flight): the wait must give up after its poll limit, record ERR_MLP_WAIT in
+// the error word and return; a second wait of the aborted warpgroup must not
+// poll again.  sink[0] (as uint32) receives the error word.
+__global__ void __launch_bounds__(128) probe_wait_timeout(uint32_t* sink) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t err;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1u);
+    err = 0u;
+  }
+  __syncthreads();
+  MlpWG g;
+  g.act = nullptr;
+  g.bar = &bar;
+  g.tmem = 0u;
+  g.bar_id = 1;
+  g.phase = 0u;
+  g.abort = false;
+  g.wg = 0;
+  g.nwg = 1;
+  mlp_wait_bounded(g, &err);
+  const bool first = g.abort;
+  mlp_wait_bounded(g, &err);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sink[0] = err;
+    sink[1] = first && g.abort ? 1u : 0u;
+  }
+}
+
 }  // namespace ks
 
 namespace ks {
@@ -105,6 +138,10 @@ extern "C" ks_status ks_probe(int kind, uint32_t blocks, uint32_t iters, void* s
       break;
     case KS_PROBE_SPLITMIX:
       *ops = ks::launch_probe_sm64(blocks, iters, (uint64_t*)sink, st);
+      break;
+    case KS_PROBE_WAIT_TIMEOUT:
+      ks::probe_wait_timeout<<<1, 128, 0, st>>>((uint32_t*)sink);
+      *ops = 1.0;
       break;
     default:
       return KS_ERR_INVALID_ARG;

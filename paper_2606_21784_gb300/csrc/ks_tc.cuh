@@ -16,23 +16,38 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// One poll of the phase with the given parity.  The hardware may suspend
+// the thread until the phase completes, but for at most MBAR_SUSPEND_NS
+// (the instruction's suspend-time hint), so every poll returns in bounded time.
+constexpr uint32_t MBAR_SUSPEND_NS = 10000u;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.b32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(MBAR_SUSPEND_NS)
       : "memory");
   return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Waits for the phase with the given parity to complete; gives up after
-// `limit` polls and returns false (the caller records the error).
+// `limit` polls or MBAR_DEADLINE_NS of wall time, whichever comes first, and
+// returns false (the caller records the error).
+constexpr uint64_t MBAR_DEADLINE_NS = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 1; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0u && globaltimer_ns() - t0 > MBAR_DEADLINE_NS) return false;
     if (i > 64) __nanosleep(32);
   }
   return false;

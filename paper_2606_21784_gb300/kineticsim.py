@@ -95,7 +95,7 @@ class ks_capture(ctypes.Structure):
     _fields_ = [("records", ctypes.c_void_p), ("record_capacity", ctypes.c_uint64),
                 ("record_agents", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
                 ("record_count", ctypes.c_void_p), ("decisions", ctypes.c_void_p),
-                ("policy_count", ctypes.c_void_p)]
+                ("policy_count", ctypes.c_void_p), ("logits", ctypes.c_void_p)]
 
 
 class ks_batch_info(ctypes.Structure):
@@ -371,6 +371,7 @@ def ks_mlp_export(params, blob=None, stream=None):
 
 
 KS_PROBE_SMEM_RED, KS_PROBE_MUL_WIDE, KS_PROBE_PHILOX, KS_PROBE_MUL_HILO, KS_PROBE_SPLITMIX = 0, 1, 2, 3, 4
+KS_PROBE_WAIT_TIMEOUT = 5
 
 
 def ks_probe(kind: int, blocks: int, iters: int, sink_ptr: int, stream=None) -> float:
@@ -461,8 +462,10 @@ class Ensemble:
         return ks_get_batch_info(self.handle)
 
     def set_capture(self, record_agents: int = 0, record_capacity: int = 0, decisions: bool = False,
-                    count_policy: bool = False):
-        """Allocates capture buffers (torch, device) and enables them; returns them."""
+                    count_policy: bool = False, logits: bool = False):
+        """Allocates capture buffers (torch, device) and enables them; returns them.
+        ``logits``: FP32 [trace_steps, agents of the traced markets, 37], NaN
+        where no policy decision was taken."""
         import torch
         c = ks_capture()
         self.capture = {}
@@ -481,6 +484,12 @@ class Ensemble:
             dec = torch.full((self.trace_steps, max(n_tr, 1)), -1, dtype=torch.int32, device="cuda")
             c.decisions = dec.data_ptr()
             self.capture["decisions"] = dec
+        if logits:
+            n_tr = int(self.offsets[self.trace_markets])
+            z = torch.full((self.trace_steps, max(n_tr, 1), MLP_OUT), float("nan"), dtype=torch.float32,
+                           device="cuda")
+            c.logits = z.data_ptr()
+            self.capture["logits"] = z
         _check(load().ks_set_capture(self.handle, ctypes.byref(c)), "ks_set_capture")
         return self.capture
 
