@@ -467,7 +467,9 @@ ks_status ks_mlp_forward(const void* params, const float* X, int64_t n, float* Z
 ks_status ks_step_n_noalloc(ks_ensemble* e, uint32_t n_steps, void* stream);
 
 /*
- * Behaviour-cloning training of the policy (hand-written FP32 kernels).
+ * Behaviour-cloning training of the policy (hand-written kernels: the
+ * contractions on the tensor cores as BF16 high + low parts with FP32
+ * accumulation, the loss and Adam in FP32).
  * Parameter vector (FP32, device, KS_MLP_NPARAM floats):
  *   W1[64][32], b1[64], W2[64][64], b2[64], W3[37][64], b3[37].
  * Samples are rule-decision records (KS_RECORD_WORDS int32 each, see
@@ -478,10 +480,18 @@ ks_status ks_step_n_noalloc(ks_ensemble* e, uint32_t n_steps, void* stream);
  */
 #define KS_MLP_NPARAM 8677
 
+/* Device workspace (bytes) that ks_bc_grad needs for n samples on the
+ * current device: one partial gradient per CTA. */
+ks_status ks_bc_workspace_size(int64_t n, size_t* bytes);
+
 /* grad += scale * d(sum of per-sample losses)/d params; *loss += scale * sum of
- * the losses (both device FP32; the caller zeroes them). */
+ * the losses (both device FP32; the caller zeroes them).  `workspace` is a
+ * caller-owned device buffer of at least ks_bc_workspace_size(n) bytes
+ * (KS_ERR_WORKSPACE_TOO_SMALL otherwise).  Deterministic: the same inputs on
+ * the same device give the same gradient and loss bit for bit (fixed tile
+ * assignment, fixed-order sums, no floating-point atomics). */
 ks_status ks_bc_grad(const float* params, const int32_t* records, int64_t n, int32_t A, float* grad, float* loss,
-                     float scale, void* stream);
+                     float scale, void* workspace, size_t ws_bytes, void* stream);
 
 /* One Adam update (Kingma and Ba, 2015) with bias correction for step >= 1;
  * m and v are the moment vectors; zeroes grad. */

@@ -80,8 +80,9 @@ def evaluate(params, records, A: int, chunk: int = 1 << 20) -> float:
     n = records.shape[0]
     grad = torch.zeros(ks.KS_MLP_NPARAM, dtype=torch.float32, device=params.device)
     loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+    ws = None
     for i in range(0, n, chunk):
-        ks.ks_bc_grad(params, records[i:i + chunk].contiguous(), A, grad, loss, 1.0 / n)
+        ws = ks.ks_bc_grad(params, records[i:i + chunk].contiguous(), A, grad, loss, 1.0 / n, workspace=ws)
     torch.cuda.synchronize()
     return float(loss.item())
 
@@ -125,6 +126,7 @@ def train(records, A: int, epochs: int = 2, batch: int = 16384, lr: float = 2e-3
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ws = torch.empty(max(ks.ks_bc_workspace_size(batch), 1), dtype=torch.uint8, device=dev)
     hist = {"val_loss": [evaluate(params, val, A)], "train_loss": []}
     step = 0
     for ep in range(epochs):
@@ -134,7 +136,7 @@ def train(records, A: int, epochs: int = 2, batch: int = 16384, lr: float = 2e-3
         for i in range(0, order.shape[0], batch):
             idx = order[i:i + batch]
             bs = idx.shape[0]
-            ks.ks_bc_grad(params, records[idx].contiguous(), A, grad, loss, 1.0 / bs)
+            ks.ks_bc_grad(params, records[idx].contiguous(), A, grad, loss, 1.0 / bs, workspace=ws)
             step += 1
             ks.ks_adam_step(params, grad, m, v, step, lr)
             seen += 1

@@ -30,6 +30,7 @@ EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_stat
            "ks_sync", "ks_error_word", "ks_set_launch", "ks_get_launch", "ks_destroy", "ks_status_string",
            "ks_last_error", "ks_version", "ks_probe", "ks_probe_state_io", "ks_set_batch_plan",
            "ks_get_batch_info", "ks_batch_variants", "ks_mlp_forward", "ks_set_capture", "ks_bc_grad",
+           "ks_bc_workspace_size",
            "ks_adam_step", "ks_mlp_export", "ks_paper_workspace_size", "ks_paper_create", "ks_paper_step_n",
            "ks_paper_step_n_naive", "ks_paper_read_state", "ks_paper_set_launch", "ks_paper_get_launch",
            "ks_paper_sync", "ks_paper_destroy")
@@ -159,7 +160,9 @@ def load(build_if_missing: bool = True):
         "ks_batch_variants": ([ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32)], ctypes.c_int),
         "ks_mlp_forward": ([vp, vp, ctypes.c_int64, vp, vp, vp], ctypes.c_int),
         "ks_set_capture": ([vp, P(ks_capture)], ctypes.c_int),
-        "ks_bc_grad": ([vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "ks_bc_workspace_size": ([ctypes.c_int64, P(ctypes.c_size_t)], ctypes.c_int),
+        "ks_bc_grad": ([vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp, ctypes.c_float, vp, ctypes.c_size_t, vp],
+                       ctypes.c_int),
         "ks_adam_step": ([vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, vp], ctypes.c_int),
         "ks_mlp_export": ([vp, vp, vp], ctypes.c_int),
@@ -352,9 +355,25 @@ def ks_mlp_forward(params_blob, X, err=None, stream=None):
     return Z, err
 
 
-def ks_bc_grad(params, records, A: int, grad, loss, scale: float, stream=None):
-    _check(load().ks_bc_grad(params.data_ptr(), records.data_ptr(), records.shape[0], int(A), grad.data_ptr(),
-                             loss.data_ptr(), float(scale), _stream_ptr(stream)), "ks_bc_grad")
+def ks_bc_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().ks_bc_workspace_size(int(n), ctypes.byref(b)), "ks_bc_workspace_size")
+    return int(b.value)
+
+
+def ks_bc_grad(params, records, A: int, grad, loss, scale: float, workspace=None, stream=None):
+    """grad += scale * dL/dparams, loss += scale * L over ``records`` (device).
+    ``workspace``: a device uint8 tensor of at least ks_bc_workspace_size(n)
+    bytes (allocated here when omitted)."""
+    import torch
+    n = int(records.shape[0])
+    need = ks_bc_workspace_size(n)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=params.device)
+    _check(load().ks_bc_grad(params.data_ptr(), records.data_ptr(), n, int(A), grad.data_ptr(),
+                             loss.data_ptr(), float(scale), workspace.data_ptr(), workspace.numel(),
+                             _stream_ptr(stream)), "ks_bc_grad")
+    return workspace
 
 
 def ks_adam_step(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

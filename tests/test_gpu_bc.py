@@ -39,6 +39,63 @@ def test_bc_gradient_matches_fp64_oracle(small_records):
     assert np.abs(g - g64).max() <= 1e-4 * max(1.0, np.abs(g64).max())
 
 
+def test_bc_gradient_is_deterministic_and_tail_safe(small_records):
+    """The gradient is bit-identical across calls (fixed tile assignment and
+    fixed-order sums); a ragged tail (n not a multiple of the 64-sample tile)
+    matches the fp64 oracle too."""
+    import torch
+    rec, w = small_records
+    A = w["A"]
+    params = bc.init_params(4)
+    outs = []
+    for _ in range(3):
+        grad = torch.zeros_like(params)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        ks.ks_bc_grad(params, rec[:50_000].contiguous(), A, grad, loss, 1.0 / 50_000)
+        torch.cuda.synchronize()
+        outs.append((grad.clone(), loss.clone()))
+    for g, l in outs[1:]:
+        assert torch.equal(g, outs[0][0]) and torch.equal(l, outs[0][1])
+    sub = rec[:1001].contiguous()
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ks.ks_bc_grad(params, sub, A, grad, loss, 1.0 / 1001)
+    torch.cuda.synchronize()
+    X, side, off, logq = _oracle_inputs(sub, A)
+    l64, g64 = o.mlp_loss_grad(params.double().cpu().numpy(), X, side, off, logq)
+    assert abs(float(loss.item()) - l64) <= 1e-4 * max(1.0, abs(l64))
+    assert np.abs(grad.double().cpu().numpy() - g64).max() <= 1e-4 * max(1.0, np.abs(g64).max())
+
+
+def test_workspace_too_small_is_refused():
+    import ctypes
+
+    import torch
+    params = bc.init_params(0)
+    rec = torch.zeros((1000, ks.KS_RECORD_WORDS), dtype=torch.int32, device="cuda")
+    rec[:, 20] = 1
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    need = ks.ks_bc_workspace_size(1000)
+    assert need > 0
+    ws = torch.empty(need - 4, dtype=torch.uint8, device="cuda")
+    rc = ks.load().ks_bc_grad(params.data_ptr(), rec.data_ptr(), 1000, 64, grad.data_ptr(), loss.data_ptr(),
+                              ctypes.c_float(1.0), ws.data_ptr(), ws.numel(), None)
+    assert rc == ks.KS_ERR_WORKSPACE_TOO_SMALL
+    torch.cuda.synchronize()
+
+
+def test_training_is_reproducible(small_records):
+    """Two training runs from the same seed give the same network bit for bit."""
+    import torch
+    rec, w = small_records
+    p1, h1, _ = bc.train(rec[:120_000], w["A"], epochs=1, batch=4096, lr=3e-3, seed=5)
+    p2, h2, _ = bc.train(rec[:120_000], w["A"], epochs=1, batch=4096, lr=3e-3, seed=5)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
+    assert h1 == h2
+
+
 def test_adam_step_matches_fp64_oracle():
     import torch
     rng = np.random.default_rng(0)
