@@ -80,9 +80,10 @@ def plain_candidates(A, policy: bool = False):
         for ak in (1, 2, 4, 8, 16):
             if nt * ak < A or nt * ak > 4 * max(A, 32):
                 continue
-            # register-cap classes 1 and 2 change nothing for 512- and 1024-thread CTAs;
-            # shapes that are not compiled are skipped when set_launch refuses them
-            for rc in ((0, 1, 2) if nt <= 256 else (0,)):
+            # register-cap classes 1 and 2 change nothing for 512- and 1024-thread CTAs,
+            # class 3 (64 registers) only for them; shapes that are not compiled are
+            # skipped when set_launch refuses them
+            for rc in ((0, 1, 2) if nt <= 256 else (0, 3)):
                 out.append(dict(threads=nt, agents_per_thread=ak, reg_cap=rc))
     return out
 

@@ -23,10 +23,12 @@ __device__ __forceinline__ void prefetch_next_market(const DevParams& P, uint32_
 }
 
 // Register-cap classes of the launch bounds: 0 = compiler's choice, 1 = 128
-// registers per thread (two 256-thread CTAs per SM), 2 = 85 (three).
+// registers per thread (two 256-thread CTAs per SM), 2 = 85 (three), 3 = 64
+// (32 warps per SM: two 512-thread CTAs or one 1024-thread CTA).
 // Returns the launch bounds' minimum of resident CTAs.
+__host__ __device__ constexpr int plain_cap_regs(int occ) { return occ == 2 ? 85 : (occ == 3 ? 64 : 128); }
 __host__ __device__ constexpr int plain_min_ctas(int nt, int occ) {
-  return occ == 0 ? 1 : (65536 / (nt * (occ == 2 ? 85 : 128)) > 0 ? 65536 / (nt * (occ == 2 ? 85 : 128)) : 1);
+  return occ == 0 ? 1 : (65536 / (nt * plain_cap_regs(occ)) > 0 ? 65536 / (nt * plain_cap_regs(occ)) : 1);
 }
 
 template <int NT, int AK, bool AGGR, int OCC, bool MLP = false>
