@@ -37,9 +37,9 @@ __device__ __forceinline__ void run_item(const DevParams& P, const BatchArgs& B,
   }
 }
 
-// Policy-capable variant: each warpgroup of a group also owns an activation
-// buffer (after the group's market shared memory), an mbarrier, 64 TMEM
-// columns of the CTA and a named barrier.
+// Policy-capable variant: each warpgroup of a group also owns an mbarrier,
+// MLP_TMEM_COLS TMEM columns of the CTA (its tile accumulator and
+// activations) and a named barrier, and evaluates policy tiles.
 template <int NT, int GT, int AK>
 __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs& B, uint4 d, uint32_t s0, uint32_t n,
                                              unsigned char* raw, const MlpCta& mc) {
@@ -48,9 +48,8 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
   const int g = (int)threadIdx.x / GT;
   if (g < G && g < (int)d.y) {
     size_t o[8];
-    const size_t mbytes = group_smem_layout(thread_reg_budget(NT, 1), GT, AK, (int)d.w, true, o);
-    const int ntw = max(1, (int)(d.z >> 16));  // warpgroups of a group evaluating policy tiles (host-chosen)
-    const size_t gsz = mbytes + (size_t)ntw * MLP_ACT_BYTES;
+    const size_t gsz = group_smem_layout(thread_reg_budget(NT, 1), GT, AK, (int)d.w, true, o);
+    const int ntw = GT / 128;  // every warpgroup of the group evaluates policy tiles
     unsigned char* graw = raw + (size_t)g * gsz;
     const Smem sm = carve<GT, AK, true, true>(graw, (int)d.w);
     const int bar = (GT == NT) ? 0 : 1 + g;
@@ -59,7 +58,6 @@ __device__ __forceinline__ void run_item_mlp(const DevParams& P, const BatchArgs
     MlpWG mw;
     mw.wg = wl;
     mw.nwg = ntw;
-    mw.act = graw + mbytes + (size_t)min(wl, ntw - 1) * MLP_ACT_BYTES;
     mw.bar = &mc.bars[wc];
     mw.tmem = *mc.tslot + (uint32_t)(wc * MLP_TMEM_COLS);
     mw.bar_id = (GT == 128) ? bar : 8 + wc;
@@ -82,6 +80,7 @@ __global__ void __launch_bounds__(NT, 1) batched_mlp_kernel(DevParams P, uint32_
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint32_t s_item;
   const uint32_t s0 = (uint32_t)(*P.step);
+  static_assert(NT / 128 <= MLP_MAX_TILE_WGS, "one TMEM share per warpgroup");
   const MlpCta mc = mlp_cta_carve(smem_raw, (uint32_t)(NT / 128) * MLP_TMEM_COLS);
   mlp_cta_setup(mc, P.mlp);
   unsigned char* raw = smem_raw + mlp_cta_bytes();

@@ -363,27 +363,20 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   const void* k = v->kernel;
   KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  const int tmem_cols = e->mlp ? (l->threads / 128) * (int)MLP_TMEM_COLS : 0;  // 64 per warpgroup
+  int tile_wgs = 1;
+  int tmem_cols = 0;
+  if (e->mlp) {
+    // as many warpgroups evaluate policy tiles (MLP_TMEM_COLS TMEM columns
+    // each, a power of two in all) as the SM's 512 columns allow without
+    // lowering the resident CTAs that the other limits give
+    int occ0 = 0;
+    KS_CUDA(resident_ctas(k, l->threads, smem, 32, &occ0));
+    tile_wgs = std::min(l->threads / 128, (int)MLP_MAX_TILE_WGS);
+    while (tile_wgs > 1 && occ0 * tile_wgs * (int)MLP_TMEM_COLS > 512) tile_wgs /= 2;
+    tmem_cols = tile_wgs * (int)MLP_TMEM_COLS;
+  }
   KS_CUDA(resident_ctas(k, l->threads, smem, tmem_cols, &occ));
   if (occ < 1) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
-  int tile_wgs = 1;
-  if (e->mlp) {
-    // as many warpgroups evaluate policy tiles (one activation buffer each)
-    // as fit without lowering the resident CTAs per SM
-    for (int w = l->threads / 128; w > 1; --w) {
-      const size_t s = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, true, w);
-      if (s > e->max_smem) continue;
-      int o = 0;
-      KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s));
-      KS_CUDA(resident_ctas(k, l->threads, s, tmem_cols, &o));
-      if (o >= occ) {
-        tile_wgs = w;
-        smem = s;
-        break;
-      }
-    }
-    KS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
   // resident CTAs must not ask for more TMEM than an SM has (512 columns)
   if (e->mlp && occ * tmem_cols > 512) return arg_fail(KS_ERR_UNSUPPORTED, "policy launch oversubscribes TMEM");
   const int per_sm = l->ctas_per_sm > 0 ? std::min(occ, l->ctas_per_sm) : occ;
@@ -408,12 +401,10 @@ static int batch_variant_id(int nt, int gt, int ak, bool mlp) {
 }
 
 // Groups of one bucket that fit one CTA: thread count, barrier ids, shared
-// memory (policy kernels: tile_wgs activation buffers per group).
-static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz, bool mlp,
-                          int tile_wgs = 1) {
+// memory (the policy kernels keep their activations in TMEM).
+static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, size_t* gsz, bool mlp) {
   size_t o[8];
-  *gsz = group_smem_layout(thread_reg_budget(nt, 1), gt, ak, Lcap, mlp, o) +
-         (mlp ? (size_t)tile_wgs * MLP_ACT_BYTES : 0);
+  *gsz = group_smem_layout(thread_reg_budget(nt, 1), gt, ak, Lcap, mlp, o);
   if (mlp) max_smem = max_smem > mlp_cta_bytes() ? max_smem - mlp_cta_bytes() : 0;
   int g = nt / gt;
   if (gt != 32 && gt != nt) g = std::min(g, 15);
@@ -511,28 +502,11 @@ static ks_status build_batch(ks_ensemble* e, int nt, const ks_bucket* buckets, i
     if (b == nb) return arg_fail(KS_ERR_INVALID_ARG, "a market matches no bucket of the plan");
     members[b].push_back(m);
   }
-  // policy kernel: as many warpgroups of a group evaluate policy tiles (one
-  // activation buffer each) as fit in the shared memory the plan needs with one
+  // policy kernel: every warpgroup of a group evaluates policy tiles (each
+  // owns MLP_TMEM_COLS columns of the CTA's tensor memory)
   std::vector<int> tile_wgs(nb, 1);
-  if (mlp) {
-    size_t cap = 0;
-    for (int b = 0; b < nb; ++b)
-      if (!members[b].empty()) cap = std::max(cap, (size_t)std::min<size_t>(G[b], members[b].size()) * gsz[b]);
-    for (int b = 0; b < nb; ++b) {
-      if (members[b].empty()) continue;
-      const size_t used = std::min<size_t>(G[b], members[b].size());
-      for (int w = buckets[b].group_threads / 128; w > 1; --w) {
-        size_t gw = 0;
-        const int Gw = groups_per_cta(nt, buckets[b].group_threads, buckets[b].agents_per_thread, buckets[b].L_max,
-                                      max_dyn, &gw, true, w);
-        if (Gw >= G[b] && used * gw <= cap) {
-          tile_wgs[b] = w;
-          gsz[b] = gw;
-          break;
-        }
-      }
-    }
-  }
+  if (mlp)
+    for (int b = 0; b < nb; ++b) tile_wgs[b] = std::max(1, buckets[b].group_threads / 128);
   struct Item {
     double cost;
     int bucket;

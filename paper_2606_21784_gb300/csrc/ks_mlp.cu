@@ -9,18 +9,20 @@
 
 namespace ks {
 
-constexpr int FWD_NWG = 2;  // warpgroups per CTA
+constexpr int FWD_NWG = 2;  // warpgroups per CTA (MLP_TMEM_COLS TMEM columns each)
 
 __host__ __device__ constexpr uint32_t fwd_smem_bytes() {
-  return ((MLP_SM_BYTES + 127u) & ~127u) + FWD_NWG * MLP_ACT_BYTES + 8 * FWD_NWG + 16;
+  return ((MLP_SM_BYTES + 127u) & ~127u) + 8 * FWD_NWG + 16;
 }
+// Dynamic shared memory requested per CTA: enough that at most two CTAs share
+// an SM, so their TMEM (2 x 256 columns) never exceeds the SM's 512.
+constexpr uint32_t FWD_SMEM_REQUEST = 100u * 1024u;
 
 __global__ void __launch_bounds__(128 * FWD_NWG, 1)
     mlp_forward_kernel(const unsigned char* blob, const float* X, int64_t n, float* Z, uint32_t* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* sw = sm;
-  unsigned char* acts = sm + ((MLP_SM_BYTES + 127u) & ~127u);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(acts + FWD_NWG * MLP_ACT_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + ((MLP_SM_BYTES + 127u) & ~127u));
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + FWD_NWG);
   const int wg = (int)threadIdx.x / 128;
   const int r = (int)threadIdx.x & 127;
@@ -38,7 +40,6 @@ __global__ void __launch_bounds__(128 * FWD_NWG, 1)
   __syncthreads();
   tc_fence_after();
   MlpWG g;
-  g.act = acts + wg * MLP_ACT_BYTES;
   g.bar = &bars[wg];
   g.tmem = *tslot + (uint32_t)(wg * MLP_TMEM_COLS);
   g.bar_id = 1 + wg;
@@ -76,17 +77,17 @@ extern "C" ks_status ks_mlp_forward(const void* params, const float* X, int64_t 
   if (!params || !err || n < 0 || (n > 0 && (!X || !Z))) return KS_ERR_INVALID_ARG;
   if (((uintptr_t)params & 15u) != 0) return KS_ERR_INVALID_ARG;
   if (n == 0) return KS_OK;
-  static_assert(ks::fwd_smem_bytes() < 227 * 1024, "smem");
-  const size_t smem = ks::fwd_smem_bytes();
+  static_assert(ks::fwd_smem_bytes() <= ks::FWD_SMEM_REQUEST, "smem");
+  const size_t smem = ks::FWD_SMEM_REQUEST;
   cudaError_t e = cudaFuncSetAttribute(ks::mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return KS_ERR_CUDA;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (n + 127) / 128;
-  // TMEM: 128 columns per CTA; the shared-memory footprint keeps at most 4 CTAs on an SM (512 columns)
+  // TMEM: 256 columns per CTA; the shared-memory request keeps at most 2 CTAs on an SM (512 columns)
   const int64_t want = (ntiles + ks::FWD_NWG - 1) / ks::FWD_NWG;
-  const int grid = (int)(want < (int64_t)sms * 4 ? want : (int64_t)sms * 4);
+  const int grid = (int)(want < (int64_t)sms * 2 ? want : (int64_t)sms * 2);
   ks::mlp_forward_kernel<<<grid, 128 * ks::FWD_NWG, smem, (cudaStream_t)stream>>>(
       (const unsigned char*)params, X, n, Z, err);
   return cudaGetLastError() == cudaSuccess ? KS_OK : KS_ERR_CUDA;

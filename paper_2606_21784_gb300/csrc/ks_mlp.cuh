@@ -7,12 +7,15 @@
 // agents of a market).  Layers 2 and 3 are dense 64-wide contractions on the
 // tensor cores: one warpgroup (128 threads) evaluates a tile of 128 agents,
 // thread r owning row r; each layer is a chain of M=128, K=16 tcgen05.mma
-// (kind::f16, BF16 x BF16 -> FP32 in tensor memory) on K-major no-swizzle
-// operands in shared memory, committed to an mbarrier.  The activation
-// operand is passed as a high and a low BF16 part (a = hi + lo, two MMAs per
-// K chunk into the same accumulator), so the only rounding left in the
-// contraction is that of the BF16 weights themselves.  The epilogue reads the
-// accumulator rows with tcgen05.ld and adds the bias.
+// (kind::f16, BF16 x BF16 -> FP32 in tensor memory) committed to an
+// mbarrier.  The weights are K-major no-swizzle operands in shared memory;
+// the activations are the A operand in tensor memory: thread r writes its
+// row into TMEM lane r with tcgen05.st, so a tile needs no shared-memory
+// activation buffer and every warpgroup of a CTA can run tiles.  The
+// activation operand is passed as a high and a low BF16 part (a = hi + lo,
+// two MMAs per K chunk into the same accumulator), so the only rounding left
+// in the contraction is that of the BF16 weights themselves.  The epilogue
+// reads the accumulator rows with tcgen05.ld and adds the bias.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -51,10 +54,14 @@ constexpr uint32_t MLP_SM_B = MLP_SM_W3 + 2 * MLP_OUT_PAD * MLP_H;  // f32 b1[64
 // f32 [64]: column 8 of W1 (the inventory input) stored contiguously for the step loop's layer 1
 constexpr uint32_t MLP_SM_W1INV = MLP_SM_B + 4 * (MLP_H + MLP_H + MLP_OUT_PAD);
 constexpr uint32_t MLP_SM_BYTES = MLP_SM_W1INV + 4 * MLP_H;
-// Per warpgroup: the hidden activations as two [128 x 64] BF16 operands (high, low part).
-constexpr uint32_t MLP_ACT_HALF = 2 * 128 * MLP_H;
-constexpr uint32_t MLP_ACT_BYTES = 2 * MLP_ACT_HALF;
-constexpr uint32_t MLP_TMEM_COLS = 64;  // per warpgroup
+// TMEM columns of a tile warpgroup: the FP32 accumulator (64 columns), then
+// the hidden activations as the A operand, high part and low part (64 BF16
+// per row = 32 columns each).  At most four tile warpgroups fit an SM's 512.
+constexpr uint32_t MLP_TMEM_ACC = 0;
+constexpr uint32_t MLP_TMEM_AHI = 64;
+constexpr uint32_t MLP_TMEM_ALO = 96;
+constexpr uint32_t MLP_TMEM_COLS = 128;  // per tile warpgroup
+constexpr int MLP_MAX_TILE_WGS = 4;
 constexpr uint32_t MLP_WAIT_LIMIT = 1u << 22;
 
 // Loads the blob into the operand layout; all threads of the CTA take part.
@@ -113,9 +120,8 @@ __device__ __forceinline__ bool named_sync_or(int id, int count, bool pred) {
 
 // State of one warpgroup's tile pipeline.
 struct MlpWG {
-  unsigned char* act;  // MLP_ACT_BYTES
   uint64_t* bar;       // mbarrier (count 1)
-  uint32_t tmem;       // TMEM address of this warpgroup's 64 columns
+  uint32_t tmem;       // TMEM address of this warpgroup's MLP_TMEM_COLS columns
   int bar_id;          // named barrier of the 128 threads
   uint32_t phase;      // parity of the next mbarrier completion
   bool abort;          // a bounded wait gave up: no further MMAs
@@ -123,16 +129,17 @@ struct MlpWG {
   int nwg;             // warpgroups of the group that evaluate policy tiles (those with wg < nwg)
 };
 
-// Issues one layer: for each 16-wide K chunk, acc += hi * W and acc += lo * W;
-// then commits the chain to the warpgroup's mbarrier.
-__device__ __forceinline__ void mlp_issue(const MlpWG& g, uint32_t act_addr, uint32_t b_addr, int N) {
+// Issues one layer: for each 16-wide K chunk (8 TMEM columns of the
+// activations), acc += hi * W and acc += lo * W; then commits the chain to
+// the warpgroup's mbarrier.
+__device__ __forceinline__ void mlp_issue(const MlpWG& g, uint32_t b_addr, int N) {
   tc_fence_after();
   const uint32_t idesc = idesc_bf16_f32(128, N);
   const uint32_t sbo = (uint32_t)MLP_H * 16;
   for (int kk = 0; kk < MLP_H / 16; ++kk) {
     const uint64_t bd = smem_desc(b_addr + 256u * kk, 128u, sbo);
-    mma_bf16(g.tmem, smem_desc(act_addr + 256u * kk, 128u, sbo), bd, idesc, kk > 0);
-    mma_bf16(g.tmem, smem_desc(act_addr + MLP_ACT_HALF + 256u * kk, 128u, sbo), bd, idesc, true);
+    mma_bf16_ts(g.tmem + MLP_TMEM_ACC, g.tmem + MLP_TMEM_AHI + 8u * kk, bd, idesc, kk > 0);
+    mma_bf16_ts(g.tmem + MLP_TMEM_ACC, g.tmem + MLP_TMEM_ALO + 8u * kk, bd, idesc, true);
   }
   mma_commit(g.bar);
 }
@@ -165,23 +172,30 @@ __device__ __forceinline__ void mlp_read(const MlpWG& g, int ncols, float* v) {
   tmem_wait_ld();
 }
 
-// Writes row r of the activation operand: h = hi + lo with hi = bf16(h) and
-// lo = bf16(h - hi), both in the core-matrix layout.
-__device__ __forceinline__ void mlp_store_split(unsigned char* act, int r, const float* h) {
+// Writes activations [8 kc, 8 kc + 8) of this thread's row into the A
+// operand in TMEM as high and low BF16 parts: hi = bf16(h), lo = bf16(h - hi),
+// two elements per column (columns 4 kc .. 4 kc + 3 of each part).
+__device__ __forceinline__ void mlp_tstore8(const MlpWG& g, int kc, const float* h) {
+  uint32_t hi[4], lo[4];
 #pragma unroll
-  for (int kc = 0; kc < MLP_H / 8; ++kc) {
-    uint32_t hi[4], lo[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float a = h[8 * kc + 2 * j], b = h[8 * kc + 2 * j + 1];
-      hi[j] = pack_bf16x2(a, b);
-      const float ah = __uint_as_float(hi[j] << 16), bh = __uint_as_float(hi[j] & 0xFFFF0000u);
-      lo[j] = pack_bf16x2(a - ah, b - bh);
-    }
-    *reinterpret_cast<uint4*>(act + cm_offset(r, 8 * kc, MLP_H)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(act + MLP_ACT_HALF + cm_offset(r, 8 * kc, MLP_H)) =
-        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  for (int j = 0; j < 4; ++j) {
+    const float a = h[2 * j], b = h[2 * j + 1];
+    hi[j] = pack_bf16x2(a, b);
+    const float ah = __uint_as_float(hi[j] << 16), bh = __uint_as_float(hi[j] & 0xFFFF0000u);
+    lo[j] = pack_bf16x2(a - ah, b - bh);
   }
+  const uint32_t lane = ((threadIdx.x >> 5) & 3u) * 32u;
+  const uint32_t t = g.tmem + (lane << 16) + 4u * (uint32_t)kc;
+  tmem_st4(t + MLP_TMEM_AHI, hi[0], hi[1], hi[2], hi[3]);
+  tmem_st4(t + MLP_TMEM_ALO, lo[0], lo[1], lo[2], lo[3]);
+}
+
+// The warpgroup's activation stores are complete and visible to the MMA the
+// issuing thread starts next.
+__device__ __forceinline__ void mlp_operand_ready(const MlpWG& g) {
+  tmem_wait_st();
+  tc_fence_before();
+  named_sync(g.bar_id, 128);
 }
 
 // Layers 2 and 3 of one 128-row tile.  h1: this thread's 64 first-layer
@@ -191,23 +205,20 @@ __device__ __forceinline__ void mlp_tile_forward(MlpWG& g, const unsigned char* 
                                                  uint32_t* err) {
   const int r = (int)(threadIdx.x & 127);
   const float* sb = reinterpret_cast<const float*>(sw + MLP_SM_B);
-  const uint32_t act_addr = smem_u32(g.act);
   const uint32_t w_addr = smem_u32(sw);
   float acc[MLP_H];
-  mlp_store_split(g.act, r, h1);
-  fence_async_smem();
-  tc_fence_before();
-  named_sync(g.bar_id, 128);
-  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W2, MLP_H);
+#pragma unroll
+  for (int kc = 0; kc < MLP_H / 8; ++kc) mlp_tstore8(g, kc, h1 + 8 * kc);
+  mlp_operand_ready(g);
+  if (r == 0 && !g.abort) mlp_issue(g, w_addr + MLP_SM_W2, MLP_H);
   mlp_wait(g, err);
   mlp_read(g, MLP_H, acc);
 #pragma unroll
   for (int i = 0; i < MLP_H; ++i) acc[i] = fmaxf(acc[i] + sb[MLP_H + i], 0.0f);
-  mlp_store_split(g.act, r, acc);  // layer 2 is complete: its operand may be overwritten
-  fence_async_smem();
-  tc_fence_before();
-  named_sync(g.bar_id, 128);
-  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W3, MLP_OUT_PAD);
+#pragma unroll
+  for (int kc = 0; kc < MLP_H / 8; ++kc) mlp_tstore8(g, kc, acc + 8 * kc);  // layer 2 read its operand already
+  mlp_operand_ready(g);
+  if (r == 0 && !g.abort) mlp_issue(g, w_addr + MLP_SM_W3, MLP_OUT_PAD);
   mlp_wait(g, err);
   mlp_read(g, MLP_OUT_PAD, acc);
 #pragma unroll
@@ -310,21 +321,6 @@ __device__ __forceinline__ int mlp_sample(const float* z, uint32_t w) {
 }
 
 
-// Writes columns [8 kc, 8 kc + 8) of row r of the activation operand as
-// high and low BF16 parts.
-__device__ __forceinline__ void mlp_store_split8(unsigned char* act, int r, int kc, const float* h) {
-  uint32_t hi[4], lo[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float a = h[2 * j], b = h[2 * j + 1];
-    hi[j] = pack_bf16x2(a, b);
-    const float ah = __uint_as_float(hi[j] << 16), bh = __uint_as_float(hi[j] & 0xFFFF0000u);
-    lo[j] = pack_bf16x2(a - ah, b - bh);
-  }
-  *reinterpret_cast<uint4*>(act + cm_offset(r, 8 * kc, MLP_H)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4*>(act + MLP_ACT_HALF + cm_offset(r, 8 * kc, MLP_H)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-}
-
 // Step-loop policy tile: layer 1 is c + W1[:, 8] * x_inv (c: the 64
 // pre-activations shared by the market's agents, x_inv: this row's inventory
 // input), layers 2-3 on the tensor cores, 16 accumulator columns at a time.
@@ -335,7 +331,6 @@ __device__ __forceinline__ void mlp_tile_logits(MlpWG& g, const unsigned char* s
   const float4* w1i = reinterpret_cast<const float4*>(sw + MLP_SM_W1INV);
   const float4* cv = reinterpret_cast<const float4*>(cvec);
   const float* sb = reinterpret_cast<const float*>(sw + MLP_SM_B);
-  const uint32_t act_addr = smem_u32(g.act);
   const uint32_t w_addr = smem_u32(sw);
   const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) & 3) * 32u;
 #pragma unroll 1
@@ -345,32 +340,28 @@ __device__ __forceinline__ void mlp_tile_logits(MlpWG& g, const unsigned char* s
                         fmaxf(fmaf(wa.z, x_inv, ca.z), 0.0f), fmaxf(fmaf(wa.w, x_inv, ca.w), 0.0f),
                         fmaxf(fmaf(wb.x, x_inv, cb.x), 0.0f), fmaxf(fmaf(wb.y, x_inv, cb.y), 0.0f),
                         fmaxf(fmaf(wb.z, x_inv, cb.z), 0.0f), fmaxf(fmaf(wb.w, x_inv, cb.w), 0.0f)};
-    mlp_store_split8(g.act, r, kc, h);
+    mlp_tstore8(g, kc, h);
   }
-  fence_async_smem();
-  tc_fence_before();
-  named_sync(g.bar_id, 128);
-  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W2, MLP_H);
+  mlp_operand_ready(g);
+  if (r == 0 && !g.abort) mlp_issue(g, w_addr + MLP_SM_W2, MLP_H);
   mlp_wait(g, err);
 #pragma unroll 1
   for (int c = 0; c < MLP_H / 16; ++c) {
     float v[16];
-    tmem_ld16(g.tmem + (lane_base << 16) + (uint32_t)(16 * c), v);
+    tmem_ld16(g.tmem + (lane_base << 16) + MLP_TMEM_ACC + (uint32_t)(16 * c), v);
     tmem_wait_ld();
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + sb[MLP_H + 16 * c + j], 0.0f);
-    mlp_store_split8(g.act, r, 2 * c, v);
-    mlp_store_split8(g.act, r, 2 * c + 1, v + 8);
+    mlp_tstore8(g, 2 * c, v);  // layer 2 has read its operand: overwrite it with layer 3's
+    mlp_tstore8(g, 2 * c + 1, v + 8);
   }
-  fence_async_smem();
-  tc_fence_before();
-  named_sync(g.bar_id, 128);
-  if (r == 0 && !g.abort) mlp_issue(g, act_addr, w_addr + MLP_SM_W3, MLP_OUT_PAD);
+  mlp_operand_ready(g);
+  if (r == 0 && !g.abort) mlp_issue(g, w_addr + MLP_SM_W3, MLP_OUT_PAD);
   mlp_wait(g, err);
 #pragma unroll
   for (int c = 0; c < MLP_OUT_PAD / 16; ++c) {
     float v[16];
-    tmem_ld16(g.tmem + (lane_base << 16) + (uint32_t)(16 * c), v);
+    tmem_ld16(g.tmem + (lane_base << 16) + MLP_TMEM_ACC + (uint32_t)(16 * c), v);
     tmem_wait_ld();
 #pragma unroll
     for (int j = 0; j < 16; ++j)

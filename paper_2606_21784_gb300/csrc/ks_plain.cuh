@@ -37,22 +37,21 @@ __global__ void __launch_bounds__(NT, plain_min_ctas(NT, OCC)) plain_kernel(DevP
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t s0 = (uint32_t)(*P.step);
   if constexpr (MLP) {
-    // policy path: weights, then the market group; every warpgroup owns an
-    // activation buffer, an mbarrier, 64 TMEM columns and a named barrier
+    // policy path: weights, then the market group; warpgroups 0 .. tile_wgs-1
+    // evaluate policy tiles, each with MLP_TMEM_COLS TMEM columns (its
+    // accumulator and activations), an mbarrier and a named barrier
     constexpr int NWG = NT / 128;
-    const MlpCta mc = mlp_cta_carve(smem_raw, NWG * MLP_TMEM_COLS);
+    const int twg = min(max(P.mlp_tile_wgs, 1), min(NWG, MLP_MAX_TILE_WGS));
+    const MlpCta mc = mlp_cta_carve(smem_raw, (uint32_t)twg * MLP_TMEM_COLS);
     mlp_cta_setup(mc, P.mlp);
     unsigned char* graw = smem_raw + mlp_cta_bytes();
-    size_t o[8];
-    const size_t mbytes = group_smem_layout(BUDGET, NT, AK, P.Lmax, true, o);
     const Smem sm = carve<NT, AK, true, true>(graw, P.Lmax);
     const int wg = (int)threadIdx.x / 128;
     MlpWG mw;
     mw.wg = wg;
-    mw.nwg = min(max(P.mlp_tile_wgs, 1), NWG);  // activation buffers after the market group
-    mw.act = graw + mbytes + (size_t)min(wg, mw.nwg - 1) * MLP_ACT_BYTES;
+    mw.nwg = twg;
     mw.bar = &mc.bars[wg];
-    mw.tmem = *mc.tslot + (uint32_t)(wg * MLP_TMEM_COLS);
+    mw.tmem = *mc.tslot + (uint32_t)(min(wg, twg - 1) * MLP_TMEM_COLS);
     mw.bar_id = 1 + wg;
     mw.phase = 0;
     mw.abort = false;
@@ -78,11 +77,11 @@ cudaError_t launch_plain(const DevParams& p, uint32_t n_steps, int grid, size_t 
 }
 
 // Dynamic shared memory of a plain launch (occ: register-cap class; policy
-// kernels: tile_wgs activation buffers).
-__host__ __device__ inline size_t plain_launch_smem(int nt, int ak, int occ, int Lmax, bool mlp, int tile_wgs = 1) {
+// kernels add the weights, their activations live in TMEM).
+__host__ __device__ inline size_t plain_launch_smem(int nt, int ak, int occ, int Lmax, bool mlp) {
   size_t o[8];
   const size_t m = group_smem_layout(thread_reg_budget(nt, plain_min_ctas(nt, occ)), nt, ak, Lmax, mlp, o);
-  return mlp ? mlp_cta_bytes() + m + (size_t)tile_wgs * MLP_ACT_BYTES : m;
+  return mlp ? mlp_cta_bytes() + m : m;
 }
 
 }  // namespace ks

@@ -91,7 +91,6 @@ __global__ void __launch_bounds__(128) probe_wait_timeout(uint32_t* sink) {
   }
   __syncthreads();
   MlpWG g;
-  g.act = nullptr;
   g.bar = &bar;
   g.tmem = 0u;
   g.bar_id = 1;
