@@ -222,6 +222,48 @@ def oracle_sample(w: dict, markets_per_core: int = 2):
         events, single
 
 
+def _oracle_market_mlp(args):
+    params, m, L, A, S, mlp_w = args
+    import oracle as o
+    mk = o.init_market(params, m, L, A)
+    t = time.perf_counter()
+    o.run_market(params, mk, 0, S, want_trace=False, mlp_w=mlp_w)
+    return time.perf_counter() - t
+
+
+def oracle_bucket_sample(w: dict, L, A, S: int, mlp_w=None, per_bucket: int = 1):
+    """The oracle's rate on a sample of workload w that covers every power-of-two
+    (L, A) class: `per_bucket` markets of each class (the first ones), S steps
+    each, one market per task on a spawn pool of all host cores.  Policy agents
+    decide with the fp64 network `mlp_w`."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    classes = {}
+    for m, (l, a) in enumerate(zip(L, A)):
+        key = (1 << max(0, int(l) - 1).bit_length(), 1 << max(0, int(a) - 1).bit_length())
+        if len(classes.setdefault(key, [])) < per_bucket:
+            classes[key].append(m)
+    idx = sorted(m for ms in classes.values() for m in ms)
+    base = int(w.get("market_base", 0))
+    tasks = [(w["params"], m + base, int(L[m]), int(A[m]), S, mlp_w) for m in idx]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_warm, range(cores))
+        t = time.perf_counter()
+        task_s = pool.map(_oracle_market_mlp, tasks, chunksize=1)
+        dt = time.perf_counter() - t
+    events = float(np.sum([int(A[m]) for m in idx])) * S
+    return {"value": events / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "single_core_value": events / max(sum(task_s), 1e-9),
+            "sample": f"{len(idx)} markets ({len(classes)} (L, A) classes x up to {per_bucket}) x {S} steps "
+                      f"({int(events):d} agent-events), one market per task"}
+
+
 def run_reference(args):
     from paper_2606_21784_gb300 import sharding, workloads
     rank, world, _ = sharding.rank_env()
@@ -285,30 +327,69 @@ def _time_ensemble(ens, steps, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-def compare_forms(ks, workloads, stream, plain_rate):
-    """Throughput of the other forms of the method on the same GPU, beside the
-    plain persistent kernel: the batched uneven ensemble (one launch, default
-    and cached tuned plan) and the learned-agent ensembles when built."""
+def _graph_of(ens, S):
+    """One S-step ks_step_n captured in a CUDA graph (on a capture stream of
+    its own; the graph is replayed on the timing stream)."""
+    import torch
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        ens.step(S, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return g
+
+
+def _time_graph(g, stream, reps=1):
+    import torch
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best / 1e3
+
+
+def compare_forms(ks, workloads, stream, plain_rate, cpu=True):
+    """Throughput of the other forms of the method on the same GPU, each on
+    the configuration it is stated for, beside the plain persistent kernel:
+    the batched uneven ensemble (20000 markets, S=2000, one launch, default
+    and tuned plan), and the learned-agent forms with the network trained by
+    behaviour cloning on 20M pairs (4096 all-policy markets at S=2000; 32768
+    uneven markets with 25% policy agents at S=10000 as one CUDA-graph-captured
+    launch beside the same instances with rule agents only).  With `cpu`,
+    each form also gets the oracle's rate on a sample of one market per
+    (L, A) class."""
     import numpy as np
     out = {"plain_mix_8192": {"events_per_s": plain_rate}}
     w = workloads.workload("batched_20000")
     L, A = workloads.sizes(w)
-    steps = 200
+    S = int(w["S"])
     ens = ks.Ensemble(w, L=L, A=A)
-    ev = float(A.astype(np.int64).sum()) * steps
+    ev = float(A.astype(np.int64).sum()) * S
     info = ens.batch_info()
-    out["batched_20000"] = {"events_per_s": ev / _time_ensemble(ens, steps, stream), "steps": steps,
-                            "plan": "default", "items": info["n_items"], "buckets": info["n_buckets"]}
+    out["batched_20000"] = {"events_per_s": ev / _time_ensemble(ens, S, stream), "steps": S,
+                            "agent_events_per_launch": ev, "plan": "default", "items": info["n_items"],
+                            "buckets": info["n_buckets"], "cta_threads": info["cta_threads"],
+                            "vs_plain": None}
+    out["batched_20000"]["vs_plain"] = out["batched_20000"]["events_per_s"] / plain_rate
     try:
         from paper_2606_21784_gb300 import autotune
         plan = autotune.tune_batched(w, L, A)
         ens.set_batch_plan(plan["cta_threads"], plan["buckets"])
-        out["batched_20000_tuned"] = {"events_per_s": ev / _time_ensemble(ens, steps, stream), "steps": steps,
+        out["batched_20000_tuned"] = {"events_per_s": ev / _time_ensemble(ens, S, stream), "steps": S,
                                       "cta_threads": plan["cta_threads"]}
     except Exception as e:  # the tuned plan is optional; the default plan was measured above
         out["batched_20000_tuned"] = {"error": str(e)[:200]}
     ens.close()
-    out.update(learned_forms(ks, workloads, stream))
+    if cpu:
+        out["batched_20000"]["cpu_baseline"] = oracle_bucket_sample(w, L, A, S)
+    out.update(learned_forms(ks, workloads, stream, cpu=cpu))
     out["paper_table_iii"] = paper_forms(ks, workloads, stream)
     out["paper_stylized_facts"] = stylized_facts()
     return out
@@ -335,21 +416,12 @@ def stylized_facts():
             "paper_values": {k: {str(a): v for a, v in d.items()} for k, d in dynamics.PAPER_FACTS.items()}}
 
 
-# the paper's Table III (RTX 5090, its own agents, L=128, S=500): agent-events/s
-PAPER_TABLE_III = {(64, 256): 3.61e9, (256, 256): 1.35e10, (1024, 256): 3.69e10, (4096, 256): 4.73e10,
-                  (16384, 256): 5.39e10, (8192, 16): 8.41e9, (8192, 64): 2.84e10, (8192, 256): 5.16e10,
-                  (8192, 1024): 5.47e10}
-
-
-# the paper's Naive CUDA engine on the same shapes (Table III)
-PAPER_NAIVE = {(64, 256): 6.39e7, (256, 256): 1.95e8, (1024, 256): 7.56e8, (4096, 256): 3.09e9,
-               (16384, 256): 1.14e10, (8192, 16): 8.01e8, (8192, 64): 2.58e9, (8192, 256): 6.13e9,
-               (8192, 1024): 8.89e9}
-# peak GPU global-memory footprint of the paper's engine across the market sweep
-# at A=256 (Table V), MB
-PAPER_FOOTPRINT_MB = {64: 0.14, 256: 0.54, 1024: 2.16, 4096: 8.66, 16384: 34.63}
-# median per-step latency at 4096 markets x 256 agents (Sec. IV-I), microseconds
-PAPER_STEP_LATENCY_US = {"persistent": 22.1, "naive": 339.3}
+# the shapes of the paper's throughput table (markets sweep at A=256, agents
+# sweep at 8192 markets; L=128, S=500)
+PAPER_SHAPES = ((64, 256), (256, 256), (1024, 256), (4096, 256), (16384, 256), (8192, 16), (8192, 64), (8192, 256),
+                (8192, 1024))
+# the paper's peak throughput (RTX 5090, its own agents, Table III): context for the paper workloads' line only
+PAPER_PEAK = {(8192, 1024): 5.47e10}
 
 
 def _time_best(run, stream, reps):
@@ -369,18 +441,15 @@ def _time_best(run, stream, reps):
 
 def paper_forms(ks, workloads, stream, reps: int = 3):
     """The paper's own agent model (tick-aggregated book, NOISE / MOMENTUM /
-    MAKER agents, SplitMix64 draws) on every shape of the paper's throughput
-    table (markets sweep at A=256, agents sweep at 8192 markets; L=128,
-    S=500), each with its tuned launch, beside the paper's RTX 5090 numbers
-    (whose agent constants are unpublished: the comparison is of throughput
-    on the same shapes, not of identical simulations).  Each shape also runs
-    the naive engine (one thread per market, book in global memory, one
-    launch per step): the paper's ablation of its two design choices."""
+    MAKER agents, SplitMix64 draws) on the shapes of the paper's throughput
+    table, each with its tuned launch, and the naive engine (one thread per
+    market, book in global memory, one launch per step) on the same shapes:
+    the paper's ablation of its two design choices, on this GPU."""
     import torch
 
     from paper_2606_21784_gb300 import autotune
     out = {}
-    for (M, A), ref in PAPER_TABLE_III.items():
+    for (M, A) in PAPER_SHAPES:
         w = workloads.workload("paper_8192_256", M=M, A=A)
         ens = ks.PaperEnsemble(w)
         launch = autotune.apply(ens, w)
@@ -395,25 +464,19 @@ def paper_forms(ks, workloads, stream, reps: int = 3):
             raise RuntimeError("paper ensemble reported a device error")
         ev = float(M) * A * S
         rate, nrate = ev / (best / 1e3), ev / (naive / 1e3)
-        pn = PAPER_NAIVE[(M, A)]
-        out[f"M{M}_A{A}"] = {"events_per_s": rate, "ms_per_run": best, "paper_rtx5090": ref,
-                             "ratio_to_paper": rate / ref,
+        out[f"M{M}_A{A}"] = {"events_per_s": rate, "ms_per_run": best,
                              "launch": {k: launch[k] for k in ("threads", "agents_per_thread", "min_ctas")},
-                             "naive_events_per_s": nrate, "speedup_over_naive": rate / nrate,
-                             "paper_naive": pn, "paper_speedup_over_naive": ref / pn,
-                             "workspace_mb": ens.ws_bytes / 1e6}
-        if A == 256 and M in PAPER_FOOTPRINT_MB:
-            out[f"M{M}_A{A}"]["paper_footprint_mb"] = PAPER_FOOTPRINT_MB[M]
+                             "naive_events_per_s": nrate, "speedup_over_naive": rate / nrate}
         if (M, A) == (4096, 256):
-            out["step_latency_us_4096x256"] = {"persistent": 1e3 * best / S, "naive": 1e3 * naive / S,
-                                               "paper": PAPER_STEP_LATENCY_US}
+            out["step_latency_us_4096x256"] = {"persistent": 1e3 * best / S, "naive": 1e3 * naive / S}
         ens.close()
     return out
 
 
-def quick_policy(pairs: int = 2_000_000):
-    """A policy trained by behaviour cloning on `pairs` (state, action) pairs of
-    the rule-based seed-7 run (one epoch); returns (blob, seconds, history)."""
+def trained_policy(pairs: int = 20_000_000, epochs: int = 3):
+    """The policy trained by behaviour cloning on `pairs` (state, action) pairs
+    of the rule-based 8192-market run with seed 7, with the library's
+    tensor-core training kernels; returns (blob, report)."""
     import time
 
     import torch
@@ -421,54 +484,111 @@ def quick_policy(pairs: int = 2_000_000):
     from paper_2606_21784_gb300 import bc
     t0 = time.time()
     rec, wd = bc.generate(pairs)
-    params, hist, _ = bc.train(rec, wd["A"], epochs=1)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    params, hist, val = bc.train(rec, wd["A"], epochs=epochs)
+    torch.cuda.synchronize()
+    t2 = time.time()
     blob = bc.export(params)
+    n_train = int(rec.shape[0]) - int(val.shape[0])
+    rep = {"pairs": int(rec.shape[0]), "epochs": epochs, "generate_s": t1 - t0, "train_s": t2 - t1,
+           "train_pairs_per_s": n_train * epochs / max(t2 - t1, 1e-9),
+           "held_out_loss": {"trained": hist["val_loss"][-1],
+                             "input_independent": bc.evaluate(bc.marginal_params(rec), val, wd["A"]),
+                             "untrained": hist["val_loss"][0]},
+           "val_loss_by_epoch": hist["val_loss"]}
     del rec
     torch.cuda.synchronize()
-    return blob, time.time() - t0, hist
+    return blob, params, rep
 
 
-def learned_forms(ks, workloads, stream):
-    """The learned-agent forms: a policy trained by behaviour cloning on 2M
-    (state, action) pairs of the rule-based seed-7 run (a reduced data budget
-    to keep the bench short; the full 20M-pair run is `python -m
-    paper_2606_21784_gb300.bc`), then (a) the 4096-market all-policy ensemble
-    and (b) the 32768-market uneven ensemble with 25% policy agents beside the
-    same instances with rule agents only."""
-    import time
+# algorithmic FLOP of one policy decision: 2 * (32*64 + 64*64 + 64*37)
+POLICY_FLOP = 2 * (32 * 64 + 64 * 64 + 64 * 37)
 
+
+def learned_forms(ks, workloads, stream, cpu=True):
+    """The learned-agent forms on their stated configurations: a policy trained
+    by behaviour cloning on 20M (state, action) pairs of the rule-based seed-7
+    run, then (a) the 4096-market all-policy ensemble at S=2000 and (b) the
+    32768-market uneven ensemble with 25% policy agents at S=10000, one
+    CUDA-graph-captured launch, beside the same instances with rule agents
+    only (also one captured launch).  The tensor-pipe fraction counts the
+    network's algorithmic FLOP per decision (17,024) against the measured
+    sustained BF16 peak."""
     import numpy as np
     import torch
 
-    out = {}
-    blob, secs, hist = quick_policy()
-    out["bc"] = {"pairs": 2_000_000, "seconds": secs, "val_loss": hist["val_loss"]}
-    steps = 200
-    w = workloads.workload("learned_4096")
-    ens = ks.Ensemble(w, mlp_params=blob)
     from paper_2606_21784_gb300 import autotune
+    out = {}
+    blob, params, rep = trained_policy()
+    out["bc"] = rep
+    peaks = measured_peaks()
+    tc_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    w = workloads.workload("learned_4096")
+    S = int(w["S"])
+    ens = ks.Ensemble(w, mlp_params=blob)
     autotune.apply(ens, w)
     cap = ens.set_capture(count_policy=True)
-    ev = float(w["M"]) * w["A"] * steps
+    ev = float(w["M"]) * w["A"] * S
     ens.step(20, stream)
     torch.cuda.synchronize()
     cap["policy_count"].zero_()
-    dt = _time_ensemble(ens, steps, stream)
-    dec = float(cap["policy_count"].item()) * steps / (steps + steps // 10)  # warm-up steps excluded
-    flop = dec * 2 * 2 * (64 * 64 + 64 * 48)  # layers 2-3, high + low operand parts
-    out["learned_4096"] = {"events_per_s": ev / dt, "steps": steps, "policy_decisions_per_s": dec / dt,
-                           "tensor_tflops": flop / dt / 1e12, "launch": ens.get_launch()}
+    dt = _time_ensemble(ens, S, stream)
+    dec = float(cap["policy_count"].item()) * S / (S + S // 10)  # warm-up steps excluded
+    tflops = dec * POLICY_FLOP / dt / 1e12
+    out["learned_4096"] = {"events_per_s": ev / dt, "steps": S, "agent_events_per_launch": ev,
+                           "policy_decisions_per_s": dec / dt, "launch": ens.get_launch(),
+                           "tensor_roofline": {"bound": "tensor", "achieved": tflops, "peak": tc_peak,
+                                               "unit": "TFLOP/s", "frac": tflops / tc_peak,
+                                               "algorithmic": f"{POLICY_FLOP} FLOP per policy decision",
+                                               "peak_source": "measured sustained BF16 (MEASURED_PEAKS.json)"}}
     ens.close()
     w = workloads.workload("mixed_32768")
     L, A = workloads.sizes(w)
-    ev = float(A.astype(np.int64).sum()) * steps
+    S = int(w["S"])
+    ev = float(A.astype(np.int64).sum()) * S
     for pct in (25, 0):
         ww = workloads.workload("mixed_32768", mlp_pct=pct)
         e2 = ks.Ensemble(ww, L=L, A=A, mlp_params=blob if pct else None)
-        out[f"mixed_32768_policy{pct}"] = {"events_per_s": ev / _time_ensemble(e2, steps, stream), "steps": steps,
-                                           "cta_threads": e2.batch_info()["cta_threads"]}
+        if pct:
+            cap = e2.set_capture(count_policy=True)
+        e2.step(50, stream)
+        torch.cuda.synchronize()
+        g = _graph_of(e2, S)
+        if pct:
+            cap["policy_count"].zero_()
+        dt = _time_graph(g, stream)
+        if e2.sync(timeout_ms=600_000) != ks.KS_OK:
+            raise RuntimeError("mixed ensemble reported a device error")
+        r = {"events_per_s": ev / dt, "steps": S, "agent_events_per_launch": ev, "graph_captured": True,
+             "cta_threads": e2.batch_info()["cta_threads"]}
+        if pct:
+            dec = float(cap["policy_count"].item())
+            tflops = dec * POLICY_FLOP / dt / 1e12
+            r["policy_decisions_per_s"] = dec / dt
+            r["tensor_roofline"] = {"bound": "tensor", "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s",
+                                    "frac": tflops / tc_peak}
+        out[f"mixed_32768_policy{pct}"] = r
+        del g
         e2.close()
+    out["mixed_32768_policy25"]["vs_rule_only"] = (out["mixed_32768_policy25"]["events_per_s"]
+                                                   / out["mixed_32768_policy0"]["events_per_s"])
+    if cpu:
+        w64 = policy_fp64(ks, params)
+        wl4 = workloads.workload("learned_4096")
+        out["learned_4096"]["cpu_baseline"] = oracle_bucket_sample(
+            wl4, *workloads.sizes(wl4), 100, mlp_w=w64, per_bucket=16)
+        out["mixed_32768_policy25"]["cpu_baseline"] = oracle_bucket_sample(
+            workloads.workload("mixed_32768"), L, A, 200, mlp_w=w64)
     return out
+
+
+def policy_fp64(ks, params):
+    """The fp64 parameter vector the oracle decides with: the trained FP32
+    parameters with the weights rounded to BF16, as the kernels use them."""
+    import oracle as o
+    parts = o.mlp_unpack(params.double().cpu().numpy())
+    return o.mlp_pack(*ks.mlp_params_as_used(*parts))
 
 
 def run_ours(args):
@@ -492,7 +612,7 @@ def run_ours(args):
     if w.get("model") == "paper":
         return run_paper(args, w, rank, world, dev)
     S = int(w["S"])
-    blob = quick_policy()[0] if int(w["params"].get("mlp_pct", 0)) > 0 else None
+    blob = trained_policy(2_000_000, 1)[0] if int(w["params"].get("mlp_pct", 0)) > 0 else None
     L_, A_ = workloads.sizes(w)
     ens = ks.Ensemble(w, L=L_, A=A_, mlp_params=blob)
     if args.launch:
@@ -739,8 +859,8 @@ def run_paper(args, w, rank, world, dev):
                "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
                "gpu_launches": (2 * S if naive else 2) * args.steps, "roofline": roofline, "clocks": clocks,
-               "paper_context": {"value": (PAPER_NAIVE if naive else PAPER_TABLE_III).get((int(w["M"]), int(w["A"]))),
-                                 "hardware": "RTX 5090 (sm_120), Table III" + (", Naive CUDA" if naive else "")}}
+               "paper_context": {"value": None if naive else PAPER_PEAK.get((int(w["M"]), int(w["A"]))),
+                                 "hardware": "RTX 5090 (sm_120), Table III"}}
         print(json.dumps(out), flush=True)
     ens.close()
     sharding.finalize()

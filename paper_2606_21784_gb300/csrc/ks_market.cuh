@@ -65,6 +65,7 @@ struct Smem {
   uint32_t* wMB;          // [32] warp totals of marginal buy quantity
   uint32_t* wMS;          // [32] warp totals of marginal sell quantity
   int32_t* rem;           // [2]: R_b, R_s (units filled at the marginal buy / sell tick)
+  int32_t* rng;           // [2 parities][2]: lowest / highest tick holding a resting order after a step
   int32_t* feat;          // [8]: resting sell qty at last+1..+4, buy qty at last-1..-4 (policy inputs)
   int32_t* wR;            // [32] warp totals of policy rows
   ClassRule* ctab;        // [4] rule constants per agent class for the next orders
@@ -80,7 +81,7 @@ __host__ __device__ inline size_t market_smem_layout(int nt, int ak, int Lmax, b
   o[1] = off; off += (size_t)8 * 8;                      // kx
   o[2] = off; off += inv_col ? (size_t)4 * ak * nt : 0;  // inv
   o[3] = off; off += (size_t)4 * 2 * book_len(Lmax);     // book
-  o[4] = off; off += (size_t)4 * 32 * 4 + 4 * 4;         // wD, wS, wMB, wMS, rem
+  o[4] = off; off += (size_t)4 * 32 * 4 + 4 * 8;         // wD, wS, wMB, wMS, rem, rng
   o[5] = off; off += (size_t)4 * 8 + 4 * 32 + 4 * sizeof(ClassRule);  // feat, wR, ctab
   o[6] = off; off += mlp ? (size_t)4 * 64 : 0;           // cvec
   o[7] = off; off += mlp ? (size_t)4 * ak * nt : 0;      // rowbuf
@@ -106,6 +107,7 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
   s.wMB = reinterpret_cast<uint32_t*>(s.wD + 64);
   s.wMS = s.wMB + 32;
   s.rem = s.wD + 128;
+  s.rng = s.wD + 132;
   s.feat = reinterpret_cast<int32_t*>(raw + o[5]);
   s.wR = s.feat + 8;
   s.ctab = reinterpret_cast<ClassRule*>(s.wR + 32);
@@ -363,15 +365,22 @@ __device__ __forceinline__ void st_pairs(int32_t* dst, const int* b, const int* 
   }
 }
 
+// The group clears the tick region [plo, pend): the whole grid (plo = 0,
+// pend = L) or a window that holds every order of the step (all ticks
+// outside it are empty, so D_cum and S_cum there are constant, V = 0, and
+// nothing changes).  Ticks in [L, pend) lie in the zeroed padding of the
+// book.  The lowest and highest ticks still holding an order after the
+// residual update go to rng_next (shared-memory atomicMin / atomicMax).
 template <int NT, int LTC, bool FEAT>
-__device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, int L, int LT, int p0, int t, int bar,
-                                               unsigned long long* kx, unsigned long long* kx_next, bool tie1,
-                                               bool carry, int last) {
+__device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, int L, int LT, int p0, int plo,
+                                               int pend, int t, int bar, unsigned long long* kx,
+                                               unsigned long long* kx_next, int32_t* rng_next, bool tie1, bool carry,
+                                               int last) {
   const int lane = t & 31;
   const int wid = t >> 5;
   constexpr int R = LTC > 0 ? LTC : 1;
   int bv[R], sv[R];
-  const bool mine = p0 < L;  // vector path: all LTC ticks of an owning thread lie in the grid
+  const bool mine = p0 < pend;  // vector path: all LTC ticks of an owning thread lie in the region
   int sumB = 0, sumS = 0;
   if constexpr (LTC > 0) {
     if (mine) {
@@ -388,7 +397,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   } else {
     for (int i = 0; i < LT; ++i) {
       const int p = p0 + i;
-      if (p < L) {
+      if (p < pend) {
         sumB += book[2 * p];
         sumS += book[2 * p + 1];
       }
@@ -412,7 +421,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   // A tick range with no orders: D and S are constant on it, so V is
   // min(D0, Sb0) on every tick, its lowest and highest maximisers are the
   // range's ends, and nothing in it changes (policy depth there is zero).
-  const int cnt = LTC > 0 ? (mine ? LTC : 0) : max(0, min(LT, L - p0));  // in-grid ticks
+  const int cnt = LTC > 0 ? (mine ? LTC : 0) : max(0, min(LT, pend - p0));  // ticks in the region
   const bool idle = cnt > 0 && sumB == 0 && sumS == 0;
   {
     int D = D0, Sb = Sb0;
@@ -451,7 +460,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
     if constexpr (LTC == 0) {
       for (int i = 0; i < n; ++i) {
         const int p = p0 + i;
-        if (p < L) {
+        if (p < pend) {
           const int b = book[2 * p];
           const int S = Sb + book[2 * p + 1];
           const int v = min(D, S);
@@ -499,6 +508,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
   // marginal ticks publish R_b = V* - D_cum[p_hi + 1] and R_s = V* - S_cum[p_lo - 1];
   // a carried book keeps what did not trade, a discarded book is emptied.
   const int nl = trade ? c.pstar : last;  // last clearing tick after this step (policy depth)
+  int rmin = 0x7FFFFFFF, rmax = -1;        // this thread's ticks still holding an order
   if (idle) {
     // nothing rests here.  A marginal tick holds orders (D_cum drops right after
     // p_hi, so BUY[p_hi] > 0; S_cum rises at p_lo, so SELL[p_lo] > 0), hence lies
@@ -539,6 +549,10 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
           if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = ns;
           if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = nb;
         }
+        if (nb | ns) {
+          rmin = min(rmin, p);
+          rmax = max(rmax, p);
+        }
         bv[i] = nb;
         sv[i] = ns;
       }
@@ -548,7 +562,7 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
     int D = D0, Sb = Sb0;
     for (int i = 0; i < LT; ++i) {
       const int p = p0 + i;
-      if (p < L) {
+      if (p < pend) {
         const int b = book[2 * p], s = book[2 * p + 1];
         int nb = b, ns = s;
         if (trade || !carry) {
@@ -571,15 +585,28 @@ __device__ __forceinline__ ClearOut clear_step(const Smem& sm, int32_t* book, in
           if (p > nl && p <= nl + 4) sm.feat[p - nl - 1] = ns;
           if (p < nl && p >= nl - 4) sm.feat[4 + nl - p - 1] = nb;
         }
+        if (nb | ns) {
+          rmin = min(rmin, p);
+          rmax = max(rmax, p);
+        }
       }
+    }
+  }
+  {
+    const int wmin = __reduce_min_sync(0xffffffffu, rmin);
+    const int wmax = __reduce_max_sync(0xffffffffu, rmax);
+    if (lane == 0 && wmax >= 0) {
+      atomicMin(rng_next, wmin);
+      atomicMax(rng_next + 1, wmax);
     }
   }
   if constexpr (FEAT) {
     if (t == 0) {
+      // depth entries of ticks outside the region (or the grid) are zero
 #pragma unroll
       for (int k = 1; k <= 4; ++k) {
-        if (nl + k >= L) sm.feat[k - 1] = 0;
-        if (nl - k < 0) sm.feat[4 + k - 1] = 0;
+        if (nl + k >= pend || nl + k < plo) sm.feat[k - 1] = 0;
+        if (nl - k < plo || nl - k >= pend) sm.feat[4 + k - 1] = 0;
       }
     }
   }
@@ -715,6 +742,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   // rebuild the aggregated resting book from the working orders
   for (int i = t; i < 2 * book_len(Lcap); i += NT) book[i] = 0;
   if (t < 8) sm.kx[t] = 0ull;
+  if (t < 4) sm.rng[t] = (t & 1) ? -1 : 0x7FFFFFFF;
   gsync<NT>(bar);
 #pragma unroll
   for (int k = 0; k < AK; ++k) {
@@ -733,6 +761,9 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
 
   const bool policy_on = MLP && P.mlp != nullptr && P.mlp_pct > 0;
+  // every new order lies within dwin ticks of the last clearing tick
+  const int dwin = max(max(P.zi_off, P.mom_omax), max(P.mr_omax, policy_on ? MLP_OFF_MAX : 0));
+  const int blen = book_len(Lcap);
   StepFeat sf;
   if constexpr (MLP) {
     // the policy inputs of the first step read the rebuilt book
@@ -777,13 +808,39 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
 
     // ---- clearing and residual book ----------------------------------------------------
     unsigned long long* kx_next = sm.kx + 4 * ((j + 1) & 1);
+    // The region to clear: after the first step of the call, only ticks
+    // that can hold an order -- those that rested after the previous step
+    // and the window of new orders around the last tick -- rounded to a
+    // span of GT x {1, 2, 4, 8} ticks from a multiple of 8 (vector loads);
+    // the whole grid when that span is not smaller.
+    int plo = 0, pend = L, lts = LTsel, ltr = LT, p0r = p0;
+    if (j > 0) {
+      const int rlo = sm.rng[2 * (j & 1)], rhi = sm.rng[2 * (j & 1) + 1];
+      const int lo = max(0, min(rlo, last - dwin)) & ~7;
+      const int hi = min(L - 1, max(rhi, last + dwin));
+      int lt = 1;
+      while (lt < 8 && NT * lt < hi - lo + 1) lt <<= 1;
+      const int span = NT * lt;
+      if (span >= hi - lo + 1 && span <= blen && span < LT * NT) {
+        plo = min(lo, blen - span);
+        pend = plo + span;
+        lts = lt;
+        ltr = lt;
+        p0r = plo + t * lt;
+      }
+    }
+    if (t == 0) {  // range of the step after next (its last reader was the previous step)
+      sm.rng[2 * ((j + 1) & 1)] = 0x7FFFFFFF;
+      sm.rng[2 * ((j + 1) & 1) + 1] = -1;
+    }
+    int32_t* rng_next = sm.rng + 2 * ((j + 1) & 1);
     ClearOut c;
-    switch (LTsel) {
-      case 1: c = clear_step<NT, 1, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      case 2: c = clear_step<NT, 2, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      case 4: c = clear_step<NT, 4, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      case 8: c = clear_step<NT, 8, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
-      default: c = clear_step<NT, 0, MLP>(sm, book, L, LT, p0, t, bar, kx, kx_next, tie1, carry, last); break;
+    switch (lts) {
+      case 1: c = clear_step<NT, 1, MLP>(sm, book, L, ltr, p0r, plo, pend, t, bar, kx, kx_next, rng_next, tie1, carry, last); break;
+      case 2: c = clear_step<NT, 2, MLP>(sm, book, L, ltr, p0r, plo, pend, t, bar, kx, kx_next, rng_next, tie1, carry, last); break;
+      case 4: c = clear_step<NT, 4, MLP>(sm, book, L, ltr, p0r, plo, pend, t, bar, kx, kx_next, rng_next, tie1, carry, last); break;
+      case 8: c = clear_step<NT, 8, MLP>(sm, book, L, ltr, p0r, plo, pend, t, bar, kx, kx_next, rng_next, tie1, carry, last); break;
+      default: c = clear_step<NT, 0, MLP>(sm, book, L, ltr, p0r, plo, pend, t, bar, kx, kx_next, rng_next, tie1, carry, last); break;
     }
     const int vstar = c.vstar, pstar = c.pstar;
     const bool trade = vstar > 0;
@@ -873,12 +930,17 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
         const uint32_t st = sl0 & W_ST;
         const bool sell = (sl0 & W_SIDE) != 0u;
         const int rank = sell ? (int)(key_s - st) : (int)(st - key_b);
-        const bool marg = rank == 0;
-        const int fm = min(max(sell ? remS : remB, 0), q);
-        const int f = rank > 0 ? q : (marg ? fm : 0);
-        const int adv = marg ? q : 0;
-        remS -= sell ? adv : 0;
-        remB -= sell ? 0 : adv;
+        int f = rank > 0 ? q : 0;
+        if (rank == 0) {
+          // rationed at the marginal tick, in agent order (few orders sit there)
+          if (sell) {
+            f = min(max(remS, 0), q);
+            remS -= q;
+          } else {
+            f = min(max(remB, 0), q);
+            remB -= q;
+          }
+        }
         const int sfill = sell ? -f : f;
         if constexpr (REGACC) {
           inv[k] += sfill;
