@@ -275,6 +275,9 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
   gsync<NT>(bar);
   if (t == 0 && total > 0 && P.pol_count) atomicAdd(P.pol_count, (unsigned long long)total);
   if (total > 0 && mw.wg < mw.nwg) {
+    // stream-3 draws (counter (sdec, agent, market, 3)): the agent-independent
+    // parts of rounds 1-3 once per step, as for the per-step draws
+    const StepKey sk3 = step_key(sdec, gm, 3u, P.rk);
     for (int tile = mw.wg; tile * 128 < total; tile += mw.nwg) {
       const int row = tile * 128 + (t & 127);
       const bool valid = row < total;
@@ -284,7 +287,7 @@ __device__ __forceinline__ void policy_phase(const DevParams& P, const Smem& sm,
       float z[MLP_OUT];
       mlp_tile_logits(mw, sw, sm.cvec, (float)inv * (1.0f / 256.0f), z, P.err);
       if (valid) {
-        const uint4 w = philox_rk(sdec, (uint32_t)a, gm, 3u, P.rk);
+        const uint4 w = step_draw_x0(sk3, sk3.c0 ^ (uint32_t)a, P.rk);
         sm.rowbuf[row] = mlp_decision(z, w, last, L, P.rb_qmax);
         if (traced && P.logit_trace && sdec < P.trace_steps) {
           float* zo = P.logit_trace + ((size_t)sdec * P.dec_trace_agents + (size_t)(aoff + a)) * MLP_OUT;

@@ -298,11 +298,19 @@ __device__ __forceinline__ void mlp_cta_teardown(const MlpCta& c) {
 // inverse-CDF draws of side (w0) and tick offset (w1) from the softmax of
 // their heads, quantity clamp(round(exp(z[36])), 1, qmax).
 // ---------------------------------------------------------------------------------------------
+// Largest of z[0, N) as a pairwise tree (max is exact in any order).
+template <int N>
+__device__ __forceinline__ float max_tree(const float* z) {
+  if constexpr (N == 1) {
+    return z[0];
+  } else {
+    return fmaxf(max_tree<N / 2>(z), max_tree<N - N / 2>(z + N / 2));
+  }
+}
+
 template <int N>
 __device__ __forceinline__ int mlp_sample(const float* z, uint32_t w) {
-  float mx = z[0];
-#pragma unroll
-  for (int i = 1; i < N; ++i) mx = fmaxf(mx, z[i]);
+  const float mx = max_tree<N>(z);
   // running sums c_i of exp(z - max); the total is c_{N-1}
   float c[N];
   float run = 0.0f;
