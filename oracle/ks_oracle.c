@@ -924,3 +924,141 @@ done:
   free(buy); free(sell); free(dcum); free(scum); free(vol); free(cls);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Continuous double auction (the pattern's generalisation the paper names    */
+/* in its discussion section; its rules are readings C1-C6).                  */
+/*                                                                            */
+/* The agents, draws, cancellation and rule decisions are the main model's.   */
+/* Each step: C1 every working order is cancelled with its step-s draw;       */
+/* C2 every agent without a working order decides from the step-start state  */
+/* (the rule of ko_decide_rule); C3 the new orders arrive one by one in       */
+/* ascending agent index and each trades at once against the opposite side   */
+/* in price-time priority: the best price first, at a price the earliest     */
+/* arrival first, each fill at the resting order's tick, while the incoming  */
+/* limit still crosses; the remainder rests with arrival stamp s * A + a.    */
+/* C4 every fill moves inventory and cash at the fill's tick.  C5 the step's  */
+/* last clearing tick is that of its last fill (unchanged without fills), the */
+/* history shifts it in, trades counts fills, sum_p adds tick * qty of every  */
+/* fill, sum_v and last_v the step's volume, and the trace hash folds (last   */
+/* fill tick or -1, step volume).  C6 the resting book has no identity beyond */
+/* (side, tick, stamp): it is plain per-agent state, and price-time priority  */
+/* is evaluated by scanning the agents (slow and plain).                      */
+/* ------------------------------------------------------------------------ */
+
+/* The resting order that an incoming order of side `side` (0 buy, 1 sell)
+ * with limit `tick` trades against next: the best opposite price that
+ * crosses, among those the smallest stamp; -1 if none crosses. */
+static int32_t ko_cda_best(int32_t A, const ko_agents* ag, const int64_t* stamp, int32_t side, int32_t tick) {
+  int32_t best = -1;
+  for (int32_t b = 0; b < A; ++b) {
+    if (ag->qty[b] <= 0 || ag->side[b] == side) continue;
+    const int32_t t = ag->tick[b];
+    if (side == 0 ? t > tick : t < tick) continue; /* does not cross the limit */
+    if (best < 0) { best = b; continue; }
+    const int32_t tb = ag->tick[best];
+    const int better = side == 0 ? (t < tb) : (t > tb);
+    if (better || (t == tb && stamp[b] < stamp[best])) best = b;
+  }
+  return best;
+}
+
+/* Run steps [s0, s0 + n) of CDA market m.  stamp[a]: arrival stamp of a's
+ * resting order (-1 if none).  trace_p / trace_v (nullable) receive the last
+ * fill tick (-1 without fills) and the volume of each step.  fills (nullable,
+ * fills_cap rows of 5 int32: step, incoming agent, resting agent, tick, qty)
+ * receives the fill log, *fills_count the number of fills (also beyond the
+ * capacity).  inject (nullable, test use): entry j * A + a replaces the
+ * decision of agent a at step j of the call if it decides (qty <= 0: no
+ * order).  Returns 0 on success. */
+int ko_cda_run(const ko_params* P, uint32_t m, int32_t L, int32_t A, ko_agents* ag, int64_t* stamp,
+               ko_market_scalars* ms, uint32_t s0, uint32_t n, int32_t* trace_p, int32_t* trace_v, int32_t* fills,
+               int64_t fills_cap, int64_t* fills_count, const ko_replay* inject) {
+  if (L < 2 || A < 0) return -1;
+  for (int32_t a = 0; a < A; ++a)
+    if (ag->mlp[a]) return -5; /* policy agents are not part of this model */
+  int32_t* dside = (int32_t*)malloc(sizeof(int32_t) * (size_t)(A > 0 ? A : 1));
+  int32_t* dtick = (int32_t*)malloc(sizeof(int32_t) * (size_t)(A > 0 ? A : 1));
+  int32_t* dqty = (int32_t*)malloc(sizeof(int32_t) * (size_t)(A > 0 ? A : 1));
+  if (!dside || !dtick || !dqty) { free(dside); free(dtick); free(dqty); return -2; }
+  int64_t nf = fills_count ? *fills_count : 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    const uint32_t s = s0 + j;
+    /* C1 cancellations and C2 decisions, all from the step-start state */
+    for (int32_t a = 0; a < A; ++a) {
+      uint32_t w[4];
+      ko_draw(P->seed, s, (uint32_t)a, m, 0u, w);
+      dqty[a] = 0;
+      if (ag->qty[a] > 0 && w[0] < P->cancel_thresh) {
+        ag->qty[a] = 0;
+        stamp[a] = -1;
+      }
+      if (ag->qty[a] > 0) continue;
+      if (inject) {
+        const size_t e = (size_t)j * (size_t)A + (size_t)a;
+        dside[a] = inject->side[e];
+        dtick[a] = inject->tick[e];
+        dqty[a] = inject->qty[e];
+        if (dqty[a] > 0 && (dside[a] < 0 || dside[a] > 1 || dtick[a] < 0 || dtick[a] >= L)) {
+          free(dside); free(dtick); free(dqty);
+          return -6;
+        }
+        continue;
+      }
+      ko_decide_rule(P, L, ag->atype[a], ms, w, &dside[a], &dtick[a], &dqty[a]);
+    }
+    /* C3 arrivals in agent order */
+    int64_t vol = 0;
+    int32_t last_fill = -1;
+    for (int32_t a = 0; a < A; ++a) {
+      int32_t q = dqty[a];
+      if (q <= 0) continue;
+      const int32_t sd = dside[a], tk = dtick[a];
+      while (q > 0) {
+        const int32_t r = ko_cda_best(A, ag, stamp, sd, tk);
+        if (r < 0) break;
+        const int32_t px = ag->tick[r];
+        const int32_t f = q < ag->qty[r] ? q : ag->qty[r];
+        /* C4 accounts at the resting order's tick */
+        if (sd == 0) {
+          ag->inv[a] += f; ag->cash[a] -= (int64_t)px * f;
+          ag->inv[r] -= f; ag->cash[r] += (int64_t)px * f;
+        } else {
+          ag->inv[a] -= f; ag->cash[a] += (int64_t)px * f;
+          ag->inv[r] += f; ag->cash[r] -= (int64_t)px * f;
+        }
+        ag->qty[r] -= f;
+        if (ag->qty[r] == 0) stamp[r] = -1;
+        q -= f;
+        vol += f;
+        last_fill = px;
+        ms->trades += 1;
+        ms->sum_p += (int64_t)px * f;
+        if (fills && nf < fills_cap) {
+          int32_t* e = fills + 5 * nf;
+          e[0] = (int32_t)s; e[1] = a; e[2] = r; e[3] = px; e[4] = f;
+        }
+        nf += 1;
+      }
+      if (q > 0) { /* the remainder rests */
+        ag->side[a] = sd;
+        ag->tick[a] = tk;
+        ag->qty[a] = q;
+        stamp[a] = (int64_t)s * (int64_t)A + a;
+      }
+    }
+    /* C5 step statistics */
+    if (vol > 0x7FFFFFFF) { free(dside); free(dtick); free(dqty); return -7; }
+    if (last_fill >= 0) ms->last = last_fill;
+    for (int k = KO_HIST - 1; k > 0; --k) ms->hist[k] = ms->hist[k - 1];
+    ms->hist[0] = ms->last;
+    ms->last_v = (int32_t)vol;
+    ms->sum_v += vol;
+    ms->hash = ko_trace_hash_update(ms->hash, s, last_fill, (int32_t)vol);
+    if (trace_p) trace_p[j] = last_fill;
+    if (trace_v) trace_v[j] = (int32_t)vol;
+  }
+  if (fills_count) *fills_count = nf;
+  free(dside); free(dtick); free(dqty);
+  return 0;
+}

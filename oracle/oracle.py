@@ -170,6 +170,11 @@ def _load():
                                          ctypes.c_void_p, ctypes.c_void_p, P(PaperMarket), ctypes.c_uint32,
                                          ctypes.c_uint32, ctypes.c_void_p]
             lib.ko_paper_run.restype = ctypes.c_int
+            lib.ko_cda_run.argtypes = [P(Params), ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, P(_Agents),
+                                       ctypes.c_void_p, P(MarketScalars), ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       P(ctypes.c_int64), P(_Replay)]
+            lib.ko_cda_run.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -501,3 +506,55 @@ def paper_simulate(params: dict, market: int, L: int, A: int, steps: int):
     bk = paper_init(market, L, A)
     tp, tv = paper_run(params, bk, 0, steps)
     return bk, tp, tv
+
+
+# ---------------------------------------------------------------------------
+# Continuous double auction (the main model's agents, continuous matching)
+# ---------------------------------------------------------------------------
+def cda_init(params: dict, m: int, L: int, A: int):
+    """A CDA market: the main model's initial state plus arrival stamps (-1: no resting order)."""
+    mk = init_market(params, m, L, A)
+    mk.stamp = np.full(max(A, 1), -1, np.int64)[:A]
+    return mk
+
+
+def cda_run(params: dict, mk: Market, s0: int, n: int, fills_cap: int = 0, inject=None):
+    """Advance CDA market ``mk`` over steps [s0, s0+n); returns (trace_p, trace_v, fills)
+    with fills an int32 [count, 5] log (step, incoming agent, resting agent, tick, qty)
+    when ``fills_cap`` > 0.  ``inject`` (tests): dict of int32 arrays ``side``, ``tick``,
+    ``qty`` of shape (n, A) replacing the decisions of deciding agents."""
+    P = make_params(params)
+    keep = []
+    inj = None
+    if inject is not None:
+        keep = [np.ascontiguousarray(inject[k], dtype=np.int32) for k in ("side", "tick", "qty")]
+        for a in keep:
+            assert a.size == n * mk.A
+        inj = ctypes.byref(_Replay(*[_ptr(a) for a in keep]))
+    tp = np.zeros(max(n, 1), np.int32)
+    tv = np.zeros(max(n, 1), np.int32)
+    fl = np.zeros((max(fills_cap, 1), 5), np.int32)
+    cnt = ctypes.c_int64(0)
+    rc = _load().ko_cda_run(ctypes.byref(P), mk.m, mk.L, mk.A, ctypes.byref(mk._agents()), _ptr(mk.stamp),
+                            ctypes.byref(mk.sc), s0, n, _ptr(tp), _ptr(tv), _ptr(fl) if fills_cap > 0 else None,
+                            int(fills_cap), ctypes.byref(cnt), inj)
+    del keep
+    if rc != 0:
+        raise ValueError(f"ko_cda_run failed: {rc}")
+    return tp[:n], tv[:n], fl[:min(int(cnt.value), fills_cap)]
+
+
+def cda_next(mk: Market) -> np.ndarray:
+    """Time-priority successor of every resting order: the agent resting next at
+    the same side and tick (by arrival stamp), -1 for the last one and for agents
+    without a resting order."""
+    nxt = np.full(mk.A, -1, np.int32)
+    live = np.nonzero(mk.qty > 0)[0]
+    keys = {}
+    for a in live:
+        keys.setdefault((int(mk.side[a]), int(mk.tick[a])), []).append(int(a))
+    for ags in keys.values():
+        ags.sort(key=lambda x: int(mk.stamp[x]))
+        for x, y in zip(ags, ags[1:]):
+            nxt[x] = y
+    return nxt

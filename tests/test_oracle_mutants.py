@@ -52,6 +52,17 @@ MUTANTS = {
                              "w[i] -= lr * (m[i] / c1) / sqrt(v[i] / c2 + eps);"),
     "adam_b1_in_second_moment": ("v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];",
                                  "v[i] = b1 * v[i] + (1.0 - b1) * g[i] * g[i];"),
+    # the continuous double auction
+    "cda_lifo": ("if (better || (t == tb && stamp[b] < stamp[best])) best = b;",
+                 "if (better || (t == tb && stamp[b] > stamp[best])) best = b;"),
+    "cda_fill_at_arrival_price": ("const int32_t px = ag->tick[r];", "const int32_t px = tk;"),
+    "cda_worst_price_first": ("const int better = side == 0 ? (t < tb) : (t > tb);",
+                              "const int better = side == 0 ? (t > tb) : (t < tb);"),
+    "cda_strict_cross": ("if (side == 0 ? t > tick : t < tick) continue;",
+                         "if (side == 0 ? t >= tick : t <= tick) continue;"),
+    "cda_last_from_first_fill": ("        last_fill = px;\n", "        if (last_fill < 0) last_fill = px;\n"),
+    "cda_resting_seller_cash_sign": ("ag->inv[r] -= f; ag->cash[r] += (int64_t)px * f;",
+                                     "ag->inv[r] -= f; ag->cash[r] -= (int64_t)px * f;"),
     # the paper-agent mode
     "paper_maker_parity": ("sd = (int32_t)(((int64_t)a + (int64_t)s) % 2);",
                            "sd = (int32_t)(((int64_t)a + (int64_t)s + 1) % 2);"),
@@ -91,6 +102,7 @@ def test_pins_catch_mutant(name):
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                             os.path.join(ROOT, "tests", "test_oracle_mlp_pins.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_paper_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_paper_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_cda_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
