@@ -501,6 +501,86 @@ ks_status ks_adam_step(float* params, float* grad, float* m, float* v, int32_t s
 /* Writes the policy blob the step loop reads (BF16 weights, FP32 biases). */
 ks_status ks_mlp_export(const float* params, void* blob, void* stream);
 
+/*
+ * Continuous double auction (CDA).  The paper clears by a per-step call
+ * auction and names the continuous double auction as a market the same
+ * persistent, state-carrying pattern extends to (Discussion and
+ * Limitations; Conclusion and Future Work).  This ensemble keeps the main
+ * model's agents, draws, one working order per agent, per-order
+ * cancellation and accounts, and replaces the batch clearing by continuous
+ * matching.  Each step of a market:
+ *  1. every working order is cancelled iff its step-s draw word w0 is below
+ *     cancel_thresh_q32;
+ *  2. every agent without a working order decides from the step-start
+ *     state with the rule of the main model (zero intelligence, momentum,
+ *     mean reversion);
+ *  3. the new orders arrive one by one in ascending agent index; each
+ *     trades at once against the opposite side in price-time priority (best
+ *     price first, at one price the earliest arrival first), every fill at
+ *     the resting order's tick, while its limit still crosses; the
+ *     remainder rests behind the orders already at its tick;
+ *  4. each fill moves the buyer's and the seller's inventory and cash at the
+ *     fill's tick;
+ *  5. the last clearing tick becomes the tick of the step's last fill
+ *     (unchanged without fills); the trace records (that tick or -1, the
+ *     step's volume), which the trace hash folds as in ks_state_view.
+ * One warp runs one market at a time with the book in shared memory: a FIFO
+ * of resting agents per (side, tick) and a bitmap of the nonempty ticks per
+ * side.  Uniform markets; 2 <= L <= KS_MAX_TICKS, 0 <= A <= KS_CDA_MAX_AGENTS
+ * (KS_ERR_UNSUPPORTED beyond, or when one market's book does not fit the
+ * shared memory of a CTA).  The configuration's policy agents are not part
+ * of this model.
+ */
+#define KS_CDA_MAX_AGENTS 8192
+typedef struct ks_cda_config {
+  uint32_t n_markets;          /* M                                                  */
+  uint32_t market_base;        /* global index of market 0 (draws use it)           */
+  int32_t L;                   /* ticks                                              */
+  int32_t A;                   /* agents per market                                  */
+  uint64_t seed;
+  uint32_t cancel_thresh_q32;  /* per-order cancellation probability x 2^32          */
+  uint32_t mix_pct[3];         /* zero intelligence / momentum / mean reversion, sum 100 */
+  int32_t zi_offset, zi_qmax, mom_lookback, mom_offset_max, mr_offset_max, rb_qmax;
+                               /* as ks_config (offsets 0..2047, quantities 1..255)  */
+  uint32_t trace_markets;      /* leading markets that record a per-step trace       */
+  uint32_t trace_steps;
+} ks_cda_config;
+
+typedef struct ks_cda_ensemble ks_cda_ensemble;
+
+/* State of a CDA ensemble (caller-owned host buffers; NULL fields skipped). */
+typedef struct ks_cda_state_view {
+  uint32_t* order;       /* [N] order words as ks_state_view::order              */
+  int32_t* inventory;    /* [N]                                                    */
+  int64_t* cash;         /* [N]                                                    */
+  int32_t* next;         /* [N] the agent resting next at the same side and tick
+                            (time priority), -1 for the last one and for agents
+                            without a resting order                             */
+  int32_t* last_tick;    /* [M] last clearing tick                                 */
+  int32_t* history;      /* [M*KS_HISTORY] newest first                           */
+  int32_t* fundamental;  /* [M]                                                    */
+  int32_t* fills;        /* [M] fills so far                                       */
+  int32_t* last_volume;  /* [M] volume of the latest step                          */
+  int64_t* traded_value; /* [M] sum over fills of tick * quantity                  */
+  int64_t* sum_volume;   /* [M]                                                    */
+  uint64_t* trace_hash;  /* [M]                                                    */
+  uint64_t* step;        /* [1] absolute step counter                              */
+  int32_t* trace;        /* [trace_markets*trace_steps*2] (last fill tick or -1, volume) */
+} ks_cda_state_view;
+
+/* Workspace bytes; creation in a caller-owned device workspace (initial state
+ * as ks_create_ensemble: no resting orders, opening tick L/2; queued on
+ * `stream`); steps [s, s+n) in one persistent launch (asynchronous); state
+ * copies to host (then `stream` is synchronised); deadline wait and error
+ * word check; handle release.  Errors as the functions of ks_config. */
+ks_status ks_cda_workspace_size(const ks_cda_config* cfg, size_t* bytes);
+ks_status ks_cda_create(const ks_cda_config* cfg, void* dev_workspace, size_t ws_bytes, void* cuda_stream,
+                        ks_cda_ensemble** out);
+ks_status ks_cda_step_n(ks_cda_ensemble* e, uint32_t n_steps, void* cuda_stream);
+ks_status ks_cda_read_state(ks_cda_ensemble* e, const ks_cda_state_view* dst, void* cuda_stream);
+ks_status ks_cda_sync(ks_cda_ensemble* e, void* cuda_stream, uint32_t timeout_ms);
+ks_status ks_cda_destroy(ks_cda_ensemble* e);
+
 /* Library version, e.g. 0x000100 for 0.1.0. */
 uint32_t ks_version(void);
 

@@ -952,6 +952,12 @@ ks_status internal_launch_batched(ks_ensemble* e, uint32_t n_steps, const BatchA
 }
 
 int internal_device(const ks_ensemble* e) { return e ? e->device : -1; }
+
+// The initial state of a uniform ensemble described by p (for the CDA ensemble).
+cudaError_t internal_init_state(const DevParams& p, int grid, cudaStream_t st) {
+  init_kernel<<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
 }  // namespace ks
 
 extern "C" {

@@ -33,7 +33,8 @@ EXPORTS = ("ks_workspace_size", "ks_create_ensemble", "ks_step_n", "ks_read_stat
            "ks_bc_workspace_size",
            "ks_adam_step", "ks_mlp_export", "ks_paper_workspace_size", "ks_paper_create", "ks_paper_step_n",
            "ks_paper_step_n_naive", "ks_paper_read_state", "ks_paper_set_launch", "ks_paper_get_launch",
-           "ks_paper_sync", "ks_paper_destroy")
+           "ks_paper_sync", "ks_paper_destroy", "ks_cda_workspace_size", "ks_cda_create", "ks_cda_step_n",
+           "ks_cda_read_state", "ks_cda_sync", "ks_cda_destroy")
 KS_MLP_NPARAM = 8677
 
 KS_RECORD_WORDS = 22
@@ -113,6 +114,21 @@ class ks_paper_config(ctypes.Structure):
                 ("trace_markets", ctypes.c_uint32), ("trace_steps", ctypes.c_uint32), ("window", ctypes.c_int32)]
 
 
+class ks_cda_config(ctypes.Structure):
+    _fields_ = [("n_markets", ctypes.c_uint32), ("market_base", ctypes.c_uint32), ("L", ctypes.c_int32),
+                ("A", ctypes.c_int32), ("seed", ctypes.c_uint64), ("cancel_thresh_q32", ctypes.c_uint32),
+                ("mix_pct", ctypes.c_uint32 * 3), ("zi_offset", ctypes.c_int32), ("zi_qmax", ctypes.c_int32),
+                ("mom_lookback", ctypes.c_int32), ("mom_offset_max", ctypes.c_int32),
+                ("mr_offset_max", ctypes.c_int32), ("rb_qmax", ctypes.c_int32), ("trace_markets", ctypes.c_uint32),
+                ("trace_steps", ctypes.c_uint32)]
+
+
+class ks_cda_state_view(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "order", "inventory", "cash", "next", "last_tick", "history", "fundamental", "fills", "last_volume",
+        "traded_value", "sum_volume", "trace_hash", "step", "trace")]
+
+
 class ks_paper_state_view(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in (
         "bid", "ask", "last_tick", "mid2", "trades", "last_volume", "sum_price", "sum_volume", "trace_hash",
@@ -175,6 +191,12 @@ def load(build_if_missing: bool = True):
         "ks_paper_get_launch": ([vp, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)], ctypes.c_int),
         "ks_paper_sync": ([vp, vp, ctypes.c_uint32], ctypes.c_int),
         "ks_paper_destroy": ([vp], ctypes.c_int),
+        "ks_cda_workspace_size": ([P(ks_cda_config), P(ctypes.c_size_t)], ctypes.c_int),
+        "ks_cda_create": ([P(ks_cda_config), vp, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+        "ks_cda_step_n": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
+        "ks_cda_read_state": ([vp, P(ks_cda_state_view), vp], ctypes.c_int),
+        "ks_cda_sync": ([vp, vp, ctypes.c_uint32], ctypes.c_int),
+        "ks_cda_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -663,3 +685,87 @@ class PaperEnsemble:
             setattr(v, f, t.data_ptr() if t.numel() else None)
         _check(load().ks_paper_read_state(self.handle, ctypes.byref(v), _stream_ptr(stream)), "ks_paper_read_state")
         return {f: t.numpy().view(PAPER_STATE_FIELDS[f][0]).copy() for f, t in bufs.items()}
+
+
+# ---------------------------------------------------------------------------
+# Continuous double auction ensemble (ks_cda_*)
+# ---------------------------------------------------------------------------
+CDA_STATE_FIELDS = {
+    "order": (np.uint32, "agent"), "inventory": (np.int32, "agent"), "cash": (np.int64, "agent"),
+    "next": (np.int32, "agent"), "last_tick": (np.int32, "market"), "history": (np.int32, "hist"),
+    "fundamental": (np.int32, "market"), "fills": (np.int32, "market"), "last_volume": (np.int32, "market"),
+    "traded_value": (np.int64, "market"), "sum_volume": (np.int64, "market"), "trace_hash": (np.uint64, "market"),
+    "step": (np.uint64, "one"), "trace": (np.int32, "trace"),
+}
+
+
+def make_cda_config(w: dict, trace_markets: int = 0, trace_steps: int = 0) -> ks_cda_config:
+    """ks_cda_config from a workload dict with uniform L and A (see ``workloads``)."""
+    p = w["params"]
+    c = ks_cda_config()
+    c.n_markets, c.market_base, c.L, c.A = int(w["M"]), int(w.get("market_base", 0)), int(w["L"]), int(w["A"])
+    c.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
+    c.cancel_thresh_q32 = int(p["cancel_thresh_q32"])
+    for i in range(3):
+        c.mix_pct[i] = int(p["mix_pct"][i])
+    c.zi_offset, c.zi_qmax = int(p["zi_offset"]), int(p["zi_qmax"])
+    c.mom_lookback, c.mom_offset_max = int(p["mom_lookback"]), int(p["mom_offset_max"])
+    c.mr_offset_max, c.rb_qmax = int(p["mr_offset_max"]), int(p["rb_qmax"])
+    c.trace_markets, c.trace_steps = int(trace_markets), int(trace_steps) if trace_markets else 0
+    return c
+
+
+class CdaEnsemble:
+    """Markets of the continuous double auction on the current CUDA device; the
+    workspace is a torch uint8 tensor held by this object."""
+
+    def __init__(self, workload: dict, trace_markets: int = 0, trace_steps: int = 0, stream=None):
+        import torch
+        self.workload = workload
+        self.cfg = make_cda_config(workload, trace_markets, trace_steps)
+        self.M, self.L, self.A = int(workload["M"]), int(workload["L"]), int(workload["A"])
+        self.trace_markets = int(self.cfg.trace_markets)
+        self.trace_steps = int(self.cfg.trace_steps)
+        n = ctypes.c_size_t()
+        _check(load().ks_cda_workspace_size(ctypes.byref(self.cfg), ctypes.byref(n)), "ks_cda_workspace_size")
+        self.ws_bytes = n.value
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        _check(load().ks_cda_create(ctypes.byref(self.cfg), self.workspace.data_ptr(), self.ws_bytes,
+                                    _stream_ptr(stream), ctypes.byref(h)), "ks_cda_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ks_cda_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int, stream=None):
+        _check(load().ks_cda_step_n(self.handle, int(n), _stream_ptr(stream)), "ks_cda_step_n")
+
+    def sync(self, timeout_ms: int = 0, stream=None) -> int:
+        return int(load().ks_cda_sync(self.handle, _stream_ptr(stream), int(timeout_ms)))
+
+    def market_slice(self, m: int) -> slice:
+        return slice(m * self.A, (m + 1) * self.A)
+
+    def read_state(self, fields=None, stream=None) -> dict:
+        """Copy the state to host numpy arrays."""
+        fields = list(CDA_STATE_FIELDS) if fields is None else list(fields)
+        shapes = {"agent": (self.M * self.A,), "market": (self.M,), "hist": (self.M, KS_HISTORY), "one": (1,),
+                  "trace": (self.trace_markets, self.trace_steps, 2)}
+        v = ks_cda_state_view()
+        out = {}
+        for f in fields:
+            dt, per = CDA_STATE_FIELDS[f]
+            a = np.zeros(shapes[per], dt)
+            out[f] = a
+            setattr(v, f, a.ctypes.data if a.size else None)
+        _check(load().ks_cda_read_state(self.handle, ctypes.byref(v), _stream_ptr(stream)), "ks_cda_read_state")
+        return out

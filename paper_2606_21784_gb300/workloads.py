@@ -16,6 +16,11 @@ Five workloads, one per benchmark configuration of the method:
 ``mixed_32768``     32768 markets, L in {256..2048}, A log-uniform in
                     [128, 8192], S=10000, 25% MLP agents.
 
+The continuous double auction (``CdaEnsemble``; the paper names it as a market
+the same pattern extends to) with the configuration's agents:
+
+``cda_8192``        8192 markets, L=1024, A=1024, S=500, agents as ``plain_mix_8192``.
+
 The paper's own agent model (tick-aggregated book, NOISE / MOMENTUM / MAKER
 agents around the mid price, SplitMix64 draws; ``PaperEnsemble``) on the
 shapes of the paper's throughput tables (L=128, S=500):
@@ -63,6 +68,7 @@ WORKLOADS = {
     "learned_4096": dict(M=4096, L=512, A=2048, S=2000, params=dict(_MIX_CARRY, mlp_pct=100)),
     "mixed_32768": dict(M=32768, L=None, A=None, S=10000, params=dict(_MIX_CARRY, mlp_pct=25),
                         instance=dict(kind="mixed", seed=5)),
+    "cda_8192": dict(M=8192, L=1024, A=1024, S=500, params=_MIX_CARRY, model="cda"),
     "paper_8192_1024": dict(M=8192, L=128, A=1024, S=500, params=_PAPER_AGENTS, model="paper"),
     "paper_8192_256": dict(M=8192, L=128, A=256, S=500, params=_PAPER_AGENTS, model="paper"),
 }
