@@ -390,8 +390,55 @@ def compare_forms(ks, workloads, stream, plain_rate, cpu=True):
     if cpu:
         out["batched_20000"]["cpu_baseline"] = oracle_bucket_sample(w, L, A, S)
     out.update(learned_forms(ks, workloads, stream, cpu=cpu))
+    out["cda_8192"] = cda_form(ks, workloads, stream, cpu=cpu)
     out["paper_table_iii"] = paper_forms(ks, workloads, stream)
     out["paper_stylized_facts"] = stylized_facts()
+    return out
+
+
+def _oracle_cda_market(args):
+    params, m, L, A, S = args
+    import oracle as o
+    mk = o.cda_init(params, m, L, A)
+    t = time.perf_counter()
+    o.cda_run(params, mk, 0, S)
+    return time.perf_counter() - t
+
+
+def cda_form(ks, workloads, stream, cpu=True, reps=2):
+    """The continuous double auction over the configuration's agents (8192
+    markets x 1024 agents x 1024 ticks, S=500, one launch), and the oracle on
+    one market per host core."""
+    import multiprocessing as mp
+
+    import torch
+    w = workloads.workload("cda_8192")
+    S = int(w["S"])
+    ens = ks.CdaEnsemble(w)
+    ens.step(20, stream)
+    torch.cuda.synchronize()
+    best = _time_best(lambda: ens.step(S, stream), stream, reps)
+    if ens.sync(timeout_ms=600_000) != ks.KS_OK:
+        raise RuntimeError("CDA ensemble reported a device error")
+    st = ens.read_state(["fills"])
+    ev = float(w["M"]) * w["A"] * S
+    out = {"events_per_s": ev / (best / 1e3), "ms_per_run": best, "steps": S,
+           "fills_per_market_step": float(st["fills"].mean()) / (S * reps + 20)}
+    ens.close()
+    if cpu:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        tasks = [(w["params"], m, int(w["L"]), int(w["A"]), S) for m in range(cores)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_warm, range(cores))
+            t = time.perf_counter()
+            task_s = pool.map(_oracle_cda_market, tasks, chunksize=1)
+            dt = time.perf_counter() - t
+        cev = float(cores) * w["A"] * S
+        out["cpu_baseline"] = {"value": cev / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+                               "single_core_value": cev / max(sum(task_s), 1e-9),
+                               "sample": f"{cores} markets x {S} steps, one market per task"}
     return out
 
 
