@@ -658,6 +658,8 @@ def run_ours(args):
     w = sharding.shard(w, rank, world)
     if w.get("model") == "paper":
         return run_paper(args, w, rank, world, dev)
+    if w.get("model") == "cda":
+        return run_cda(args, w, rank, world, dev)
     S = int(w["S"])
     blob = trained_policy(2_000_000, 1)[0] if int(w["params"].get("mlp_pct", 0)) > 0 else None
     L_, A_ = workloads.sizes(w)
@@ -908,6 +910,63 @@ def run_paper(args, w, rank, world, dev):
                "gpu_launches": (2 * S if naive else 2) * args.steps, "roofline": roofline, "clocks": clocks,
                "paper_context": {"value": None if naive else PAPER_PEAK.get((int(w["M"]), int(w["A"]))),
                                  "hardware": "RTX 5090 (sm_120), Table III"}}
+        print(json.dumps(out), flush=True)
+    ens.close()
+    sharding.finalize()
+    return 0
+
+
+def run_cda(args, w, rank, world, dev):
+    """The continuous double auction as the main workload (``--workload
+    cda_8192``): same timing rules; the end-to-end leg reads the state back."""
+    import torch
+
+    from paper_2606_21784_gb300 import kineticsim as ks
+    from paper_2606_21784_gb300 import sharding
+    ens = ks.CdaEnsemble(w)
+    S = int(w["S"])
+    events_per_step = float(w["M"]) * w["A"] * S
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ens.step(S, stream)
+    torch.cuda.synchronize()
+    sharding.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    t0e = torch.cuda.Event(enable_timing=True)
+    t1e = torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for _ in range(args.steps):
+        ens.step(S, stream)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    sharding.barrier()
+    clocks = sampler.stop()
+    total_ms = sharding.max_over_ranks(t0e.elapsed_time(t1e), dev)
+    value = world * events_per_step * args.steps / (total_ms / 1e3)
+    if ens.sync(timeout_ms=600_000) != ks.KS_OK:
+        raise RuntimeError("CDA ensemble reported a device error")
+    fields = ["order", "inventory", "cash", "next", "last_tick", "fills", "sum_volume"]
+    ens.step(S, stream)
+    ens.read_state(fields, stream)
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(args.e2e_steps):
+        ens.step(S, stream)
+        st = ens.read_state(fields, stream)
+        nbytes = sum(a.nbytes for a in st.values())
+    e2e_s = sharding.max_over_ranks(time.perf_counter() - t0, dev)
+    if rank == 0:
+        out = {"metric": "agent_events_per_s", "value": value, "unit": "events/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+               "data": "synthetic",
+               "config": {"workload": args.workload, "M": int(w["M"]), "L": int(w["L"]), "A": int(w["A"]), "S": S,
+                          "model": "continuous double auction, the configuration's agents",
+                          "l2": "book resident on chip; state read and written once per launch"},
+               "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
+                       "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
+               "gpu_launches": 2 * args.steps, "roofline": None, "clocks": clocks}
         print(json.dumps(out), flush=True)
     ens.close()
     sharding.finalize()
