@@ -264,6 +264,28 @@ __device__ __forceinline__ uint32_t decide_tab(uint32_t slot, uint4 w, const Cla
   return (slot & W_STATIC) | qty | (sell31 >> 23) | ((uint32_t)tick << W_TICK_SHIFT);
 }
 
+// The same decision from eight rows indexed by (class, side coin), the coin
+// being bit 31 of w1: row 2c + coin holds {n, qmax, base, sgn} with the
+// side and the offset's sign already resolved, and sell[2c + coin] the side
+// bit of the order word.  Equal to decide_tab for every input.
+__device__ __forceinline__ void decision_row(uint4* rows, uint32_t* sell, int r, int last, int side_mom, int side_mr,
+                                             const RuleConsts& rc) {
+  const ClassRule cr = class_rule(r >> 1, last, side_mom, side_mr, rc);
+  const uint32_t coin = (uint32_t)(r & 1) << 31;
+  const int sgn = (coin & cr.sgn_mask) ? -1 : cr.sgn_fix;
+  rows[r] = make_uint4(cr.n, cr.qmax, (uint32_t)cr.base, (uint32_t)sgn);
+  sell[r] = ((coin & cr.coin_mask) | cr.forced_sell) ? W_SIDE : 0u;
+}
+
+__device__ __forceinline__ uint32_t decide_rows(uint32_t slot, uint4 w, const uint4* rows, const uint32_t* sell, int L) {
+  const uint32_t idx = ((slot >> (W_CLASS_SHIFT - 1)) & 6u) | (w.y >> 31);
+  const uint4 r = rows[idx];
+  const int o = (int)__umulhi(w.z, r.x);
+  const int tick = min(max((int)r.z + (int)r.w * o, 0), L - 1);
+  const uint32_t qty = 1u + __umulhi(w.w, r.y);
+  return (slot & W_STATIC) | qty | sell[idx] | ((uint32_t)tick << W_TICK_SHIFT);
+}
+
 // SplitMix64 finaliser (Sec. III-G) folding the per-step clearing trace.
 __device__ __forceinline__ uint64_t trace_mix(uint64_t h, uint32_t step, int32_t pstar, int32_t vol) {
   uint64_t z = h ^ (((uint64_t)(uint32_t)pstar << 32) | (uint64_t)(uint32_t)vol) ^

@@ -68,7 +68,8 @@ struct Smem {
   int32_t* rng;           // [2 parities][2]: lowest / highest tick holding a resting order after a step
   int32_t* feat;          // [8]: resting sell qty at last+1..+4, buy qty at last-1..-4 (policy inputs)
   int32_t* wR;            // [32] warp totals of policy rows
-  ClassRule* ctab;        // [4] rule constants per agent class for the next orders
+  uint4* drow;            // [8] decision rows per (agent class, side coin) for the next orders
+  uint32_t* dsell;        // [8] their side bits
   float* cvec;            // [64] layer-1 pre-activation shared by the market's agents (policy kernels)
   uint32_t* rowbuf;       // [NT * AK] policy rows: agent index, then the decision (policy kernels)
 };
@@ -82,7 +83,7 @@ __host__ __device__ inline size_t market_smem_layout(int nt, int ak, int Lmax, b
   o[2] = off; off += inv_col ? (size_t)4 * ak * nt : 0;  // inv
   o[3] = off; off += (size_t)4 * 2 * book_len(Lmax);     // book
   o[4] = off; off += (size_t)4 * 32 * 4 + 4 * 8;         // wD, wS, wMB, wMS, rem, rng
-  o[5] = off; off += (size_t)4 * 8 + 4 * 32 + 4 * sizeof(ClassRule);  // feat, wR, ctab
+  o[5] = off; off += (size_t)4 * 8 + 4 * 32 + 8 * 16 + 8 * 4;  // feat, wR, drow, dsell
   o[6] = off; off += mlp ? (size_t)4 * 64 : 0;           // cvec
   o[7] = off; off += mlp ? (size_t)4 * ak * nt : 0;      // rowbuf
   return (off + 15) & ~(size_t)15;
@@ -110,7 +111,8 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, int Lmax) {
   s.rng = s.wD + 132;
   s.feat = reinterpret_cast<int32_t*>(raw + o[5]);
   s.wR = s.feat + 8;
-  s.ctab = reinterpret_cast<ClassRule*>(s.wR + 32);
+  s.drow = reinterpret_cast<uint4*>(s.wR + 32);
+  s.dsell = reinterpret_cast<uint32_t*>(s.drow + 8);
   s.cvec = reinterpret_cast<float*>(raw + o[6]);
   s.rowbuf = reinterpret_cast<uint32_t*>(raw + o[7]);
   return s;
@@ -187,7 +189,8 @@ __device__ __forceinline__ void record_decision(const DevParams& P, const StepFe
 // instead of deciding, and rule decisions of recorded agents are appended.
 template <bool AGGR, bool MLP = false>
 __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, uint32_t x0, bool valid, const StepRules& sr,
-                                                uint32_t cthr, int L, const ClassRule* tab, uint32_t book_s,
+                                                uint32_t cthr, int L, const uint4* drow, const uint32_t* dsell,
+                                                uint32_t book_s,
                                                 const uint32_t* rk, bool* policy = nullptr,
                                                 const DevParams* P = nullptr, const StepFeat* f = nullptr,
                                                 int inv = 0) {
@@ -197,7 +200,7 @@ __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, uint32_t x0,
   red_add_if(book_s + 4u * w_bidx(sl), -(int)q, cancel);
   const bool empty = valid && (q == 0u || cancel);
   const bool dec = empty && !(sl & W_MLP);
-  const uint32_t ns = decide_tab(sl, w, tab, L);
+  const uint32_t ns = decide_rows(sl, w, drow, dsell, L);
   book_add<AGGR>(book_s, dec, ns);
   if constexpr (MLP) {
     *policy = empty && (sl & W_MLP);
@@ -740,7 +743,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
   const uint32_t gm = P.market_base + m;
   // rule constants of the first step's orders
   StepRules sr0 = step_rules(P, s0, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
-  if (t < 4) sm.ctab[t] = class_rule(t, last, sr0.side_mom, sr0.side_mr, rc);
+  if (t < 8) decision_row(sm.drow, sm.dsell, t, last, sr0.side_mom, sr0.side_mr, rc);
 
   // rebuild the aggregated resting book from the working orders
   for (int i = t; i < 2 * book_len(Lcap); i += NT) book[i] = 0;
@@ -790,11 +793,11 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
       const uint32_t x0 = FIT ? sr.sk.c0 ^ (uint32_t)(a0 + k) : x0a ^ (uint32_t)k;
       if constexpr (MLP) {
         bool pol = false;
-        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk, &pol,
+        slot[k] = order_agent<AGGR, true>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk, &pol,
                                           &P, &sf, sm.inv[k * NT + t]);
         pflags |= pol ? (1u << k) : 0u;
       } else {
-        slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.ctab, book_s, P.rk);
+        slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk);
       }
     }
     if constexpr (MLP) {
@@ -900,7 +903,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     }
     const bool more = j + 1 < n_steps;
     const StepRules sr = step_rules(P, s + 1, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
-    if (t < 4) sm.ctab[t] = class_rule(t, last, sr.side_mom, sr.side_mr, rc);
+    if (t < 8) decision_row(sm.drow, sm.dsell, t, last, sr.side_mom, sr.side_mr, rc);
     gsync<NT>(bar);  // B5: book residual, remainders, marginal totals and rule constants visible
 
     // ---- fills of step s, fused with the orders of step s+1 ------------------------------
@@ -962,11 +965,11 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
           const bool valid = a0 + k < A && (!FIT || k < akeff);
           if constexpr (MLP) {
             bool pol = false;
-            sl[i] = order_agent<AGGR, true>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.ctab, book_s, P.rk, &pol, &P,
+            sl[i] = order_agent<AGGR, true>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk, &pol, &P,
                                             &sf, sm.inv[k * NT + t]);
             pflags |= pol ? (1u << k) : 0u;
           } else {
-            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.ctab, book_s, P.rk);
+            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk);
           }
         }
       }
