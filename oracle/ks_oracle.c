@@ -516,6 +516,13 @@ static void ko_decide_rule(const ko_params* P, int32_t L, int32_t atype,
   *qty = 1 + (int32_t)ko_range(w[3], P->rb_qmax);
 }
 
+/* The rule decision of an agent of class atype from its draw words w in a
+ * market with scalars ms (test entry point): out = (side, tick, qty). */
+void ko_rule_decision(const ko_params* P, int32_t L, int32_t atype, const ko_market_scalars* ms, const uint32_t w[4],
+                      int32_t* out) {
+  ko_decide_rule(P, L, atype, ms, w, &out[0], &out[1], &out[2]);
+}
+
 /* Optional replay of externally supplied decisions for MLP agents (used to
  * re-run the clearing on orders emitted by another engine).  For step j of
  * the call and agent a, entry j*A + a holds side (0 buy, 1 sell, 2 pass),

@@ -175,6 +175,9 @@ def _load():
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        P(ctypes.c_int64), P(_Replay)]
             lib.ko_cda_run.restype = ctypes.c_int
+            lib.ko_rule_decision.argtypes = [P(Params), ctypes.c_int32, ctypes.c_int32, P(MarketScalars),
+                                             P(ctypes.c_uint32), P(ctypes.c_int32)]
+            lib.ko_rule_decision.restype = None
             _lib = lib
     return _lib
 
@@ -558,3 +561,19 @@ def cda_next(mk: Market) -> np.ndarray:
         for x, y in zip(ags, ags[1:]):
             nxt[x] = y
     return nxt
+
+
+def rule_decision(params: dict, L: int, atype: int, last: int, hist, fund: int, words):
+    """(side, tick, qty) of a rule agent of class ``atype`` with draw words ``words``
+    in a market whose last clearing tick, history (newest first) and fundamental
+    are given."""
+    P = make_params(params)
+    ms = MarketScalars()
+    ms.last = int(last)
+    for j in range(HIST):
+        ms.hist[j] = int(hist[j])
+    ms.fund = int(fund)
+    w = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in words])
+    out = (ctypes.c_int32 * 3)()
+    _load().ko_rule_decision(ctypes.byref(P), int(L), int(atype), ctypes.byref(ms), w, out)
+    return int(out[0]), int(out[1]), int(out[2])

@@ -52,6 +52,20 @@ MUTANTS = {
                              "w[i] -= lr * (m[i] / c1) / sqrt(v[i] / c2 + eps);"),
     "adam_b1_in_second_moment": ("v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];",
                                  "v[i] = b1 * v[i] + (1.0 - b1) * g[i] * g[i];"),
+    # the rule decisions
+    "rule_coin_reversed": ("int32_t coin = (w[1] >> 31) ? 1 : 0;", "int32_t coin = (w[1] >> 31) ? 0 : 1;"),
+    "rule_zi_range_short": ("int64_t off = ko_range(w[2], 2 * (int64_t)P->zi_offset + 1) - P->zi_offset;",
+                            "int64_t off = ko_range(w[2], 2 * (int64_t)P->zi_offset) - P->zi_offset;"),
+    "rule_momentum_lag": ("int32_t ret = ms->hist[0] - ms->hist[P->mom_lookback];",
+                          "int32_t ret = ms->hist[0] - ms->hist[P->mom_lookback - 1];"),
+    "rule_reversion_away": ("s = last < ms->fund ? 0 : (last > ms->fund ? 1 : coin);",
+                            "s = last < ms->fund ? 1 : (last > ms->fund ? 0 : coin);"),
+    "rule_through_price_sign": ("*tick = ko_clamp((int64_t)last + (s == 0 ? off : -off), 0, L - 1);",
+                                "*tick = ko_clamp((int64_t)last + (s == 0 ? -off : off), 0, L - 1);"),
+    "rule_qty_uses_zi_qmax": ("*qty = 1 + (int32_t)ko_range(w[3], P->rb_qmax);",
+                              "*qty = 1 + (int32_t)ko_range(w[3], P->zi_qmax);"),
+    "init_class_threshold": ("if (pct < P->mix_pct[0]) ag->atype[a] = KO_ZI;", "if (pct <= P->mix_pct[0]) ag->atype[a] = KO_ZI;"),
+    "init_fundamental_stream": ("ko_draw(P->seed, 0u, 0u, m, 2u, w);", "ko_draw(P->seed, 0u, 0u, m, 1u, w);"),
     # the continuous double auction
     "cda_lifo": ("if (better || (t == tb && stamp[b] < stamp[best])) best = b;",
                  "if (better || (t == tb && stamp[b] > stamp[best])) best = b;"),
@@ -103,6 +117,7 @@ def test_pins_catch_mutant(name):
                             os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                             os.path.join(ROOT, "tests", "test_oracle_mlp_pins.py"),
                             os.path.join(ROOT, "tests", "test_oracle_paper_pins.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_cda_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_cda_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_rule_pins.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
