@@ -23,7 +23,10 @@ MUTANTS = {
     "buyer_cash_sign": ("ag->cash[a] -= (int64_t)cr.pstar * f;", "ag->cash[a] += (int64_t)cr.pstar * f;"),
     "philox_operand": ("KO_PHILOX_MUL_B * (uint64_t)x2", "KO_PHILOX_MUL_B * (uint64_t)x1"),
     "philox_key_schedule": ("k1 += KO_PHILOX_WEYL_B;", "k1 += KO_PHILOX_WEYL_A;"),
-    "history_not_shifted": ("ms->hist[0] = ms->last;", "ms->hist[0] = ms->hist[1];"),
+    "history_not_shifted": ("ms->hist[0] = ms->last;\n    ms->last_v = (int32_t)cr.vstar;",
+                            "ms->hist[0] = ms->hist[1];\n    ms->last_v = (int32_t)cr.vstar;"),
+    "cda_history_not_shifted": ("ms->hist[0] = ms->last;\n    ms->last_v = (int32_t)vol;",
+                                "ms->hist[0] = ms->hist[1];\n    ms->last_v = (int32_t)vol;"),
     "marginal_buy_strict": ("if (dcum[p] >= vmax) res->p_buy = p;", "if (dcum[p] > vmax) res->p_buy = p;"),
     "mixer_shift": ("z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;", "z = (z ^ (z >> 28)) * 0x94d049bb133111ebull;"),
     "agent_priority_reversed": ("for (int32_t a = 0; a < A; ++a) {\n    if (qty[a] <= 0) continue;\n    order[",
