@@ -1,16 +1,20 @@
 // ks_cda.cu -- continuous double auction over the main model's agents (see
 // kineticsim.h, ks_cda_*): one warp per market, the book in shared memory.
 //
-// The book of a market is a FIFO of resting agents per (side, tick) --
-// doubly linked through per-agent next / previous indices -- plus one bitmap
-// of nonempty ticks per side, so the best bid and ask are found with a few
-// word scans.  Per step the warp's lanes draw the Philox blocks, cancel and
-// decide for 32 agents at a time (the per-step cost that the call auction
-// also has); lane 0 then removes the cancelled orders and matches the new
-// orders one by one in agent order, which continuous trading makes
-// sequential.  Only the next indices of the FIFOs persist in global memory;
-// heads, tails, previous indices and bitmaps are rebuilt when a market is
-// loaded.
+// The book of a market is a FIFO of resting agents per (side, tick), singly
+// linked through per-agent next indices with a head and a tail per (side,
+// tick), plus one bitmap of nonempty ticks per side, so the best bid and ask
+// are found with a few word scans.  Per step the warp's lanes draw the Philox
+// blocks, cancel and decide for 32 agents at a time (the per-step cost that
+// the call auction also has); lane 0 then removes the cancelled orders and
+// matches the new orders one by one in agent order, which continuous trading
+// makes sequential.  The serial matching waits on shared-memory latency, so a
+// market keeps only 6 bytes per agent and 8 per tick on chip and many markets
+// share an SM: lane 0 adds every fill to the inventory and cash in global
+// memory with reductions (no kernel reads them back), and an agent that
+// cancels draws its new order again after the cancellations instead of
+// keeping it.  Only the next indices persist in global memory; heads, tails
+// and bitmaps are rebuilt when a market is loaded.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -52,16 +56,12 @@ struct CdaParams {
 
 // Shared memory of one market (one warp), 16-byte aligned regions.
 struct CdaSmem {
-  uint32_t* ord;   // [A] order words
-  uint32_t* inc;   // [A] the step's new order words
-  int32_t* inv;    // [A]
-  int64_t* cash;   // [A]
-  int16_t* nxt;    // [A] next agent in the FIFO, -1 at the tail
-  int16_t* prv;    // [A] previous agent, -1 at the head
+  uint32_t* ord;   // [A] order words; a deciding agent's new order until it is matched
+  int16_t* nxt;    // [A] next agent in the FIFO; -1 at the tail and without a resting order
   int16_t* head;   // [2][L] first agent per (side, tick), -1 if empty
-  int16_t* tail;   // [2][L]
+  int16_t* tail;   // [2][L] last agent per (side, tick)
   uint32_t* bits;  // [2][NW] nonempty ticks per side
-  uint32_t* cbits; // [ceil(A / 32)] cancelled this step
+  uint32_t* cbits; // [ceil(A / 32)] cancelled this step (while loading: agents with a predecessor)
   uint32_t* dbits; // [ceil(A / 32)] deciding this step
   ClassRule* ctab; // [4]
 };
@@ -71,38 +71,30 @@ __host__ __device__ inline int cda_words(int L) { return (L + 31) / 32; }
 
 __host__ __device__ inline size_t cda_smem_layout(int A, int L, size_t* o) {
   size_t off = 0;
-  const size_t a = (size_t)(A > 0 ? A : 1);
+  const size_t a = (size_t)(A > 0 ? A : 1), nwa = (a + 31) / 32;
   o[0] = off; off = al16(off + 4 * a);                               // ord
-  o[1] = off; off = al16(off + 4 * a);                               // inc
-  o[2] = off; off = al16(off + 4 * a);                               // inv
-  o[3] = off; off = al16(off + 8 * a);                               // cash
-  o[4] = off; off = al16(off + 2 * a);                               // nxt
-  o[5] = off; off = al16(off + 2 * a);                               // prv
-  o[6] = off; off = al16(off + 2 * 2 * (size_t)L);                   // head
-  o[7] = off; off = al16(off + 2 * 2 * (size_t)L);                   // tail
-  o[8] = off; off = al16(off + 4 * 2 * (size_t)cda_words(L));        // bits
-  o[9] = off; off = al16(off + 4 * ((a + 31) / 32));                 // cbits
-  o[10] = off; off = al16(off + 4 * ((a + 31) / 32));                // dbits
-  o[11] = off; off = al16(off + 4 * sizeof(ClassRule));              // ctab
+  o[1] = off; off = al16(off + 2 * a);                               // nxt
+  o[2] = off; off = al16(off + 2 * 2 * (size_t)L);                   // head
+  o[3] = off; off = al16(off + 2 * 2 * (size_t)L);                   // tail
+  o[4] = off; off = al16(off + 4 * 2 * (size_t)cda_words(L));        // bits
+  o[5] = off; off = al16(off + 4 * nwa);                             // cbits
+  o[6] = off; off = al16(off + 4 * nwa);                             // dbits
+  o[7] = off; off = al16(off + 4 * sizeof(ClassRule));               // ctab
   return off;
 }
 
 __device__ inline CdaSmem cda_carve(unsigned char* raw, int A, int L) {
-  size_t o[12];
+  size_t o[8];
   cda_smem_layout(A, L, o);
   CdaSmem s;
   s.ord = reinterpret_cast<uint32_t*>(raw + o[0]);
-  s.inc = reinterpret_cast<uint32_t*>(raw + o[1]);
-  s.inv = reinterpret_cast<int32_t*>(raw + o[2]);
-  s.cash = reinterpret_cast<int64_t*>(raw + o[3]);
-  s.nxt = reinterpret_cast<int16_t*>(raw + o[4]);
-  s.prv = reinterpret_cast<int16_t*>(raw + o[5]);
-  s.head = reinterpret_cast<int16_t*>(raw + o[6]);
-  s.tail = reinterpret_cast<int16_t*>(raw + o[7]);
-  s.bits = reinterpret_cast<uint32_t*>(raw + o[8]);
-  s.cbits = reinterpret_cast<uint32_t*>(raw + o[9]);
-  s.dbits = reinterpret_cast<uint32_t*>(raw + o[10]);
-  s.ctab = reinterpret_cast<ClassRule*>(raw + o[11]);
+  s.nxt = reinterpret_cast<int16_t*>(raw + o[1]);
+  s.head = reinterpret_cast<int16_t*>(raw + o[2]);
+  s.tail = reinterpret_cast<int16_t*>(raw + o[3]);
+  s.bits = reinterpret_cast<uint32_t*>(raw + o[4]);
+  s.cbits = reinterpret_cast<uint32_t*>(raw + o[5]);
+  s.dbits = reinterpret_cast<uint32_t*>(raw + o[6]);
+  s.ctab = reinterpret_cast<ClassRule*>(raw + o[7]);
   return s;
 }
 
@@ -138,27 +130,56 @@ struct CdaBest {
   int bid, ask;
 };
 
-// Removes agent a (resting at `side`, `tick`) from its FIFO.
-__device__ inline void cda_unlink(const CdaSmem& sm, int L, int NW, int a, int side, int tick, CdaBest& best) {
-  const int p = sm.prv[a], n = sm.nxt[a];
+// The FIFO of (side, tick) has become empty: clear its bit and move the side's
+// best price past it.
+__device__ inline void cda_emptied(const CdaSmem& sm, int L, int NW, int side, int tick, CdaBest& best) {
+  uint32_t* b = sm.bits + side * NW;
+  b[tick >> 5] &= ~(1u << (tick & 31));
+  if (side == 0 && tick == best.bid) best.bid = cda_scan_down(b, tick - 1);
+  if (side == 1 && tick == best.ask) best.ask = cda_scan_up(b, NW, tick + 1, L);
+}
+
+// Removes agent r, the first of the FIFO of (side, tick).
+__device__ inline void cda_pop(const CdaSmem& sm, int L, int NW, int r, int side, int tick, CdaBest& best) {
   const int key = side * L + tick;
-  if (p >= 0) sm.nxt[p] = (int16_t)n; else sm.head[key] = (int16_t)n;
-  if (n >= 0) sm.prv[n] = (int16_t)p; else sm.tail[key] = (int16_t)p;
-  sm.nxt[a] = -1;
-  sm.prv[a] = -1;
-  if (sm.head[key] < 0) {
-    uint32_t* b = sm.bits + side * NW;
-    b[tick >> 5] &= ~(1u << (tick & 31));
-    if (side == 0 && tick == best.bid) best.bid = cda_scan_down(b, tick - 1);
-    if (side == 1 && tick == best.ask) best.ask = cda_scan_up(b, NW, tick + 1, L);
+  const int n = sm.nxt[r];
+  sm.head[key] = (int16_t)n;
+  sm.nxt[r] = -1;
+  if (n < 0) {
+    sm.tail[key] = -1;
+    cda_emptied(sm, L, NW, side, tick, best);
   }
+}
+
+// Removes agent a from anywhere in the FIFO of (side, tick); its predecessor
+// is found by walking from the head (at most A links).  False when a is not
+// in that FIFO.
+__device__ inline bool cda_remove(const CdaSmem& sm, int L, int NW, int A, int a, int side, int tick,
+                                  CdaBest& best) {
+  const int key = side * L + tick;
+  int p = sm.head[key];
+  if (p == a) {
+    cda_pop(sm, L, NW, a, side, tick, best);
+    return true;
+  }
+  for (int guard = 0; p >= 0 && guard < A; ++guard) {
+    const int n = sm.nxt[p];
+    if (n == a) {
+      const int an = sm.nxt[a];
+      sm.nxt[p] = (int16_t)an;
+      if (an < 0) sm.tail[key] = (int16_t)p;
+      sm.nxt[a] = -1;
+      return true;
+    }
+    p = n;
+  }
+  return false;
 }
 
 // Appends agent a at the tail of the FIFO of (side, tick).
 __device__ inline void cda_append(const CdaSmem& sm, int L, int NW, int a, int side, int tick, CdaBest& best) {
   const int key = side * L + tick;
   const int t = sm.tail[key];
-  sm.prv[a] = (int16_t)t;
   sm.nxt[a] = -1;
   if (t >= 0) sm.nxt[t] = (int16_t)a; else sm.head[key] = (int16_t)a;
   sm.tail[key] = (int16_t)a;
@@ -170,22 +191,24 @@ __device__ inline void cda_append(const CdaSmem& sm, int L, int NW, int a, int s
 // Steps [s0, s0 + n) of market m by one warp.
 __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t n, const CdaSmem& sm, int lane) {
   const int L = P.L, A = P.A, NW = cda_words(L);
+  const int nwa = (A + 31) / 32;
   const int64_t aoff = (int64_t)m * A;
   const uint32_t gm = P.market_base + m;
   // ---- load and rebuild the book ---------------------------------------------------------
   for (int a = lane; a < A; a += 32) {
-    sm.ord[a] = P.ord[aoff + a];
-    sm.inv[a] = P.inv[aoff + a];
-    sm.cash[a] = P.cash[aoff + a];
+    const uint32_t o = P.ord[aoff + a];
     const int nx = P.nxt[aoff + a];
-    sm.nxt[a] = (int16_t)(nx >= 0 && nx < A ? nx : -1);
-    sm.prv[a] = -1;
+    sm.ord[a] = o;
+    sm.nxt[a] = (int16_t)(w_qty(o) != 0u && nx >= 0 && nx < A ? nx : -1);
   }
   for (int i = lane; i < 2 * L; i += 32) sm.head[i] = sm.tail[i] = -1;
   for (int i = lane; i < 2 * NW; i += 32) sm.bits[i] = 0u;
+  for (int i = lane; i < nwa; i += 32) sm.cbits[i] = 0u;
   __syncwarp();
-  for (int a = lane; a < A; a += 32)
-    if (w_qty(sm.ord[a]) != 0u && sm.nxt[a] >= 0) sm.prv[sm.nxt[a]] = (int16_t)a;
+  for (int a = lane; a < A; a += 32) {
+    const int nx = sm.nxt[a];
+    if (nx >= 0) atomicOr(&sm.cbits[nx >> 5], 1u << (nx & 31));  // nx has a predecessor
+  }
   __syncwarp();
   for (int a = lane; a < A; a += 32) {
     const uint32_t o = sm.ord[a];
@@ -195,7 +218,7 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
       atomicOr(P.err, ERR_TICK);
       continue;
     }
-    if (sm.prv[a] < 0) sm.head[side * L + tick] = (int16_t)a;
+    if (!((sm.cbits[a >> 5] >> (a & 31)) & 1u)) sm.head[side * L + tick] = (int16_t)a;
     if (sm.nxt[a] < 0) sm.tail[side * L + tick] = (int16_t)a;
     atomicOr(&sm.bits[side * NW + (tick >> 5)], 1u << (tick & 31));
   }
@@ -218,7 +241,8 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
     best.ask = cda_scan_up(sm.bits + NW, NW, 0, L);
   }
   const bool traced = m < P.trace_markets;
-  const int nwa = (A + 31) / 32;
+  int32_t* const ginv = P.inv + aoff;
+  unsigned long long* const gcash = reinterpret_cast<unsigned long long*>(P.cash + aoff);
 
   for (uint32_t j = 0; j < n; ++j) {
     const uint32_t s = s0 + j;
@@ -239,38 +263,53 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
       const uint4 w = step_draw_x0(sk, sk.c0 ^ (uint32_t)a, P.rk);
       const uint32_t q = w_qty(sl);
       const bool cancel = valid && q != 0u && w.x < P.cancel_thr;
-      const bool dec = valid && (q == 0u || cancel);
-      if (dec) sm.inc[a] = decide_tab(sl, w, sm.ctab, L);
+      if (valid && q == 0u) sm.ord[a] = decide_tab(sl, w, sm.ctab, L);  // no resting order: decide in place
       const uint32_t cb = __ballot_sync(0xffffffffu, cancel);
-      const uint32_t db = __ballot_sync(0xffffffffu, dec);
+      const uint32_t db = __ballot_sync(0xffffffffu, valid && (q == 0u || cancel));
       if (lane == 0) {
         sm.cbits[wi] = cb;
         sm.dbits[wi] = db;
       }
     }
     __syncwarp();
-    // ---- lane 0: cancellations, then the arrivals in agent order -------------------------
-    int last_fill = -1;
-    int vol = 0;
+    // ---- lane 0: the cancellations -----------------------------------------------------------
     if (lane == 0) {
       for (int wi = 0; wi < nwa; ++wi) {
         for (uint32_t b = sm.cbits[wi]; b; b &= b - 1u) {
           const int a = wi * 32 + __ffs(b) - 1;
           const uint32_t o = sm.ord[a];
-          cda_unlink(sm, L, NW, a, (int)w_sell(o), (int)w_tick(o), best);
+          if (!cda_remove(sm, L, NW, A, a, (int)w_sell(o), (int)w_tick(o), best)) atomicOr(P.err, ERR_SHAPE);
           sm.ord[a] = o & W_STATIC;
         }
       }
+    }
+    __syncwarp();
+    // ---- the new orders of the agents that cancelled: the same draws again -------------------
+    for (int wi = 0; wi < nwa; ++wi) {
+      const uint32_t cb = sm.cbits[wi];  // the same word for every lane
+      if (cb == 0u) continue;
+      const int a = wi * 32 + lane;
+      const uint4 w = step_draw_x0(sk, sk.c0 ^ (uint32_t)a, P.rk);
+      if ((cb >> lane) & 1u) sm.ord[a] = decide_tab(sm.ord[a], w, sm.ctab, L);
+    }
+    __syncwarp();
+    // ---- lane 0: the arrivals in agent order ---------------------------------------------------
+    int last_fill = -1;
+    int vol = 0;
+    if (lane == 0) {
       for (int wi = 0; wi < nwa; ++wi) {
         for (uint32_t b = sm.dbits[wi]; b; b &= b - 1u) {
           const int a = wi * 32 + __ffs(b) - 1;
-          const uint32_t o = sm.inc[a];
+          const uint32_t o = sm.ord[a];
           int q = (int)w_qty(o);
           const int sd = (int)w_sell(o), tk = (int)w_tick(o);
+          const int sgn = sd == 0 ? 1 : -1;  // the arriving agent buys (+) or sells (-)
+          const int okey = (1 - sd) * L;
+          int dq = 0, dv = 0;  // the arriving order's filled quantity and traded value
           while (q > 0) {
             const int px = sd == 0 ? best.ask : best.bid;
             if (px < 0 || (sd == 0 ? px > tk : px < tk)) break;  // the limit no longer crosses
-            const int r = sm.head[(1 - sd) * L + px];
+            const int r = sm.head[okey + px];
             if (r < 0) {  // bitmap and FIFO disagree: record it and stop matching this order
               atomicOr(P.err, ERR_SHAPE);
               break;
@@ -279,26 +318,29 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
             const int rq = (int)w_qty(ro);
             if (rq == 0) {  // an empty order in a FIFO: record it, drop it (the loop still ends)
               atomicOr(P.err, ERR_SHAPE);
-              cda_unlink(sm, L, NW, r, 1 - sd, px, best);
+              cda_pop(sm, L, NW, r, 1 - sd, px, best);
               continue;
             }
             const int f = min(q, rq);
-            const int sgn = sd == 0 ? 1 : -1;  // the arriving agent buys (+) or sells (-)
-            sm.inv[a] += sgn * f;
-            sm.cash[a] -= (int64_t)sgn * px * f;
-            sm.inv[r] -= sgn * f;
-            sm.cash[r] += (int64_t)sgn * px * f;
+            atomicAdd(ginv + r, -sgn * f);
+            atomicAdd(gcash + r, (unsigned long long)(long long)(sgn * px * f));
+            dq += f;
+            dv += px * f;
             q -= f;
-            vol += f;
             last_fill = px;
             fills += 1;
-            value += (int64_t)px * f;
             if (f == rq) {
-              cda_unlink(sm, L, NW, r, 1 - sd, px, best);
+              cda_pop(sm, L, NW, r, 1 - sd, px, best);
               sm.ord[r] = ro & W_STATIC;
             } else {
               sm.ord[r] = ro - (uint32_t)f;
             }
+          }
+          if (dq) {
+            atomicAdd(ginv + a, sgn * dq);
+            atomicAdd(gcash + a, (unsigned long long)(-(long long)sgn * dv));
+            vol += dq;
+            value += dv;
           }
           if (q > 0) {
             sm.ord[a] = (o & ~W_QTY) | (uint32_t)q;
@@ -328,11 +370,9 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
     }
     __syncwarp();
   }
-  // ---- store ----------------------------------------------------------------------------------
+  // ---- store (the accounts are already in global memory) ----------------------------------------
   for (int a = lane; a < A; a += 32) {
     P.ord[aoff + a] = sm.ord[a];
-    P.inv[aoff + a] = sm.inv[a];
-    P.cash[aoff + a] = sm.cash[a];
     P.nxt[aoff + a] = sm.nxt[a];
   }
   if (lane == 0) {
@@ -351,7 +391,7 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
 }
 
 // Persistent: warp w of CTA b runs markets b * WPB + w, + grid * WPB, ...
-__global__ void __launch_bounds__(256) cda_kernel(CdaParams P, uint32_t n_steps, uint32_t stride) {
+__global__ void __launch_bounds__(1024) cda_kernel(CdaParams P, uint32_t n_steps, uint32_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
   const int wpb = (int)blockDim.x >> 5;
@@ -481,15 +521,27 @@ ks_status ks_cda_create(const ks_cda_config* cfg, void* dev_workspace, size_t ws
     delete e;
     return ccuda(ce, "device query");
   }
-  size_t o[12];
+  int smem_sm = 0;
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, e->device);
+  if (ce != cudaSuccess) {
+    delete e;
+    return ccuda(ce, "device query");
+  }
+  size_t o[8];
   const size_t per = cda_smem_layout(cfg->A, cfg->L, o);
   e->stride = (uint32_t)per;
-  // markets (warps) per CTA: as many as the shared memory holds, up to 8
-  e->wpb = (int)std::min<size_t>(8, (size_t)max_optin / per);
-  if (e->wpb < 1) {
+  // One CTA per SM holds as many books (warps) as the shared memory fits, up to
+  // 32; of those, as few as keep the number of rounds over the markets.
+  const size_t room = std::min<size_t>((size_t)max_optin, smem_sm > 1024 ? (size_t)smem_sm - 1024 : 0);
+  const int fit = (int)std::min<size_t>(32, room / per);
+  if (fit < 1) {
     delete e;
     return cfail(KS_ERR_UNSUPPORTED, "one market's book does not fit the shared memory of a CTA");
   }
+  const int64_t per_round = (int64_t)fit * e->num_sms;
+  const int64_t rounds = ((int64_t)cfg->n_markets + per_round - 1) / per_round;
+  const int64_t need = ((int64_t)cfg->n_markets + rounds * e->num_sms - 1) / (rounds * e->num_sms);
+  e->wpb = (int)std::max<int64_t>(1, std::min<int64_t>(fit, need));
   e->smem = (size_t)e->wpb * per;
   ce = cudaFuncSetAttribute(cda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
   int occ = 0;

@@ -61,7 +61,7 @@ def test_every_market_and_step_matches_the_oracle(L, A):
     assert total > 0
 
 
-@pytest.mark.parametrize("L,A", [(2, 1), (2, 40), (1000, 31), (4096, 2000), (128, 0), (300, 8192)])
+@pytest.mark.parametrize("L,A", [(2, 1), (2, 40), (1000, 31), (4096, 2000), (128, 0), (300, 8192), (4096, 8192)])
 def test_edge_shapes(L, A):
     w = wl.workload("cda_8192", M=3, L=L, A=A)
     steps = 60
@@ -70,6 +70,30 @@ def test_edge_shapes(L, A):
         mk = o.cda_init(w["params"], m, L, A)
         tp, tv, _ = o.cda_run(w["params"], mk, 0, steps)
         _compare(gs, ens, m, mk, tp, tv)
+
+
+@pytest.mark.parametrize("thr", [0, 0x40000000, 0xC0000000, 0xFFFFFFFF])
+def test_cancellation_rates(thr):
+    """From no cancellations to every working order cancelled each step: orders
+    leave their FIFOs from the head, the middle and the tail."""
+    w = wl.workload("cda_8192", M=6, L=128, A=500, cancel_thresh_q32=thr)
+    steps = 80
+    ens, gs = _run(w, steps)
+    for m in range(w["M"]):
+        mk = o.cda_init(w["params"], m, 128, 500)
+        tp, tv, _ = o.cda_run(w["params"], mk, 0, steps)
+        _compare(gs, ens, m, mk, tp, tv)
+
+
+def test_many_markets_per_cta():
+    """Enough markets that each CTA holds several books (one warp each)."""
+    w = wl.workload("cda_8192", M=1000, L=64, A=100)
+    steps = 40
+    ens, gs = _run(w, steps, trace=False)
+    for m in range(w["M"]):
+        mk = o.cda_init(w["params"], m, 64, 100)
+        o.cda_run(w["params"], mk, 0, steps)
+        _compare(gs, ens, m, mk)
 
 
 def test_split_calls_keep_time_priority():
