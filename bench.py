@@ -966,11 +966,29 @@ def run_cda(args, w, rank, world, dev):
                           "l2": "book resident on chip; state read and written once per launch"},
                "e2e": {"value": world * events_per_step * args.e2e_steps / e2e_s, "unit": "events/s",
                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes},
-               "gpu_launches": 2 * args.steps, "roofline": None, "clocks": clocks}
+               "gpu_launches": 2 * args.steps, "roofline": cda_roofline(events_per_step, total_ms / args.steps),
+               "clocks": clocks}
         print(json.dumps(out), flush=True)
     ens.close()
     sharding.finalize()
     return 0
+
+
+def cda_roofline(events_per_launch, launch_ms):
+    """The CDA kernel against the ALU roof of its draws: one Philox block (20
+    wide products) per agent-event, the peak derived as for the plain line at
+    the nominal 32 products/clk/SM.  The fraction is small by construction:
+    the kernel waits on the dependent shared-memory accesses of the serial
+    matching (one lane per market), not on a pipe."""
+    achieved = PHILOX_MULW_PER_EVENT * events_per_launch / (launch_ms / 1e3) / 1e12
+    peak = SM_COUNT_NOMINAL * 32 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tproducts/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "cda_kernel", "launch_ms": launch_ms,
+            "algorithmic": f"{PHILOX_MULW_PER_EVENT} 32x32->64 products per agent-event x "
+                           f"{events_per_launch:.4g} agent-events per launch",
+            "peak_source": f"derived: {SM_COUNT_NOMINAL} SMs x 32 products/clk/SM x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
+            "note": "latency-bound: the matching is a chain of dependent shared-memory accesses on one lane per "
+                    "market; issue slots 55% busy in the ncu capture"}
 
 
 def main():

@@ -3,7 +3,7 @@
 1. ``generate``: runs the rule-based 8192-market configuration (L=1024,
    A=4096, 60/20/20 agent mix, carried book) with seed 7 on the GPU and
    records the new orders of the first ``record_agents`` agents of every
-   market (features and action) until ``n_pairs`` records are collected.
+   market (features and action), in a canonical order, ``n_pairs`` of them.
 2. ``train``: minibatch Adam on the records with the library's hand-written
    forward/backward kernels (``ks_bc_grad``, ``ks_adam_step``).
 3. ``evaluate`` / ``action_match``: held-out loss, and agreement of the
@@ -25,24 +25,52 @@ from . import workloads
 DECISIONS_PER_AGENT_STEP = 0.25  # lower bound of the rule agents' order rate (measured ~0.29)
 
 
+def canonical_order(records):
+    """The records sorted lexicographically by their words (first word most
+    significant): one order for one multiset of records, whatever order the
+    kernels appended them in."""
+    import torch
+    idx = torch.arange(records.shape[0], device=records.device)
+    for j in reversed(range(records.shape[1])):
+        _, o = torch.sort(records[idx, j], stable=True)
+        idx = idx[o]
+    return records[idx].contiguous()
+
+
 def generate(n_pairs: int = 20_000_000, seed: int = 7, record_agents: int = 64, steps: int = 2000,
              markets: int | None = None):
-    """Records of rule decisions (device int32 [n, 22]) and the workload used."""
+    """Records of rule decisions (device int32 [n, 22]) and the workload used.
+
+    The kernels append records in completion order, so the run keeps every
+    record (a second run with the exact capacity when the first fills up),
+    puts them in canonical order and, when there are more than ``n_pairs``,
+    keeps ``n_pairs`` of them chosen by a generator seeded with ``seed``: the
+    same arguments give the same records, and so the same trained network."""
     import torch
     w = workloads.workload("plain_mix_8192", seed=seed)
     if markets is None:
         markets = int(math.ceil(n_pairs / (DECISIONS_PER_AGENT_STEP * record_agents * steps)))
     w["M"] = markets
     w["S"] = steps
-    ens = ks.Ensemble(w)
-    cap = ens.set_capture(record_agents=record_agents, record_capacity=n_pairs)
-    ens.step(steps)
-    if ens.sync(timeout_ms=600_000) != ks.KS_OK:
-        raise RuntimeError("data generation run reported a device error")
-    torch.cuda.synchronize()
-    n = min(int(cap["record_count"].item()), n_pairs)
-    rec = cap["records"][:n]
-    ens.close()
+    capacity = int(n_pairs * 1.5) + 1024
+    for _ in range(2):
+        ens = ks.Ensemble(w)
+        cap = ens.set_capture(record_agents=record_agents, record_capacity=capacity)
+        ens.step(steps)
+        if ens.sync(timeout_ms=600_000) != ks.KS_OK:
+            raise RuntimeError("data generation run reported a device error")
+        torch.cuda.synchronize()
+        count = int(cap["record_count"].item())
+        ens.close()
+        if count <= capacity:
+            break
+        capacity = count
+    rec = canonical_order(cap["records"][:count])
+    del cap
+    if count > n_pairs:
+        g = torch.Generator(device=rec.device).manual_seed(seed)
+        keep = torch.randperm(count, generator=g, device=rec.device)[:n_pairs].sort().values
+        rec = rec[keep].contiguous()
     return rec, w
 
 

@@ -1,20 +1,21 @@
 // ks_cda.cu -- continuous double auction over the main model's agents (see
 // kineticsim.h, ks_cda_*): one warp per market, the book in shared memory.
 //
-// The book of a market is a FIFO of resting agents per (side, tick), singly
-// linked through per-agent next indices with a head and a tail per (side,
-// tick), plus one bitmap of nonempty ticks per side, so the best bid and ask
-// are found with a few word scans.  Per step the warp's lanes draw the Philox
-// blocks, cancel and decide for 32 agents at a time (the per-step cost that
-// the call auction also has); lane 0 then removes the cancelled orders and
-// matches the new orders one by one in agent order, which continuous trading
-// makes sequential.  The serial matching waits on shared-memory latency, so a
-// market keeps only 6 bytes per agent and 8 per tick on chip and many markets
+// The book of a market is a FIFO of resting agents per (side, tick): a
+// circular list through per-agent next indices whose last agent is kept per
+// (side, tick) and points at the first; plus one bitmap of nonempty ticks per
+// side, so the best bid and ask are found with a few word scans.  Per step
+// the warp's lanes draw the Philox blocks, cancel and decide for 32 agents at
+// a time (the per-step cost that the call auction also has); lane 0 then
+// removes the cancelled orders and matches the new orders one by one in agent
+// order, which continuous trading makes sequential.  The serial matching waits on shared-memory latency, so a
+// market keeps only 6 bytes per agent and 4 per tick on chip and many markets
 // share an SM: lane 0 adds every fill to the inventory and cash in global
 // memory with reductions (no kernel reads them back), and an agent that
 // cancels draws its new order again after the cancellations instead of
-// keeping it.  Only the next indices persist in global memory; heads, tails
-// and bitmaps are rebuilt when a market is loaded.
+// keeping it.  Only the next indices persist in global memory (-1 after the
+// last agent of a FIFO); the circular links, the last agents and the bitmaps
+// are rebuilt when a market is loaded.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -57,9 +58,8 @@ struct CdaParams {
 // Shared memory of one market (one warp), 16-byte aligned regions.
 struct CdaSmem {
   uint32_t* ord;   // [A] order words; a deciding agent's new order until it is matched
-  int16_t* nxt;    // [A] next agent in the FIFO; -1 at the tail and without a resting order
-  int16_t* head;   // [2][L] first agent per (side, tick), -1 if empty
-  int16_t* tail;   // [2][L] last agent per (side, tick)
+  int16_t* nxt;    // [A] next agent in the circular FIFO; -1 without a resting order
+  int16_t* tail;   // [2][L] last agent per (side, tick), -1 if empty; its next is the first
   uint32_t* bits;  // [2][NW] nonempty ticks per side
   uint32_t* cbits; // [ceil(A / 32)] cancelled this step (while loading: agents with a predecessor)
   uint32_t* dbits; // [ceil(A / 32)] deciding this step
@@ -74,27 +74,25 @@ __host__ __device__ inline size_t cda_smem_layout(int A, int L, size_t* o) {
   const size_t a = (size_t)(A > 0 ? A : 1), nwa = (a + 31) / 32;
   o[0] = off; off = al16(off + 4 * a);                               // ord
   o[1] = off; off = al16(off + 2 * a);                               // nxt
-  o[2] = off; off = al16(off + 2 * 2 * (size_t)L);                   // head
-  o[3] = off; off = al16(off + 2 * 2 * (size_t)L);                   // tail
-  o[4] = off; off = al16(off + 4 * 2 * (size_t)cda_words(L));        // bits
-  o[5] = off; off = al16(off + 4 * nwa);                             // cbits
-  o[6] = off; off = al16(off + 4 * nwa);                             // dbits
-  o[7] = off; off = al16(off + 4 * sizeof(ClassRule));               // ctab
+  o[2] = off; off = al16(off + 2 * 2 * (size_t)L);                   // tail
+  o[3] = off; off = al16(off + 4 * 2 * (size_t)cda_words(L));        // bits
+  o[4] = off; off = al16(off + 4 * nwa);                             // cbits
+  o[5] = off; off = al16(off + 4 * nwa);                             // dbits
+  o[6] = off; off = al16(off + 4 * sizeof(ClassRule));               // ctab
   return off;
 }
 
 __device__ inline CdaSmem cda_carve(unsigned char* raw, int A, int L) {
-  size_t o[8];
+  size_t o[7];
   cda_smem_layout(A, L, o);
   CdaSmem s;
   s.ord = reinterpret_cast<uint32_t*>(raw + o[0]);
   s.nxt = reinterpret_cast<int16_t*>(raw + o[1]);
-  s.head = reinterpret_cast<int16_t*>(raw + o[2]);
-  s.tail = reinterpret_cast<int16_t*>(raw + o[3]);
-  s.bits = reinterpret_cast<uint32_t*>(raw + o[4]);
-  s.cbits = reinterpret_cast<uint32_t*>(raw + o[5]);
-  s.dbits = reinterpret_cast<uint32_t*>(raw + o[6]);
-  s.ctab = reinterpret_cast<ClassRule*>(raw + o[7]);
+  s.tail = reinterpret_cast<int16_t*>(raw + o[2]);
+  s.bits = reinterpret_cast<uint32_t*>(raw + o[3]);
+  s.cbits = reinterpret_cast<uint32_t*>(raw + o[4]);
+  s.dbits = reinterpret_cast<uint32_t*>(raw + o[5]);
+  s.ctab = reinterpret_cast<ClassRule*>(raw + o[6]);
   return s;
 }
 
@@ -130,44 +128,52 @@ struct CdaBest {
   int bid, ask;
 };
 
-// The FIFO of (side, tick) has become empty: clear its bit and move the side's
+// The FIFO of (SIDE, tick) has become empty: clear its bit and move the side's
 // best price past it.
-__device__ inline void cda_emptied(const CdaSmem& sm, int L, int NW, int side, int tick, CdaBest& best) {
-  uint32_t* b = sm.bits + side * NW;
+template <int SIDE>
+__device__ __forceinline__ void cda_emptied(const CdaSmem& sm, int L, int NW, int tick, CdaBest& best) {
+  uint32_t* b = sm.bits + SIDE * NW;
   b[tick >> 5] &= ~(1u << (tick & 31));
-  if (side == 0 && tick == best.bid) best.bid = cda_scan_down(b, tick - 1);
-  if (side == 1 && tick == best.ask) best.ask = cda_scan_up(b, NW, tick + 1, L);
+  if (SIDE == 0) {
+    if (tick == best.bid) best.bid = cda_scan_down(b, tick - 1);
+  } else {
+    if (tick == best.ask) best.ask = cda_scan_up(b, NW, tick + 1, L);
+  }
 }
 
-// Removes agent r, the first of the FIFO of (side, tick).
-__device__ inline void cda_pop(const CdaSmem& sm, int L, int NW, int r, int side, int tick, CdaBest& best) {
-  const int key = side * L + tick;
-  const int n = sm.nxt[r];
-  sm.head[key] = (int16_t)n;
-  sm.nxt[r] = -1;
-  if (n < 0) {
+// Removes agent r, the first of the FIFO of (SIDE, tick) whose last is t.
+template <int SIDE>
+__device__ __forceinline__ void cda_pop(const CdaSmem& sm, int L, int NW, int r, int t, int tick, CdaBest& best) {
+  const int key = SIDE * L + tick;
+  if (r == t) {
     sm.tail[key] = -1;
-    cda_emptied(sm, L, NW, side, tick, best);
+    cda_emptied<SIDE>(sm, L, NW, tick, best);
+  } else {
+    sm.nxt[t] = sm.nxt[r];
   }
+  sm.nxt[r] = -1;
 }
 
-// Removes agent a from anywhere in the FIFO of (side, tick); its predecessor
-// is found by walking from the head (at most A links).  False when a is not
-// in that FIFO.
-__device__ inline bool cda_remove(const CdaSmem& sm, int L, int NW, int A, int a, int side, int tick,
-                                  CdaBest& best) {
-  const int key = side * L + tick;
-  int p = sm.head[key];
-  if (p == a) {
-    cda_pop(sm, L, NW, a, side, tick, best);
-    return true;
-  }
-  for (int guard = 0; p >= 0 && guard < A; ++guard) {
+// Removes agent a from anywhere in the FIFO of (SIDE, tick); its predecessor
+// is found by walking the circle from the last agent (at most A + 1 links).
+// False when a is not in that FIFO.
+template <int SIDE>
+__device__ inline bool cda_remove(const CdaSmem& sm, int L, int NW, int A, int a, int tick, CdaBest& best) {
+  const int key = SIDE * L + tick;
+  const int t = sm.tail[key];
+  if (t < 0) return false;
+  int p = t;
+  for (int guard = 0; guard <= A; ++guard) {
     const int n = sm.nxt[p];
+    if (n < 0) return false;
     if (n == a) {
-      const int an = sm.nxt[a];
-      sm.nxt[p] = (int16_t)an;
-      if (an < 0) sm.tail[key] = (int16_t)p;
+      if (p == a) {
+        sm.tail[key] = -1;
+        cda_emptied<SIDE>(sm, L, NW, tick, best);
+      } else {
+        sm.nxt[p] = sm.nxt[a];
+        if (a == t) sm.tail[key] = (int16_t)p;
+      }
       sm.nxt[a] = -1;
       return true;
     }
@@ -176,16 +182,85 @@ __device__ inline bool cda_remove(const CdaSmem& sm, int L, int NW, int A, int a
   return false;
 }
 
-// Appends agent a at the tail of the FIFO of (side, tick).
-__device__ inline void cda_append(const CdaSmem& sm, int L, int NW, int a, int side, int tick, CdaBest& best) {
-  const int key = side * L + tick;
+// Appends agent a at the tail of the FIFO of (SIDE, tick).
+template <int SIDE>
+__device__ __forceinline__ void cda_append(const CdaSmem& sm, int L, int NW, int a, int tick, CdaBest& best) {
+  const int key = SIDE * L + tick;
   const int t = sm.tail[key];
-  sm.nxt[a] = -1;
-  if (t >= 0) sm.nxt[t] = (int16_t)a; else sm.head[key] = (int16_t)a;
+  if (t >= 0) {
+    sm.nxt[a] = sm.nxt[t];
+    sm.nxt[t] = (int16_t)a;
+  } else {
+    sm.nxt[a] = (int16_t)a;
+    sm.bits[SIDE * NW + (tick >> 5)] |= 1u << (tick & 31);
+    if (SIDE == 0) {
+      if (tick > best.bid) best.bid = tick;
+    } else {
+      if (best.ask < 0 || tick < best.ask) best.ask = tick;
+    }
+  }
   sm.tail[key] = (int16_t)a;
-  sm.bits[side * NW + (tick >> 5)] |= 1u << (tick & 31);
-  if (side == 0 && tick > best.bid) best.bid = tick;
-  if (side == 1 && (best.ask < 0 || tick < best.ask)) best.ask = tick;
+}
+
+// The new order o of agent a on side SD (0 buys, 1 sells): trades against the
+// opposite side in price-time priority while its limit crosses, every fill at
+// the resting order's tick, then rests its remainder.  Each fill goes to the
+// resting agent's inventory and cash in global memory at once, the arriving
+// agent's once for the order.  Returns the filled quantity.
+template <int SD>
+__device__ __forceinline__ int cda_arrive(const CdaSmem& sm, int L, int NW, int a, uint32_t o, CdaBest& best,
+                                          int32_t* ginv, unsigned long long* gcash, int& last_fill, int& fills,
+                                          int64_t& value, uint32_t* err) {
+  constexpr int OS = 1 - SD;
+  const int tk = (int)w_tick(o);
+  const int16_t* ot = sm.tail + OS * L;
+  int q = (int)w_qty(o);
+  int dq = 0, dv = 0;  // filled quantity and traded value of the order
+  while (q > 0) {
+    const int px = SD == 0 ? best.ask : best.bid;
+    // the limit no longer crosses, or the opposite side is empty (-1)
+    if (SD == 0 ? (uint32_t)px > (uint32_t)tk : px < tk) break;
+    const int t = ot[px];
+    const int r = t >= 0 ? sm.nxt[t] : -1;
+    if (r < 0) {  // bitmap and FIFO disagree: record it and stop matching this order
+      atomicOr(err, ERR_SHAPE);
+      break;
+    }
+    const uint32_t ro = sm.ord[r];
+    const int rq = (int)w_qty(ro);
+    if (rq == 0) {  // an empty order in a FIFO: record it, drop it (the loop still ends)
+      atomicOr(err, ERR_SHAPE);
+      cda_pop<OS>(sm, L, NW, r, t, px, best);
+      continue;
+    }
+    const int f = min(q, rq);
+    const int pf = px * f;
+    atomicAdd(ginv + r, SD == 0 ? -f : f);
+    atomicAdd(gcash + r, (unsigned long long)(long long)(SD == 0 ? pf : -pf));
+    dq += f;
+    dv += pf;
+    q -= f;
+    last_fill = px;
+    fills += 1;
+    if (f == rq) {
+      cda_pop<OS>(sm, L, NW, r, t, px, best);
+      sm.ord[r] = ro & W_STATIC;
+    } else {
+      sm.ord[r] = ro - (uint32_t)f;
+    }
+  }
+  if (dq) {
+    atomicAdd(ginv + a, SD == 0 ? dq : -dq);
+    atomicAdd(gcash + a, (unsigned long long)(long long)(SD == 0 ? -dv : dv));
+    value += dv;
+  }
+  if (q > 0) {
+    sm.ord[a] = (o & ~W_QTY) | (uint32_t)q;
+    cda_append<SD>(sm, L, NW, a, tk, best);
+  } else {
+    sm.ord[a] = o & W_STATIC;
+  }
+  return dq;
 }
 
 // Steps [s0, s0 + n) of market m by one warp.
@@ -194,14 +269,14 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
   const int nwa = (A + 31) / 32;
   const int64_t aoff = (int64_t)m * A;
   const uint32_t gm = P.market_base + m;
-  // ---- load and rebuild the book ---------------------------------------------------------
+  // ---- load and rebuild the book: links, last agents, bitmaps ------------------------------
   for (int a = lane; a < A; a += 32) {
     const uint32_t o = P.ord[aoff + a];
     const int nx = P.nxt[aoff + a];
     sm.ord[a] = o;
     sm.nxt[a] = (int16_t)(w_qty(o) != 0u && nx >= 0 && nx < A ? nx : -1);
   }
-  for (int i = lane; i < 2 * L; i += 32) sm.head[i] = sm.tail[i] = -1;
+  for (int i = lane; i < 2 * L; i += 32) sm.tail[i] = -1;
   for (int i = lane; i < 2 * NW; i += 32) sm.bits[i] = 0u;
   for (int i = lane; i < nwa; i += 32) sm.cbits[i] = 0u;
   __syncwarp();
@@ -214,13 +289,20 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
     const uint32_t o = sm.ord[a];
     if (w_qty(o) == 0u) continue;
     const int side = (int)w_sell(o), tick = (int)w_tick(o);
-    if (tick >= L) {  // written by no kernel of this library
+    if (tick >= L) {  // written by no kernel of this library: record it, drop the order
       atomicOr(P.err, ERR_TICK);
+      sm.ord[a] = o & W_STATIC;
       continue;
     }
-    if (!((sm.cbits[a >> 5] >> (a & 31)) & 1u)) sm.head[side * L + tick] = (int16_t)a;
     if (sm.nxt[a] < 0) sm.tail[side * L + tick] = (int16_t)a;
     atomicOr(&sm.bits[side * NW + (tick >> 5)], 1u << (tick & 31));
+  }
+  __syncwarp();
+  for (int a = lane; a < A; a += 32) {  // close each FIFO: the last agent's next is the first
+    const uint32_t o = sm.ord[a];
+    if (w_qty(o) == 0u || (int)w_tick(o) >= L || ((sm.cbits[a >> 5] >> (a & 31)) & 1u)) continue;
+    const int t = sm.tail[(int)w_sell(o) * L + (int)w_tick(o)];
+    if (t >= 0) sm.nxt[t] = (int16_t)a; else atomicOr(P.err, ERR_SHAPE);
   }
   __syncwarp();
   const int32_t* mi = P.mi32 + (size_t)m * MI32_STRIDE;
@@ -278,7 +360,9 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
         for (uint32_t b = sm.cbits[wi]; b; b &= b - 1u) {
           const int a = wi * 32 + __ffs(b) - 1;
           const uint32_t o = sm.ord[a];
-          if (!cda_remove(sm, L, NW, A, a, (int)w_sell(o), (int)w_tick(o), best)) atomicOr(P.err, ERR_SHAPE);
+          const bool found = w_sell(o) ? cda_remove<1>(sm, L, NW, A, a, (int)w_tick(o), best)
+                                       : cda_remove<0>(sm, L, NW, A, a, (int)w_tick(o), best);
+          if (!found) atomicOr(P.err, ERR_SHAPE);
           sm.ord[a] = o & W_STATIC;
         }
       }
@@ -301,53 +385,8 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
         for (uint32_t b = sm.dbits[wi]; b; b &= b - 1u) {
           const int a = wi * 32 + __ffs(b) - 1;
           const uint32_t o = sm.ord[a];
-          int q = (int)w_qty(o);
-          const int sd = (int)w_sell(o), tk = (int)w_tick(o);
-          const int sgn = sd == 0 ? 1 : -1;  // the arriving agent buys (+) or sells (-)
-          const int okey = (1 - sd) * L;
-          int dq = 0, dv = 0;  // the arriving order's filled quantity and traded value
-          while (q > 0) {
-            const int px = sd == 0 ? best.ask : best.bid;
-            if (px < 0 || (sd == 0 ? px > tk : px < tk)) break;  // the limit no longer crosses
-            const int r = sm.head[okey + px];
-            if (r < 0) {  // bitmap and FIFO disagree: record it and stop matching this order
-              atomicOr(P.err, ERR_SHAPE);
-              break;
-            }
-            const uint32_t ro = sm.ord[r];
-            const int rq = (int)w_qty(ro);
-            if (rq == 0) {  // an empty order in a FIFO: record it, drop it (the loop still ends)
-              atomicOr(P.err, ERR_SHAPE);
-              cda_pop(sm, L, NW, r, 1 - sd, px, best);
-              continue;
-            }
-            const int f = min(q, rq);
-            atomicAdd(ginv + r, -sgn * f);
-            atomicAdd(gcash + r, (unsigned long long)(long long)(sgn * px * f));
-            dq += f;
-            dv += px * f;
-            q -= f;
-            last_fill = px;
-            fills += 1;
-            if (f == rq) {
-              cda_pop(sm, L, NW, r, 1 - sd, px, best);
-              sm.ord[r] = ro & W_STATIC;
-            } else {
-              sm.ord[r] = ro - (uint32_t)f;
-            }
-          }
-          if (dq) {
-            atomicAdd(ginv + a, sgn * dq);
-            atomicAdd(gcash + a, (unsigned long long)(-(long long)sgn * dv));
-            vol += dq;
-            value += dv;
-          }
-          if (q > 0) {
-            sm.ord[a] = (o & ~W_QTY) | (uint32_t)q;
-            cda_append(sm, L, NW, a, sd, tk, best);
-          } else {
-            sm.ord[a] = o & W_STATIC;
-          }
+          vol += w_sell(o) ? cda_arrive<1>(sm, L, NW, a, o, best, ginv, gcash, last_fill, fills, value, P.err)
+                           : cda_arrive<0>(sm, L, NW, a, o, best, ginv, gcash, last_fill, fills, value, P.err);
         }
       }
     }
@@ -373,7 +412,9 @@ __device__ void cda_market(const CdaParams& P, uint32_t m, uint32_t s0, uint32_t
   // ---- store (the accounts are already in global memory) ----------------------------------------
   for (int a = lane; a < A; a += 32) {
     P.ord[aoff + a] = sm.ord[a];
-    P.nxt[aoff + a] = sm.nxt[a];
+    const uint32_t o = sm.ord[a];
+    const bool last_one = w_qty(o) != 0u && sm.tail[(int)w_sell(o) * L + (int)w_tick(o)] == a;
+    P.nxt[aoff + a] = last_one ? -1 : sm.nxt[a];
   }
   if (lane == 0) {
     int32_t* mo = P.mi32 + (size_t)m * MI32_STRIDE;
@@ -527,7 +568,7 @@ ks_status ks_cda_create(const ks_cda_config* cfg, void* dev_workspace, size_t ws
     delete e;
     return ccuda(ce, "device query");
   }
-  size_t o[8];
+  size_t o[7];
   const size_t per = cda_smem_layout(cfg->A, cfg->L, o);
   e->stride = (uint32_t)per;
   // One CTA per SM holds as many books (warps) as the shared memory fits, up to

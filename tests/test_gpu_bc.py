@@ -96,6 +96,23 @@ def test_training_is_reproducible(small_records):
     assert h1 == h2
 
 
+def test_generation_is_reproducible():
+    """The records (and so the network) follow from the arguments alone: the
+    kernels append in completion order; a full capacity is rerun; a subset
+    is drawn by the seed."""
+    import torch
+    kw = dict(n_pairs=10_000, markets=8, record_agents=64, steps=300)
+    a, _ = bc.generate(**kw)
+    b, _ = bc.generate(**kw)
+    assert a.shape == (10_000, 22)
+    assert torch.equal(a, b)
+    c, _ = bc.generate(**dict(kw, n_pairs=10**6))  # every record, no subset
+    assert c.shape[0] > 10_000
+    assert torch.equal(c, bc.canonical_order(c))
+    d, _ = bc.generate(**dict(kw, n_pairs=10**6))
+    assert torch.equal(c, d)
+
+
 def test_adam_step_matches_fp64_oracle():
     import torch
     rng = np.random.default_rng(0)
