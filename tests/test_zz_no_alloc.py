@@ -3,9 +3,10 @@ static device array, for callers that cannot allocate device memory for the
 kernel's work schedule and ticket counter (an allocator that is capped or
 frozen, or a host framework that only hands out the buffers it owns).
 
-Checks, through the C ABI, that two calls in a row give exactly the state that
-two ks_step_n calls give (the simulation is integer, so the tolerance of the
-other parity tests is equality): for rule agents on the default plan, for a
+Checks, through the C ABI, that two calls in a row give the oracle's state
+and trace on every market, and exactly the state that two ks_step_n calls
+give (the simulation is integer, so the tolerance of the other parity tests
+is equality): for rule agents on the default plan, for a
 1024-thread plan, and for the policy-capable kernel, on the default stream and
 on a stream of its own.  Also checks the documented limits: a plain-mode
 ensemble, too many markets and a capturing stream are refused.
@@ -60,6 +61,25 @@ def _pair(kind):
         ref.set_batch_plan(*plan)
         got.set_batch_plan(*plan)
     return ref, got
+
+
+def test_noalloc_matches_the_oracle():
+    """Rule agents over two no-alloc calls, every market and its per-step trace
+    against the oracle directly (not only through ks_step_n)."""
+    import torch
+    from helpers import compare_market, oracle_markets
+    M = 40
+    L, A = wl.batched_sizes(M, seed=23)
+    w = wl.workload("batched_20000", M=M)
+    ens = ks.Ensemble(w, trace_markets=M, trace_steps=70, L=L, A=A)
+    assert ens.batch_info()["batched"] == 1
+    assert _noalloc(ens, 45) == ks.KS_OK
+    assert _noalloc(ens, 25) == ks.KS_OK
+    torch.cuda.synchronize()
+    assert ens.sync(timeout_ms=600_000) == ks.KS_OK
+    gs = ens.read_state()
+    for m, (mk, tp, tv) in oracle_markets(w["params"], range(M), L, A, 0, 70).items():
+        compare_market(gs, ens, m, mk, tp, tv)
 
 
 @pytest.mark.parametrize("kind,own_stream", [("rule", False), ("plan1024", True), ("policy", True)])
