@@ -423,7 +423,8 @@ def cda_form(ks, workloads, stream, cpu=True, reps=2):
     st = ens.read_state(["fills"])
     ev = float(w["M"]) * w["A"] * S
     out = {"events_per_s": ev / (best / 1e3), "ms_per_run": best, "steps": S,
-           "fills_per_market_step": float(st["fills"].mean()) / (S * reps + 20)}
+           "fills_per_market_step": float(st["fills"].mean()) / (S * reps + 20),
+           "roofline": cda_roofline(ev, best)}
     ens.close()
     if cpu:
         import oracle
