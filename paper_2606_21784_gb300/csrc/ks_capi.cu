@@ -419,14 +419,23 @@ static int groups_per_cta(int nt, int gt, int ak, int Lcap, size_t max_smem, siz
 // ticks that can hold orders, small groups no longer pay for wide grids:
 // measured on the 20000-market ensemble this rule gives 1.37e11 agent-events/s
 // against 1.32e11 for the earlier one (4 agents per thread up to A = 512, at
-// least 128 threads).  Policy buckets, and shapes a CTA size does not compile,
-// take the tightest fit at about 8 agents per thread.
+// least 128 threads).  Policy buckets take the same table with groups of at
+// least one warpgroup (fewer agents per thread below 1024 agents): measured on
+// the 32768-market 25%-policy ensemble (10000 steps), 4.00e10 against 3.87e10
+// for the tightest fit at 8 agents per thread (512 x 8 for 4096 agents, where
+// 256 x 16 runs two markets per CTA).  Shapes a CTA size does not compile take the
+// tightest fit at about 8 agents per thread.
 static bool default_shape(int nt, int Ac, int* gt, int* ak, bool mlp) {
   int n = 0;
   const int(*tab)[2] = batch_table(nt, &n, mlp);
-  if (!mlp) {
-    const int k = Ac <= 2048 ? 8 : (Ac <= 8192 ? 16 : 32);
-    const int g = std::max(32, Ac / k);
+  {
+    // 8 agents per thread up to 2048 agents, 16 up to 8192, then 32; a group
+    // is at least a warp (a warpgroup for the policy kernel, whose narrowest
+    // groups then take fewer agents per thread)
+    const int k0 = Ac <= 2048 ? 8 : (Ac <= 8192 ? 16 : 32);
+    const int gmin = mlp ? 128 : 32;
+    const int g = std::max(gmin, Ac / k0);
+    const int k = mlp ? std::max(4, Ac / g) : k0;
     for (int i = 0; i < n; ++i)
       if (tab[i][0] == g && tab[i][1] == k && g <= nt) {
         *gt = g;
