@@ -126,15 +126,16 @@ def buckets_of(L, A):
 
 
 def tune_batched(w: dict, L=None, A=None, steps: int = 20, max_sample: int = 1216, use_cache: bool = True,
-                 verbose: bool = False) -> dict:
-    """Returns {"cta_threads": nt, "buckets": [(L_max, A_max, gt, ak), ...]} for an uneven workload."""
+                 verbose: bool = False, check_default: bool = True) -> dict:
+    """Returns {"cta_threads": nt, "buckets": [(L_max, A_max, gt, ak), ...]} for an uneven workload,
+    or buckets None when the library's default plan ran the whole ensemble faster."""
     from . import workloads
     if L is None or A is None:
         L, A = workloads.sizes(w)
     L = np.asarray(L, np.int32)
     A = np.asarray(A, np.int32)
     h = hashlib.sha256(L.tobytes() + A.tobytes()).hexdigest()[:16]
-    key = f"batched|{_device_tag()}|{h}|carry{w['params']['carry_book']}"
+    key = f"batched|{_device_tag()}|{h}|carry{w['params']['carry_book']}|vsdefault{int(check_default)}"
     if use_cache:
         c = _cache_load().get(key)
         if c:
@@ -175,6 +176,28 @@ def tune_batched(w: dict, L=None, A=None, steps: int = 20, max_sample: int = 121
         plans[nt] = (total, chosen)
     nt = min(plans, key=lambda k: plans[k][0])
     out = {"cta_threads": nt, "buckets": plans[nt][1], "estimated_s_per_step": plans[nt][0]}
+    # A bucket timed alone fills the GPU poorly when its markets are few or
+    # small, so the composed plan is checked against the library's default
+    # plan on the whole ensemble; buckets None means "keep the default".
+    if not check_default:
+        _cache_store(key, out)
+        return out
+    full = dict(w, M=len(L), market_base=0)
+    ev = float(A.astype(np.int64).sum()) * steps
+    ens = ks.Ensemble(full, L=L, A=A)
+    default_rate = ev / _time_steps(ens, steps)
+    default_nt = int(ens.batch_info()["cta_threads"])
+    try:
+        ens.set_batch_plan(nt, out["buckets"])
+        tuned_rate = ev / _time_steps(ens, steps)
+    except ks.KsError:
+        tuned_rate = 0.0
+    ens.close()
+    if verbose:
+        print("batched whole ensemble: default", f"{default_rate:.3e}", "tuned", f"{tuned_rate:.3e}")
+    if default_rate >= tuned_rate:
+        out = {"cta_threads": default_nt, "buckets": None, "estimated_s_per_step": plans[nt][0],
+               "kept_default": True}
     _cache_store(key, out)
     return out
 
@@ -223,7 +246,8 @@ def apply(ens, w: dict, use_cache: bool = True, verbose: bool = False) -> dict:
         return best
     if ens.batch_info()["batched"]:
         plan = tune_batched(w, ens.L, ens.A, use_cache=use_cache, verbose=verbose)
-        ens.set_batch_plan(plan["cta_threads"], plan["buckets"])
+        if plan["buckets"] is not None:
+            ens.set_batch_plan(plan["cta_threads"], plan["buckets"])
         return plan
     best = tune_plain(w, use_cache=use_cache, verbose=verbose, mlp_params=getattr(ens, "mlp_params", None))
     ens.set_launch(best["threads"], best["agents_per_thread"], reg_cap=best["reg_cap"])

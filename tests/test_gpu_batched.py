@@ -123,8 +123,11 @@ def test_autotuner_plan_is_valid_and_invariant():
     M, steps = 80, 30
     L, A = _uneven(M, seed=9)
     w = wl.workload("batched_20000", M=M)
-    plan = autotune.tune_batched(w, L, A, steps=5, use_cache=False)
+    plan = autotune.tune_batched(w, L, A, steps=5, use_cache=False, check_default=False)
     assert plan["cta_threads"] in (512, 1024) and plan["buckets"]
+    # against the default plan on the whole ensemble: a composed plan, or the default kept
+    final = autotune.tune_batched(w, L, A, steps=5, use_cache=False)
+    assert final["buckets"] is None or len(final["buckets"]) == len(plan["buckets"])
     _, ref = _run(w, L, A, steps)
     _, got = _run(w, L, A, steps, plan=(plan["cta_threads"], plan["buckets"]))
     for f in ref:
