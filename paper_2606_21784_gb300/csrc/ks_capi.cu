@@ -24,6 +24,9 @@ extern const PlainVariant kPlainNT256[];
 extern const PlainVariant kPlainNT512[];
 extern const PlainVariant kPlainNT1024[];
 extern const int kPlainNT128Count, kPlainNT256Count, kPlainNT512Count, kPlainNT1024Count;
+extern const PlainVariant kPlainSpreadA[];
+extern const PlainVariant kPlainSpreadB[];
+extern const int kPlainSpreadACount, kPlainSpreadBCount;
 extern const int kBatchVariants512[][2];
 extern const int kBatchVariants1024[][2];
 extern const int kBatchVariants512Count, kBatchVariants1024Count;
@@ -55,6 +58,17 @@ const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy
       const PlainVariant& v = tabs[i][j];
       if (v.threads == threads && v.ak == ak && v.aggregate == (aggregate ? 1 : 0) && v.occupancy == occupancy)
         return &v;
+    }
+  return nullptr;
+}
+
+const PlainVariant* find_plain_spread(int threads, int ak, int occupancy) {
+  const PlainVariant* tabs[2] = {kPlainSpreadA, kPlainSpreadB};
+  const int counts[2] = {kPlainSpreadACount, kPlainSpreadBCount};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < counts[i]; ++j) {
+      const PlainVariant& v = tabs[i][j];
+      if (v.threads == threads && v.ak == ak && v.occupancy == occupancy) return &v;
     }
   return nullptr;
 }
@@ -357,6 +371,12 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
                                                : "no kernel for this (threads, agents_per_thread, aggregate, reg_cap)");
   if ((int64_t)l->threads * l->agents_per_thread < e->Amax)
     return arg_fail(KS_ERR_INVALID_ARG, "threads * agents_per_thread below the largest A");
+  // a shape with room to spare: the variant that spreads each market's agents
+  // over the CTA, where one is compiled (same state bit for bit, fewer passes)
+  if (!e->mlp && !l->aggregate && (int64_t)l->threads * l->agents_per_thread > e->Amax) {
+    const PlainVariant* sv = find_plain_spread(l->threads, l->agents_per_thread, l->reg_cap);
+    if (sv) v = sv;
+  }
   if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
   size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, e->mlp);
   if (smem > e->max_smem) return arg_fail(KS_ERR_UNSUPPORTED, "launch shape needs more shared memory than a CTA has");

@@ -77,10 +77,13 @@ struct PlainVariant {
   PlainLaunchFn launch;
   const void* kernel;  // for attribute and occupancy queries
   int mlp = 0;         // policy path compiled in
+  int spread = 0;      // a market's agents spread over the CTA (ceil(A / threads) per thread)
 };
 
 // Registry filled by the instantiation translation units.
 const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy, bool mlp);
+// The spreading rule-agent variant of a shape, or nullptr where none is compiled.
+const PlainVariant* find_plain_spread(int threads, int ak, int occupancy);
 
 }  // namespace ks
 

@@ -175,3 +175,35 @@ def test_plain_kernel_state_paths_on_uneven_offsets():
     after = ens.read_state()
     for f in before:
         assert np.array_equal(before[f], after[f]), f
+
+
+@pytest.mark.parametrize("threads,ak,L,A", [(128, 8, 512, 700), (128, 16, 256, 1477),
+                                            (256, 8, 512, 1100), (256, 16, 1024, 2955), (512, 8, 256, 3001),
+                                            (512, 16, 512, 5909), (1024, 8, 256, 5000), (1024, 16, 256, 11818)])
+def test_spreading_plain_variants(threads, ak, L, A):
+    """A shape with room to spare runs the variant that spreads each market's
+    agents over the CTA (ceil(A / threads) per thread): every market and step
+    against the oracle, and the same state as the batched kernel, which
+    spreads agents the same way."""
+    M, steps = 3, 40
+    w = wl.workload("plain_mix_8192", M=M, L=L, A=A)
+    ens, gs = _run_gpu(w, steps, trace_markets=M, launch=dict(threads=threads, agents_per_thread=ak, reg_cap=1))
+    assert ens.batch_info()["batched"] == 0
+    ref = oracle_markets(w["params"], range(M), ens.L, ens.A, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
+
+
+def test_spreading_plain_variant_on_uneven_markets():
+    """Markets of 0 .. 4000 agents in one plain 256 x 16 launch (capacity 4096):
+    each spreads its own agents; ragged ends and empty markets included."""
+    As = np.array([4000, 0, 1, 255, 256, 257, 2049, 3999, 17, 4001], np.int32)
+    Ls = np.array([1024, 64, 2, 128, 256, 512, 1024, 300, 40, 777], np.int32)
+    w = wl.workload("plain_mix_8192", M=len(As))
+    steps = 35
+    ens, gs = _run_gpu(w, steps, trace_markets=len(As), launch=dict(threads=256, agents_per_thread=16, reg_cap=1),
+                       L=Ls, A=As)
+    assert ens.batch_info()["batched"] == 0
+    ref = oracle_markets(w["params"], range(len(As)), Ls, As, 0, steps)
+    for m, (mk, tp, tv) in ref.items():
+        compare_market(gs, ens, m, mk, tp, tv)
