@@ -235,7 +235,11 @@ ks_status ks_error_word(ks_ensemble* e, void* stream, uint32_t* word);
 
 /* Sets / gets the plain persistent kernel's launch shape (one market per CTA,
  * markets dealt round-robin).  ks_set_launch switches the ensemble to the
- * plain kernel. */
+ * plain kernel.  When threads * agents_per_thread exceeds the ensemble's
+ * largest A (and no warp aggregation is asked for), the launch runs the
+ * shape's spreading variant where one is compiled: each market spreads its
+ * agents over the CTA, ceil(A / threads) per thread; the results are the
+ * same bit for bit. */
 ks_status ks_set_launch(ks_ensemble* e, const ks_launch* l);
 ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l);
 
