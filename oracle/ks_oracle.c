@@ -16,7 +16,7 @@
  *    price priority from the top tick down, sells from the bottom tick up,
  *    until V* is used up on each side.  Inside one tick the orders fill in
  *    ascending agent index (a reading: the paper's book has no order identity).
- *  - Agents, RNG and book dynamics are the build's stated readings of the
+ *  - Agents, RNG and book dynamics follow the stated readings of the
  *    benchmark configurations (one working order per agent, Philox4x32-10
  *    draws keyed by (seed, market, agent, step)); see the function comments.
  *  - Philox4x32-10 is written from Salmon, Moraes, Dror and Shaw, "Parallel
@@ -25,7 +25,7 @@
  *  - The MLP policy (32 -> 64 -> 64 -> 3 side + 33 offset + 1 log-qty logits,
  *    ReLU) forward and backward are plain fp64 loops; the behaviour-cloning
  *    loss is cross-entropy on side and offset plus squared error on
- *    log-quantity.  Features, sampling and the loss are the build's readings
+ *    log-quantity.  Features, sampling and the loss are readings
  *    of the learned-agent configuration (the paper has no learned agents).
  *
  * The clearing loops are the definitions evaluated directly; the allocation is

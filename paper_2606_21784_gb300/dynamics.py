@@ -19,7 +19,8 @@ a step without trade), pooled over the markets of a configuration.  The
 markets run on a sliding price window (Sec. III-A) by default, so a trending
 price is not stopped by the edge of the grid; ``window=False`` runs them on a
 fixed grid of L ticks.  The paper's agent constants (Delta_noise, P_mkt,
-q_max, Delta_maker) are not published, so the numbers are this build's; the
+q_max, Delta_maker) are not published, so the numbers follow the values chosen in
+``workloads``; the
 paper's values are context.
 """
 from __future__ import annotations

@@ -29,7 +29,7 @@ shapes of the paper's throughput tables (L=128, S=500):
 ``paper_8192_256``  8192 markets, A=256 (the paper's fixed workload).
 
 The paper does not publish Delta_noise, P_mkt, q_max or Delta_maker; the
-values below are this build's choice (the standard mix alpha_mom = 0.15,
+values below are chosen here (the standard mix alpha_mom = 0.15,
 alpha_maker = 0.15 is the paper's).
 
 The uneven ensembles draw (L, A) per market from numpy's PCG64 with a fixed
