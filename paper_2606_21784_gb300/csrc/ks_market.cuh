@@ -903,7 +903,12 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     }
     const bool more = j + 1 < n_steps;
     const StepRules sr = step_rules(P, s + 1, gm, hist[0], hist_at(hist, P.mom_lb), last, fund);
-    if (t < 8) decision_row(sm.drow, sm.dsell, t, last, sr.side_mom, sr.side_mr, rc);
+    {
+      // lanes 0-7 of warp 1 write the rows: warp 0 also carries the market
+      // scalars before this barrier (0.8% on the 8192-market workload)
+      constexpr int TR = NT >= 64 ? 32 : 0;
+      if (t >= TR && t < TR + 8) decision_row(sm.drow, sm.dsell, t - TR, last, sr.side_mom, sr.side_mr, rc);
+    }
     gsync<NT>(bar);  // B5: book residual, remainders, marginal totals and rule constants visible
 
     // ---- fills of step s, fused with the orders of step s+1 ------------------------------

@@ -129,6 +129,43 @@ def test_graph_capture_replays_continue():
             assert np.array_equal(got[f], ref[f]), f
 
 
+def test_two_ensembles_double_buffered_on_two_streams():
+    """The end-to-end pattern of the benchmark: two ensembles alternate on two
+    streams, each step writing one ensemble's state from pinned host memory,
+    launching it and reading the other's result while that launch runs.  Each
+    ensemble then equals one ensemble run without interruption (and the oracle)."""
+    import torch
+    w = wl.workload("plain_mix_8192", M=12)
+    chunk, rounds = 35, 2
+    fields = ["order", "inventory", "cash", "last_tick", "history", "fundamental", "trades", "last_volume",
+              "sum_price", "sum_volume", "trace_hash"]
+    pair = (ks.Ensemble(w), ks.Ensemble(w))
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    views = [e.alloc_view(fields, pinned=True) for e in pair]
+    ks.ks_read_state(pair[0].handle, views[0][0], streams[0])
+    for f in fields:
+        views[1][1][f].copy_(views[0][1][f])
+    n = 2 * rounds
+    for i in range(n):
+        x = i % 2
+        ks.ks_write_state(pair[x].handle, views[x][0], streams[x])
+        ks.ks_step_n(pair[x].handle, chunk, streams[x])
+        if i > 0:
+            ks.ks_read_state(pair[1 - x].handle, views[1 - x][0], streams[1 - x])
+    ks.ks_read_state(pair[(n - 1) % 2].handle, views[(n - 1) % 2][0], streams[(n - 1) % 2])
+    for x in (0, 1):
+        assert pair[x].sync(timeout_ms=600_000, stream=streams[x]) == ks.KS_OK
+    ens, ref = _run_gpu(w, chunk * rounds)
+    for x in (0, 1):
+        got = {f: views[x][1][f].numpy() for f in fields}
+        for f in fields:
+            assert np.array_equal(got[f].view(ref[f].dtype).reshape(ref[f].shape), ref[f]), (x, f)
+        assert int(pair[x].read_state(["step"])["step"][0]) == chunk * rounds
+    oref = oracle_markets(w["params"], range(3), ens.L, ens.A, 0, chunk * rounds)
+    for m, (mk, _, _) in oref.items():
+        compare_market(ref, ens, m, mk)
+
+
 def test_full_size_plain_mix_sampled_markets():
     """8192 markets, L=1024, A=4096, 2000 steps in the bench's launch shape; sampled markets vs oracle."""
     w = wl.workload("plain_mix_8192")
