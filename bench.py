@@ -87,7 +87,7 @@ def kernel_source_hash(d: str | None = None) -> str:
     h = hashlib.sha256()
     d = d or os.path.join(ROOT, "paper_2606_21784_gb300", "csrc")
     for fn in sorted(os.listdir(d)):
-        if fn in PLAIN_SOURCES or fn.startswith("ks_plain_nt"):
+        if fn in PLAIN_SOURCES or fn.startswith("ks_plain_nt") or fn == "ks_plain_carried.cu":
             h.update(fn.encode())
             h.update(strip_comments(open(os.path.join(d, fn), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]

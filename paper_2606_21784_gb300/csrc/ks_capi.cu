@@ -26,6 +26,8 @@ extern const PlainVariant kPlainNT1024[];
 extern const int kPlainNT128Count, kPlainNT256Count, kPlainNT512Count, kPlainNT1024Count;
 extern const PlainVariant kPlainSpreadA[];
 extern const PlainVariant kPlainSpreadB[];
+extern const PlainVariant kPlainCarried[];
+extern const int kPlainCarriedCount;
 extern const int kPlainSpreadACount, kPlainSpreadBCount;
 extern const int kBatchVariants512[][2];
 extern const int kBatchVariants1024[][2];
@@ -70,6 +72,14 @@ const PlainVariant* find_plain_spread(int threads, int ak, int occupancy) {
       const PlainVariant& v = tabs[i][j];
       if (v.threads == threads && v.ak == ak && v.occupancy == occupancy) return &v;
     }
+  return nullptr;
+}
+
+const PlainVariant* find_plain_carried(int threads, int ak, int occupancy) {
+  for (int j = 0; j < kPlainCarriedCount; ++j) {
+    const PlainVariant& v = kPlainCarried[j];
+    if (v.threads == threads && v.ak == ak && v.occupancy == occupancy) return &v;
+  }
   return nullptr;
 }
 
@@ -376,6 +386,12 @@ static ks_status apply_launch(ks_ensemble* e, const ks_launch* l) {
   if (!e->mlp && !l->aggregate && (int64_t)l->threads * l->agents_per_thread > e->Amax) {
     const PlainVariant* sv = find_plain_spread(l->threads, l->agents_per_thread, l->reg_cap);
     if (sv) v = sv;
+  }
+  // a full shape over carried books: the variant compiled for that book mode,
+  // where one is compiled (1.1% on the 8192-market workload, same state)
+  if (!e->mlp && !l->aggregate && !v->spread && e->dp.carry) {
+    const PlainVariant* cv = find_plain_carried(l->threads, l->agents_per_thread, l->reg_cap);
+    if (cv) v = cv;
   }
   if (l->ctas_per_sm < 0 || l->ctas_per_sm > 32) return arg_fail(KS_ERR_INVALID_ARG, "ctas_per_sm out of range");
   size_t smem = plain_launch_smem(l->threads, l->agents_per_thread, l->reg_cap, e->Lmax, e->mlp);

@@ -78,12 +78,15 @@ struct PlainVariant {
   const void* kernel;  // for attribute and occupancy queries
   int mlp = 0;         // policy path compiled in
   int spread = 0;      // a market's agents spread over the CTA (ceil(A / threads) per thread)
+  int carried = 0;     // compiled for carried books only (else the book mode is read at run time)
 };
 
 // Registry filled by the instantiation translation units.
 const PlainVariant* find_plain(int threads, int ak, int aggregate, int occupancy, bool mlp);
 // The spreading rule-agent variant of a shape, or nullptr where none is compiled.
 const PlainVariant* find_plain_spread(int threads, int ak, int occupancy);
+// The carried-book variant of a full rule-agent shape, or nullptr where none is compiled.
+const PlainVariant* find_plain_carried(int threads, int ak, int occupancy);
 
 }  // namespace ks
 

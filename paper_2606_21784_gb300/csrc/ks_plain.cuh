@@ -34,7 +34,9 @@ __host__ __device__ constexpr int plain_min_ctas(int nt, int occ) {
 // SPREAD: each market spreads its agents over the CTA (ceil(A / NT) per
 // thread) instead of AK per thread, so a market smaller than the shape's
 // capacity takes fewer passes; the state is the same bit for bit.
-template <int NT, int AK, bool AGGR, int OCC, bool MLP = false, bool SPREAD = false>
+// CM: 2 reads the book mode from the parameters; 1 is compiled for carried
+// books only (the host launches it only for an ensemble that carries them).
+template <int NT, int AK, bool AGGR, int OCC, bool MLP = false, bool SPREAD = false, int CM = 2>
 __global__ void __launch_bounds__(NT, plain_min_ctas(NT, OCC)) plain_kernel(DevParams P, uint32_t n_steps) {
   constexpr int BUDGET = thread_reg_budget(NT, plain_min_ctas(NT, OCC));
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -68,14 +70,14 @@ __global__ void __launch_bounds__(NT, plain_min_ctas(NT, OCC)) plain_kernel(DevP
     const Smem sm = carve<NT, AK, false, !REGACC>(smem_raw, P.Lmax);
     for (uint32_t m = blockIdx.x; m < P.M; m += gridDim.x) {
       prefetch_next_market(P, m);
-      run_market<NT, AK, AGGR, false, REGACC, SPREAD>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax);
+      run_market<NT, AK, AGGR, false, REGACC, SPREAD, CM>(P, m, s0, n_steps, sm, (int)threadIdx.x, 0, P.Lmax);
     }
   }
 }
 
-template <int NT, int AK, bool AGGR, int OCC, bool MLP = false, bool SPREAD = false>
+template <int NT, int AK, bool AGGR, int OCC, bool MLP = false, bool SPREAD = false, int CM = 2>
 cudaError_t launch_plain(const DevParams& p, uint32_t n_steps, int grid, size_t smem, cudaStream_t st) {
-  plain_kernel<NT, AK, AGGR, OCC, MLP, SPREAD><<<grid, NT, smem, st>>>(p, n_steps);
+  plain_kernel<NT, AK, AGGR, OCC, MLP, SPREAD, CM><<<grid, NT, smem, st>>>(p, n_steps);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,9 @@ def test_plain_mix_reduced_every_market():
     dict(threads=256, agents_per_thread=16, ctas_per_sm=1, aggregate=1),
     dict(threads=512, agents_per_thread=8, reg_cap=3),
     dict(threads=1024, agents_per_thread=4, reg_cap=3),
+    # the carried-book kernels (full shapes in the 128-register class)
+    dict(threads=256, agents_per_thread=16, reg_cap=1),
+    dict(threads=512, agents_per_thread=8, reg_cap=1),
 ])
 def test_launch_shape_invariance(launch):
     """Any launch shape gives the same state (races in aggregation or allocation would differ)."""
