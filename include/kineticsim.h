@@ -239,7 +239,10 @@ ks_status ks_error_word(ks_ensemble* e, void* stream, uint32_t* word);
  * largest A (and no warp aggregation is asked for), the launch runs the
  * shape's spreading variant where one is compiled: each market spreads its
  * agents over the CTA, ceil(A / threads) per thread; the results are the
- * same bit for bit. */
+ * same bit for bit.  Otherwise, for an ensemble that carries its book, a full
+ * shape of the 128-register class (reg_cap 1; 128, 256 or 512 threads x 8 or
+ * 16 agents) runs the kernel compiled for carried books, again with the same
+ * results. */
 ks_status ks_set_launch(ks_ensemble* e, const ks_launch* l);
 ks_status ks_get_launch(const ks_ensemble* e, ks_launch* l);
 
