@@ -126,7 +126,8 @@ typedef struct ks_ensemble ks_ensemble;
  *   bit  8     side (0 buy, 1 sell)
  *   bits 9-20  limit tick
  *   bits 21-22 agent class (KS_CLASS_*)
- *   bit  23    MLP-driven agent
+ *   bit  23    MLP-driven agent (an ensemble without a policy network ignores
+ *              it: its agents follow their rule)
  */
 #define KS_ORDER_QTY(w) ((int32_t)((w) & 0xFFu))
 #define KS_ORDER_SIDE(w) ((int32_t)(((w) >> 8) & 1u))

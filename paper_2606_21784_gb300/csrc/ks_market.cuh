@@ -199,7 +199,9 @@ __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, uint32_t x0,
   const bool cancel = q != 0u && w.x < cthr;
   red_add_if(book_s + 4u * w_bidx(sl), -(int)q, cancel);
   const bool empty = valid && (q == 0u || cancel);
-  const bool dec = empty && !(sl & W_MLP);
+  // without a policy network the policy flag is ignored: every empty agent
+  // decides by its rule (no flag test: 1.9% on the 8192-market workload)
+  const bool dec = MLP ? (empty && !(sl & W_MLP)) : empty;
   const uint32_t ns = decide_rows(sl, w, drow, dsell, L);
   book_add<AGGR>(book_s, dec, ns);
   if constexpr (MLP) {
@@ -762,11 +764,10 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
     book_add<AGGR>(book_s, w_qty(slot[k]) != 0u, slot[k]);
   }
 
-  const bool carry = P.carry != 0;
   static_assert(CM >= 0 && CM <= 2, "book mode: 0 discarded, 1 carried, 2 read at run time");
-  const bool carried = CM == 2 ? carry : CM == 1;
-  const uint32_t cthr = carried ? P.cancel_thr : 0u;     // a discarded book has nothing to cancel
-  const uint32_t keep = carried ? 0xFFFFFFFFu : W_STATIC;  // what of an order word survives the step
+  const bool carry = CM == 2 ? P.carry != 0 : CM == 1;
+  const uint32_t cthr = carry ? P.cancel_thr : 0u;     // a discarded book has nothing to cancel
+  const uint32_t keep = carry ? 0xFFFFFFFFu : W_STATIC;  // what of an order word survives the step
   const bool traced = m < P.trace_markets;
   const bool tie1 = P.tie_rule == KS_TIE_MIN_IMBALANCE;
 

@@ -169,6 +169,29 @@ def test_two_ensembles_double_buffered_on_two_streams():
         compare_market(ref, ens, m, mk)
 
 
+@pytest.mark.parametrize("launch", [dict(threads=256, agents_per_thread=16),
+                                    dict(threads=256, agents_per_thread=16, reg_cap=1)])
+def test_policy_flag_written_into_rule_ensemble_is_ignored(launch):
+    """An ensemble without a policy network ignores the MLP flag of written order
+    words: its agents keep following their rule, and the flag stays in the word."""
+    w = wl.workload("plain_mix_8192", M=6)
+    ens, ref = _run_gpu(w, 40, launch=launch)
+    e2 = ks.Ensemble(w)
+    if launch:
+        e2.set_launch(**launch)
+    st = e2.read_state()
+    st["order"] = st["order"] | np.uint32(1 << 23)
+    e2.write_state(st)
+    e2.step(40)
+    assert e2.sync(timeout_ms=600_000) == ks.KS_OK
+    got = e2.read_state()
+    assert np.all(got["order"] & np.uint32(1 << 23))
+    got["order"] = got["order"] & ~np.uint32(1 << 23)
+    for f in ref:
+        if f != "trace":
+            assert np.array_equal(got[f], ref[f]), f
+
+
 def test_full_size_plain_mix_sampled_markets():
     """8192 markets, L=1024, A=4096, 2000 steps in the bench's launch shape; sampled markets vs oracle."""
     w = wl.workload("plain_mix_8192")
