@@ -187,7 +187,7 @@ __device__ __forceinline__ void record_decision(const DevParams& P, const StepFe
 // agent's first Philox word (StepKey::c0 ^ agent).  Returns the new order
 // word.  With MLP, a policy-driven agent without an order sets `policy`
 // instead of deciding, and rule decisions of recorded agents are appended.
-template <bool AGGR, bool MLP = false>
+template <bool AGGR, bool MLP = false, int CM = 2>
 __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, uint32_t x0, bool valid, const StepRules& sr,
                                                 uint32_t cthr, int L, const uint4* drow, const uint32_t* dsell,
                                                 uint32_t book_s,
@@ -208,6 +208,10 @@ __device__ __forceinline__ uint32_t order_agent(uint32_t sl, int a, uint32_t x0,
     *policy = empty && (sl & W_MLP);
     if (dec && (uint32_t)a < P->rec_agents) record_decision(*P, *f, inv, ns, sr.last);
   }
+  // carried-book rule kernels: an agent outside the market holds a zero word
+  // (no cancellation), and a cancelled agent decides, so an agent that does not
+  // decide keeps its word (0.4%)
+  if constexpr (!MLP && CM != 2) return dec ? ns : sl;
   return dec ? ns : (cancel ? (sl & W_STATIC) : sl);
 }
 
@@ -802,7 +806,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
                                           &P, &sf, sm.inv[k * NT + t]);
         pflags |= pol ? (1u << k) : 0u;
       } else {
-        slot[k] = order_agent<AGGR>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk);
+        slot[k] = order_agent<AGGR, false, CM>(slot[k], a0 + k, x0, a0 + k < A, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk);
       }
     }
     if constexpr (MLP) {
@@ -993,7 +997,7 @@ __device__ void run_market(const DevParams& P, uint32_t m, uint32_t s0, uint32_t
                                             &sf, sm.inv[k * NT + t]);
             pflags |= pol ? (1u << k) : 0u;
           } else {
-            sl[i] = order_agent<AGGR>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk);
+            sl[i] = order_agent<AGGR, false, CM>(sl[i], a0 + k, x0, valid, sr, cthr, L, sm.drow, sm.dsell, book_s, P.rk);
           }
         }
       }
